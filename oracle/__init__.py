@@ -1,0 +1,176 @@
+"""FP64 CPU oracle for photon-conserving adaptive ray tracing (arXiv:1012.2865).
+
+TEST INFRASTRUCTURE ONLY.  This package is the reference the CUDA path is
+checked against; the library itself never imports it.  Only the test suite,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use it.
+
+The arithmetic lives in ``rt_oracle.c`` (plain C, FP64, compiled without FMA
+contraction); this module only builds it and marshals numpy arrays:
+
+* ``pix2vec`` / ``pix2ang`` / ``ang2pix`` -- HEALPix nested scheme (Sec. 2.1,
+  Step 3a).
+* ``ray_path`` -- cell sequence and segment lengths of one unsplit ray
+  (Eq. "trace", Step 3d).
+* ``trace`` -- Steps 1-5 of Sec. 3.1 for every source of a grid: k_ph and
+  Gamma per cell (Eqs. "dtau", "flux", "kph", "gamma"), the photon budget,
+  packages created per HEALPix level and a checksum of the created set.
+* ``chem`` -- backward-Euler update of Eq. "dndt" (hydrogen only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+MAX_LEVEL = 14
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rt_oracle.c")
+_LIB = os.path.join(_HERE, "librt_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile rt_oracle.c into librt_oracle.so (FP64, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            d, i, u64 = ctypes.c_double, ctypes.c_int, ctypes.c_uint64
+            p = ctypes.c_void_p
+            lib.orc_pix2vec_nest.argtypes = [i, u64, p]
+            lib.orc_pix2vec_nest.restype = None
+            lib.orc_pix2ang_nest.argtypes = [i, u64, p, p]
+            lib.orc_pix2ang_nest.restype = None
+            lib.orc_ang2pix_nest.argtypes = [i, d, d]
+            lib.orc_ang2pix_nest.restype = u64
+            lib.orc_ray_path.argtypes = [p, p, p, d, i, p, p, p]
+            lib.orc_ray_path.restype = i
+            lib.orc_trace.argtypes = [p, d, p, p, i, p, p, p, p, i, d, d, i, p, p, p, p, p, p]
+            lib.orc_trace.restype = i
+            lib.orc_chem.argtypes = [ctypes.c_size_t, p, p, p, p, d, i, d]
+            lib.orc_chem.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def pix2vec(level: int, pix) -> np.ndarray:
+    """Unit vectors of nested pixel centres, shape (len(pix), 3)."""
+    lib = _load()
+    pix = np.atleast_1d(np.asarray(pix, dtype=np.uint64))
+    out = np.empty((pix.size, 3), dtype=np.float64)
+    v = np.empty(3, dtype=np.float64)
+    for j, p in enumerate(pix):
+        lib.orc_pix2vec_nest(int(level), int(p), _ptr(v))
+        out[j] = v
+    return out
+
+
+def pix2ang(level: int, pix):
+    """(z, phi) of nested pixel centres, phi in [0, 2 pi)."""
+    lib = _load()
+    pix = np.atleast_1d(np.asarray(pix, dtype=np.uint64))
+    z = np.empty(pix.size)
+    phi = np.empty(pix.size)
+    zz = ctypes.c_double()
+    pp = ctypes.c_double()
+    for j, p in enumerate(pix):
+        lib.orc_pix2ang_nest(int(level), int(p), ctypes.byref(zz), ctypes.byref(pp))
+        z[j] = zz.value
+        phi[j] = pp.value
+    return z, phi
+
+
+def ang2pix(level: int, z, phi) -> np.ndarray:
+    lib = _load()
+    z = np.atleast_1d(np.asarray(z, dtype=np.float64))
+    phi = np.atleast_1d(np.asarray(phi, dtype=np.float64))
+    out = np.empty(z.size, dtype=np.uint64)
+    for j in range(z.size):
+        out[j] = lib.orc_ang2pix_nest(int(level), float(z[j]), float(phi[j]))
+    return out
+
+
+def ray_path(dims, s, n, r0: float = 0.0, max_out: int = 100000):
+    """Cells (k, 3), segment lengths and entry radii of one unsplit ray (cell units)."""
+    lib = _load()
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    s = _f64(s)
+    n = _f64(n)
+    cells = np.empty((max_out, 3), dtype=np.int64)
+    dr = np.empty(max_out)
+    r = np.empty(max_out)
+    k = lib.orc_ray_path(_ptr(dims), _ptr(s), _ptr(n), float(r0), int(max_out), _ptr(cells),
+                         _ptr(dr), _ptr(r))
+    return cells[:k].copy(), dr[:k].copy(), r[:k].copy()
+
+
+def trace(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, *,
+          level0: int = 1, phi_c: float = 5.1, f_term: float = 1e-10,
+          max_level: int = MAX_LEVEL) -> dict:
+    """One radiative-transfer pass (Steps 1-5).  Cell index = i + nx*(j + ny*k).
+
+    Returns dict(kph, gamma (per cell, s^-1 and erg/s), budget=[emitted,
+    absorbed, escaped] (photons/s), counts[15], hashes[15], segments).
+    """
+    lib = _load()
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    ncell = int(np.prod(dims.astype(np.int64)))
+    n_H = _f64(n_H).reshape(-1)
+    x_HI = _f64(x_HI).reshape(-1)
+    assert n_H.size == ncell and x_HI.size == ncell
+    pos = _f64(pos_cm).reshape(-1)
+    ndot = _f64(ndot).reshape(-1)
+    nsrc = ndot.size
+    e = _f64(e_ph_eV).reshape(-1)
+    sg = _f64(sigma_cm2).reshape(-1)
+    assert pos.size == 3 * nsrc and e.size == nsrc and sg.size == nsrc
+    kph = np.empty(ncell)
+    gamma = np.empty(ncell)
+    budget = np.empty(3)
+    counts = np.zeros(MAX_LEVEL + 1, dtype=np.uint64)
+    hashes = np.zeros(MAX_LEVEL + 1, dtype=np.uint64)
+    seg = np.zeros(1, dtype=np.uint64)
+    rc = lib.orc_trace(_ptr(dims), float(box_len_cm), _ptr(n_H), _ptr(x_HI), int(nsrc), _ptr(pos),
+                       _ptr(ndot), _ptr(e), _ptr(sg), int(level0), float(phi_c), float(f_term),
+                       int(max_level), _ptr(kph), _ptr(gamma), _ptr(budget), _ptr(counts),
+                       _ptr(hashes), _ptr(seg))
+    if rc != 0:
+        raise ValueError("oracle trace rejected its arguments")
+    return dict(kph=kph, gamma=gamma, budget=budget, counts=counts, hashes=hashes,
+                segments=int(seg[0]))
+
+
+def chem(n_H, x_HI, x_HII, kph, dt_s: float, nsub: int, alpha_B: float):
+    """Backward-Euler update of Eq. "dndt"; returns new (x_HI, x_HII) arrays."""
+    lib = _load()
+    n_H = _f64(n_H).reshape(-1)
+    x = _f64(x_HI).reshape(-1).copy()
+    z = _f64(x_HII).reshape(-1).copy()
+    k = _f64(kph).reshape(-1)
+    assert n_H.size == x.size == z.size == k.size
+    lib.orc_chem(ctypes.c_size_t(x.size), _ptr(n_H), _ptr(x), _ptr(z), _ptr(k), float(dt_s),
+                 int(nsub), float(alpha_B))
+    return x, z
