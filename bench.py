@@ -1,0 +1,323 @@
+"""Benchmark: ray-segments per second of the coupled trace + ionisation step.
+
+Workload (the Strömgren convergence configuration): 128^3 uniform grid, box
+6.6 kpc, n_H = 1e-3 cm^-3, one 13.6 eV source of 5e48 photons/s at the
+corner, sigma = 6.3e-18 cm^2, HEALPix level 1, Phi_c = 5.1, f_term = 1e-10;
+state = the seeded-free synthetic snapshot with the I-front at the analytic
+500 Myr radius (synth.stromgren_snapshot).  One step = one rt_trace plus one
+rt_chem_update (dt = 0.5 Myr, 10 backward-Euler substeps), starting every time
+from that snapshot, so every step does identical work.
+
+Output: one JSON line (rank 0).  ``value`` = segments/s with inputs resident
+in HBM (device-timed with CUDA events on the library's stream, L2 flushed
+between steps); ``e2e`` = the same through the C ABI with pinned host
+buffers, host->device state upload and device->host k_ph/x_HI readback inside
+the timed region.  ``--impl reference`` times the FP64 CPU oracle on the same
+step instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray-segments/sec FP32-mixed vs FP64 at ≤1e-3 k_ph rel err; p50/p99 solve latency"
+UNIT = "ray-segments/s"
+WORKLOAD = ("stromgren-128^3: Test-1 medium (6.6 kpc, n_H=1e-3, corner source 5e48 ph/s, 13.6 eV), "
+            "I-front at the 500 Myr radius; step = rt_trace (level 1, Phi_c 5.1, f_term 1e-10) + "
+            "rt_chem_update (0.5 Myr, 10 substeps)")
+DT_S = 0.5 * 3.15576e13
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def run_native(args, rank, world, local):
+    import torch
+    from paper_1012_2865_gb300 import build, native, synth
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = native.rt_ctx_create(local)
+    g = synth.stromgren_snapshot(128)
+    params = dict(synth.DEFAULT_PARAMS)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
+
+    x0 = torch.tensor(g["x_HI"], dtype=torch.float64, device=dev)
+    z0 = torch.tensor(g["x_HII"], dtype=torch.float64, device=dev)
+
+    def measure(precision):
+        grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
+        b = grid.trace(**params)  # sizes the queue
+        cap = max(1 << 20, int(b["queue_pushed"] * 1.5))
+        qp = dict(params, queue_capacity=cap)
+        seg_per_step = b["segments"]
+        pushed = b["queue_pushed"]
+        for _ in range(max(3, args.warmup)):
+            native.rt_set_state(grid.h, x0, z0)
+            grid.trace(sync=False, **qp)
+            grid.chem(DT_S, 10, synth.ALPHA_B)
+        torch.cuda.synchronize()
+        step_ms, kern_ms = [], []
+        segs = 0
+        launches = 0
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                native.rt_set_state(grid.h, x0, z0)  # restore the snapshot (untimed)
+                flush.zero_()                         # evict L2 between steps (untimed)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                l0 = native.rt_kernel_launches()
+                e0.record(stream)
+                grid.trace(sync=False, **qp)
+                grid.chem(DT_S, 10, synth.ALPHA_B)
+                e1.record(stream)
+                launches += native.rt_kernel_launches() - l0
+                e1.synchronize()
+                bb = native.rt_get_budget(grid.h)
+                step_ms.append(e0.elapsed_time(e1))
+                kern_ms.append(bb["kernel_ms"])
+                segs += bb["segments"]
+                assert bb["segments"] == seg_per_step
+        grid.close()
+        return dict(step_ms=step_ms, kern_ms=kern_ms, segments=segs, seg_per_step=seg_per_step,
+                    pushed=pushed, launches=launches, clocks=clk.summary())
+
+    def e2e(precision):
+        grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
+        b = grid.trace(**params)
+        qp = dict(params, queue_capacity=max(1 << 20, int(b["queue_pushed"] * 1.5)))
+        n = grid.ncell
+        hx = torch.tensor(g["x_HI"], dtype=torch.float64).pin_memory()
+        hz = torch.tensor(g["x_HII"], dtype=torch.float64).pin_memory()
+        hk = torch.empty(n, dtype=torch.float64).pin_memory()
+        hxo = torch.empty(n, dtype=torch.float64).pin_memory()
+        lib = native.lib()
+        segs = 0
+        for i in range(max(3, args.warmup) + args.steps):
+            if i == max(3, args.warmup):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            native.check(lib.rt_set_state(grid.h, None, hx.data_ptr(), hz.data_ptr(), native.RT_MEM_HOST))
+            grid.trace(sync=False, **qp)
+            grid.chem(DT_S, 10, synth.ALPHA_B)
+            native.check(lib.rt_get_rates(grid.h, hk.data_ptr(), None, hxo.data_ptr(),
+                                          native.RT_DTYPE_F64, native.RT_MEM_HOST))
+            if i >= max(3, args.warmup):
+                segs += native.rt_get_budget(grid.h)["segments"]
+        dt = time.perf_counter() - t0
+        grid.close()
+        return dict(value=segs / dt, h2d=2 * n * 8, d2h=2 * n * 8)
+
+    res = {}
+    for prec in args.precisions:
+        res[prec] = measure(prec)
+    head = args.precisions[0]
+    r = res[head]
+    total_s = sum(r["step_ms"]) / 1e3
+    kern_s = sum(r["kern_ms"]) / 1e3
+    # max over ranks, sum of work
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = r["segments"] * world / total_s
+    ee = e2e(head)
+    peaks, peak_kind = _peaks()
+    ebytes = 8 if head == "fp64" else 4
+    rec = 48 if head == "fp64" else 32
+    # algorithmic bytes per launch: n_HI read + k_ph RED per segment (Gamma is
+    # identically 0 for 13.6 eV photons) + one write and one read per queue record
+    alg = r["seg_per_step"] * 2 * ebytes + r["pushed"] * 2 * rec
+    achieved = alg / (kern_s / args.steps) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": head, "segments_per_step": r["seg_per_step"],
+                   "queue_records_per_step": r["pushed"], "l2": "flushed (512 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0),
+                     "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs", 6800.0),
+                     "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "trace_kernel", "kernel_ms": 1e3 * kern_s / args.steps},
+        "e2e": {"value": ee["value"], "unit": UNIT, "h2d_bytes_per_step": ee["h2d"],
+                "d2h_bytes_per_step": ee["d2h"]},
+        "gpu_launches": int(r["launches"]),
+        "clocks": r["clocks"],
+    }
+    for prec in args.precisions[1:]:
+        q = res[prec]
+        out[f"{prec}_path"] = {"value": q["segments"] * world / (sum(q["step_ms"]) / 1e3),
+                               "ms_per_step": sum(q["step_ms"]) / args.steps,
+                               "kernel_ms": sum(q["kern_ms"]) / args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    return out
+
+
+def oracle_step(g, x, z):
+    import oracle
+    from paper_1012_2865_gb300 import synth
+    o = oracle.trace(g["dims"], g["box_len_cm"], g["n_H"], x, g["pos_cm"], g["ndot"], g["e_ph_eV"],
+                     g["sigma_cm2"], **synth.DEFAULT_PARAMS)
+    oracle.chem(g["n_H"], x, z, o["kph"], DT_S, 10, synth.ALPHA_B)
+    return o["segments"]
+
+
+def cpu_baseline(seconds: float) -> dict:
+    from paper_1012_2865_gb300 import synth
+    g = synth.stromgren_snapshot(128)
+    segs, n = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        segs += oracle_step(g, g["x_HI"], g["x_HII"])
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": segs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full steps of the bench workload (FP64 C oracle, 1 thread), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_1012_2865_gb300 import synth
+    import oracle
+    oracle.build()
+    g = synth.stromgren_snapshot(128)
+    for _ in range(args.warmup):
+        oracle_step(g, g["x_HI"], g["x_HII"])
+    segs = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        segs += oracle_step(g, g["x_HI"], g["x_HII"])
+    dt = time.perf_counter() - t0
+    v = segs / dt
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {"workload": WORKLOAD, "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full steps of the bench workload"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precisions", default="fp64")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        dist.barrier()
+    out = run_native(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * rt.h -- C ABI of the GB300 adaptive ray-tracing library.
+ *
+ * The library computes the radiation field of point sources on a uniform
+ * Cartesian grid with photon-conserving adaptive ray tracing (Wise & Abel,
+ * arXiv:1012.2865, Sec. 2.1-2.2 and Steps 1-7 of Sec. 3.1) and the
+ * hydrogen-only ionisation update that couples consecutive traces
+ * (Eq. "dndt").  All work runs in CUDA kernels on one GPU; there is no CPU
+ * fallback.
+ *
+ * Conventions for every call:
+ *   - return value: RT_OK (0) or one of the RT_ERR_* codes below; on error
+ *     rt_get_last_error() gives a message (thread-local, valid until the
+ *     next call on the same thread).  No exception crosses the ABI.
+ *   - handles are opaque; the caller owns them and releases them with the
+ *     matching *_destroy call.  A handle may be used from one host thread
+ *     at a time.
+ *   - a cell index is i + nx*(j + ny*k) (x fastest); all cells are cubes of
+ *     width dx = box_len_cm / nx.
+ *   - work is enqueued on the grid's CUDA stream (cudaStream_t passed as
+ *     void*; NULL = the legacy default stream).  Calls that return results
+ *     to the host synchronise that stream; the others are asynchronous.
+ *   - units: cm, s, photons/s, eV on input; k_ph in s^-1 and Gamma in erg/s
+ *     per absorbing atom on output.
+ */
+#ifndef GB300_RT_H
+#define GB300_RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RT_OK 0
+#define RT_ERR_INVALID_ARG 1    /* argument out of range; nothing was changed */
+#define RT_ERR_OOM 2            /* device memory could not be allocated */
+#define RT_ERR_CUDA 3           /* a CUDA call failed (message has the CUDA error) */
+#define RT_ERR_QUEUE_OVERFLOW 4 /* the package queue was too small (async traces only) */
+#define RT_ERR_LEVEL_OVERFLOW 5 /* a package would exceed RT_MAX_LEVEL */
+#define RT_ERR_TIMEOUT 6        /* a bounded device wait ran out; results are invalid */
+#define RT_ERR_STATE 7          /* call not valid in the object's current state */
+
+/* arithmetic of a grid */
+#define RT_FP64 0        /* traversal, optical depth and deposits in FP64 */
+#define RT_FP32_MIXED 1  /* traversal, tau and deposits in FP32; FP64 photon
+                            budget, FP64 split/termination decisions near
+                            ties, FP64 ionisation update */
+/* where a caller buffer lives */
+#define RT_MEM_HOST 0
+#define RT_MEM_DEVICE 1
+/* element type of a caller output buffer */
+#define RT_DTYPE_F64 0
+#define RT_DTYPE_F32 1
+
+#define RT_MAX_LEVEL 14 /* pixel numbers 12*4^14 still fit 32 bits */
+
+typedef struct rt_ctx rt_ctx;
+typedef struct rt_grid rt_grid;
+typedef struct rt_batch rt_batch;
+
+/* Grid description (Sec. 2.2: the absorber density n_HI = n_H x_HI per cell). */
+typedef struct {
+  int nx, ny, nz;        /* cells per axis, each >= 1, nx*ny*nz < 2^31 */
+  double box_len_cm;     /* x extent of the box (> 0) */
+  int precision;         /* RT_FP64 or RT_FP32_MIXED */
+  int mem_kind;          /* RT_MEM_HOST or RT_MEM_DEVICE for the arrays below */
+  const double* n_H;     /* [ncell] hydrogen density, cm^-3, >= 0 */
+  const double* x_HI;    /* [ncell] neutral fraction in [0, 1] */
+  const double* x_HII;   /* [ncell] ionised fraction, or NULL for 1 - x_HI */
+} rt_grid_desc;
+
+/* Method parameters of one trace (Sec. 2.1). */
+typedef struct {
+  int level0;            /* initial HEALPix level of emitted packages (>= 0) */
+  double phi_c;          /* minimum rays per cell face, Eq. "split" (> 0) */
+  double f_term;         /* a package ends when P < f_term * P_0, (0, 1) */
+  int max_level;         /* no split beyond this level (level0..RT_MAX_LEVEL) */
+  int64_t queue_capacity;/* package records in the device queue; 0 = automatic */
+  double timeout_s;      /* bound on any device-side wait; <= 0 = 2 s */
+  int block_threads;     /* threads per block of the trace kernel; 0 = tuned */
+  int segs_per_iter;     /* segments a lane traces between queue visits; 0 = tuned */
+} rt_trace_params;
+
+/* Result of a trace, per grid. */
+typedef struct {
+  double emitted;                      /* photons/s leaving the sources */
+  double absorbed;                     /* photons/s absorbed in the grid */
+  double escaped;                      /* photons/s leaving the box */
+  uint64_t counts[RT_MAX_LEVEL + 1];   /* packages created per HEALPix level */
+  uint64_t hashes[RT_MAX_LEVEL + 1];   /* order-free checksum of the created
+                                          (source, level, pixel) set, see below */
+  uint64_t segments;                   /* cell segments with length > 0 */
+  uint64_t fallbacks;                  /* FP32 decisions re-taken in FP64 */
+  uint64_t queue_pushed;               /* records written to the queue */
+  int status;                          /* RT_OK or the device-side error */
+  float kernel_ms;                     /* duration of the trace kernel itself
+                                          (CUDA events on the grid's stream) */
+} rt_budget;
+/* hashes[l] is the sum modulo 2^64 over created packages of
+ * mix(((uint64)src << 40) ^ ((uint64)l << 34) ^ pixel), where mix is the
+ * 64-bit finaliser x ^= x>>31; x *= 0x7fb5d329728ea185; x ^= x>>27;
+ * x *= 0x81dadef4bc2dd44d; x ^= x>>33.  src counts from 0 in the order the
+ * grid's sources were added. */
+
+/* Context: one CUDA device.  device >= 0. */
+int rt_ctx_create(int device, rt_ctx** out);
+int rt_ctx_destroy(rt_ctx* ctx);
+
+/* Create a grid (Sec. 2.2 state: n_H, x_HI, x_HII) in library-owned device
+ * memory.  The caller's arrays are copied; they may be freed on return.
+ * stream: cudaStream_t for all later work on this grid. */
+int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* desc, void* stream, rt_grid** out);
+int rt_grid_destroy(rt_grid* grid);
+
+/* Append n point sources (Sec. 2.1, Step 1).  Host arrays, copied:
+ *   pos_cm[3n] position in [0, box]^3, ndot[n] photons/s (>= 0),
+ *   e_ph_eV[n] photon energy (>= 13.6), sigma_cm2[n] absorption cross section
+ *   (>= 0).  Sources keep the order of addition (their index in hashes). */
+int rt_add_sources(rt_grid* grid, int n, const double* pos_cm, const double* ndot,
+                   const double* e_ph_eV, const double* sigma_cm2);
+int rt_clear_sources(rt_grid* grid);
+
+/* One radiative-transfer pass, Steps 1-5: zero k_ph and Gamma, emit
+ * 12*4^level0 packages per source, trace every package through the grid
+ * (DDA, Eq. "trace"; split, Eq. "split"; absorption, Eqs. "dtau", "flux";
+ * deposits, Eqs. "kph", "gamma"; termination) and reduce the photon budget.
+ * out == NULL: enqueue only (no host synchronisation; may be captured in a
+ * CUDA graph when queue_capacity > 0); read the result with rt_get_budget.
+ * out != NULL: wait, and retry with a larger queue if it overflowed. */
+int rt_trace(rt_grid* grid, const rt_trace_params* params, rt_budget* out);
+/* Result of the last trace (synchronises the grid's stream). */
+int rt_get_budget(rt_grid* grid, rt_budget* out);
+
+/* Step 6: advance x_HI, x_HII of every cell by dt_s with nsub backward-Euler
+ * substeps of Eq. "dndt" (hydrogen only, n_e = n_p = n_H x_HII, no
+ * collisional ionisation), k_ph of the last trace held fixed, then refresh
+ * the absorber density used by the next trace.  dt_s >= 0, nsub >= 1,
+ * alpha_B >= 0 (cm^3/s).  Asynchronous. */
+int rt_chem_update(rt_grid* grid, double dt_s, int nsub, double alpha_B);
+
+/* Replace the gas state of every cell (Sec. 2.2): n_H (may be NULL to keep
+ * it), x_HI, and x_HII (NULL for 1 - x_HI), in memory mem_kind, same checks
+ * as rt_create_grid; refreshes the absorber density.  Asynchronous for
+ * device pointers; host arrays are copied before the call returns. */
+int rt_set_state(rt_grid* grid, const double* n_H, const double* x_HI, const double* x_HII,
+                 int mem_kind);
+
+/* Copy k_ph (s^-1), Gamma (erg/s) and x_HI of every cell into caller buffers
+ * (any may be NULL) of element type dtype in memory mem_kind.  Synchronous. */
+int rt_get_rates(rt_grid* grid, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind);
+/* Copy x_HII likewise. */
+int rt_get_ionised(rt_grid* grid, void* x_HII, int dtype, int mem_kind);
+
+/* Wait for all work enqueued on the grid's stream. */
+int rt_synchronize(rt_grid* grid);
+
+/* Number of kernels this library launched on the calling process so far. */
+uint64_t rt_kernel_launches(void);
+
+/* Message for the last error on this host thread ("" if none). */
+const char* rt_get_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_RT_H */

@@ -1,0 +1,551 @@
+// api.cu -- host implementation of the C ABI declared in rt.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "rt.h"
+#include "rt_internal.cuh"
+
+namespace rtg {
+cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, cudaStream_t st);
+cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm);
+cudaError_t launch_trace(int precision, const TraceArgs& A, int grid, int block, cudaStream_t st);
+cudaError_t launch_chem(int precision, long long ncell, const double* nH, double* xHI, double* xHII,
+                        const void* K, void* nhi, double h, int nsub, double alpha, cudaStream_t st);
+cudaError_t launch_refresh(int precision, long long ncell, const double* nH, const double* xHI,
+                           void* nhi, cudaStream_t st);
+cudaError_t launch_convert(long long n, const void* src, int src_dtype, void* dst, int dst_dtype,
+                           cudaStream_t st);
+cudaError_t launch_complement(long long n, const double* x, double* out, cudaStream_t st);
+}  // namespace rtg
+
+using namespace rtg;
+
+static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+    }                                                                                         \
+  } while (0)
+
+#define LAUNCH_TRY(call)  \
+  do {                    \
+    CUDA_TRY(call);       \
+    g_launches.fetch_add(1); \
+  } while (0)
+
+struct rt_ctx {
+  int device;
+  int num_sms;
+};
+
+// Per-trace device resources: queue, control words, descriptors.
+struct TraceState {
+  void* queue = nullptr;
+  unsigned long long cap = 0;  // records
+  size_t rec_bytes = 0;
+  unsigned long long* ctl = nullptr;
+  ~TraceState() {
+    if (queue) cudaFree(queue);
+    if (ctl) cudaFree(ctl);
+  }
+};
+
+struct rt_grid {
+  rt_ctx* ctx;
+  int nx, ny, nz;
+  long long ncell;
+  double box_len_cm, dx;
+  int precision;
+  cudaStream_t stream;
+  double* nH = nullptr;
+  double* xHI = nullptr;
+  double* xHII = nullptr;
+  void* nhi = nullptr;  // FP64 or FP32
+  void* K = nullptr;
+  void* G = nullptr;
+  double* acc = nullptr;               // 4 doubles
+  unsigned long long* cnt = nullptr;   // kCntWords
+  InstDev* inst_dev = nullptr;
+  struct SrcIn { double pos[3], ndot, e_ph, sigma; };
+  std::vector<SrcIn> src;              // sources as given by the caller
+  SourceDev* src_dev = nullptr;
+  size_t src_dev_cap = 0;
+  bool src_dirty = true;
+  int last_level0 = -1;
+  TraceState ts;
+  // pinned readback buffer
+  void* host_rb = nullptr;
+  bool traced = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last trace kernel
+  ~rt_grid() {
+    cudaFree(nH); cudaFree(xHI); cudaFree(xHII); cudaFree(nhi); cudaFree(K); cudaFree(G);
+    cudaFree(acc); cudaFree(cnt); cudaFree(inst_dev); cudaFree(src_dev);
+    if (host_rb) cudaFreeHost(host_rb);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+};
+
+static size_t elem_bytes(int precision) { return precision == RT_FP64 ? 8 : 4; }
+
+extern "C" {
+
+const char* rt_get_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t rt_kernel_launches(void) { return g_launches.load(); }
+
+int rt_ctx_create(int device, rt_ctx** out) {
+  if (!out) return fail(RT_ERR_INVALID_ARG, "rt_ctx_create: out is NULL");
+  int n = 0;
+  CUDA_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(RT_ERR_INVALID_ARG, "rt_ctx_create: device %d of %d", device, n);
+  CUDA_TRY(cudaSetDevice(device));
+  rt_ctx* c = new rt_ctx;
+  c->device = device;
+  CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  *out = c;
+  g_last_error.clear();
+  return RT_OK;
+}
+
+int rt_ctx_destroy(rt_ctx* ctx) {
+  delete ctx;
+  return RT_OK;
+}
+
+static int upload(void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_t st) {
+  CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, mem_kind == RT_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                        : cudaMemcpyHostToDevice, st));
+  return RT_OK;
+}
+
+int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** out) {
+  if (!ctx || !d || !out) return fail(RT_ERR_INVALID_ARG, "rt_create_grid: NULL argument");
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(RT_ERR_INVALID_ARG, "rt_create_grid: dims must be >= 1");
+  const long long ncell = (long long)d->nx * d->ny * d->nz;
+  if (ncell >= (1LL << 31)) return fail(RT_ERR_INVALID_ARG, "rt_create_grid: %lld cells exceed 2^31", ncell);
+  if (!(d->box_len_cm > 0) || !isfinite(d->box_len_cm))
+    return fail(RT_ERR_INVALID_ARG, "rt_create_grid: box_len_cm must be positive");
+  if (d->precision != RT_FP64 && d->precision != RT_FP32_MIXED)
+    return fail(RT_ERR_INVALID_ARG, "rt_create_grid: unknown precision %d", d->precision);
+  if (d->mem_kind != RT_MEM_HOST && d->mem_kind != RT_MEM_DEVICE)
+    return fail(RT_ERR_INVALID_ARG, "rt_create_grid: unknown mem_kind %d", d->mem_kind);
+  if (!d->n_H || !d->x_HI) return fail(RT_ERR_INVALID_ARG, "rt_create_grid: n_H and x_HI are required");
+  if (d->mem_kind == RT_MEM_HOST) {
+    for (long long c = 0; c < ncell; ++c) {
+      const double n = d->n_H[c], x = d->x_HI[c];
+      if (!(n >= 0) || !isfinite(n)) return fail(RT_ERR_INVALID_ARG, "rt_create_grid: n_H[%lld] = %g", c, n);
+      if (!(x >= 0 && x <= 1)) return fail(RT_ERR_INVALID_ARG, "rt_create_grid: x_HI[%lld] = %g", c, x);
+    }
+  }
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  rt_grid* g = new rt_grid;
+  g->ctx = ctx;
+  g->nx = d->nx; g->ny = d->ny; g->nz = d->nz;
+  g->ncell = ncell;
+  g->box_len_cm = d->box_len_cm;
+  g->dx = d->box_len_cm / d->nx;
+  g->precision = d->precision;
+  g->stream = (cudaStream_t)stream;
+  const size_t n8 = (size_t)ncell * 8, ne = (size_t)ncell * elem_bytes(d->precision);
+  int rc = RT_OK;
+#define ALLOC(p, b)                                        \
+  do {                                                     \
+    cudaError_t e_ = cudaMalloc((void**)&(p), (b));        \
+    if (e_ != cudaSuccess) {                               \
+      delete g;                                            \
+      return fail(RT_ERR_OOM, "rt_create_grid: cudaMalloc(%zu): %s", (size_t)(b), cudaGetErrorString(e_)); \
+    }                                                      \
+  } while (0)
+  ALLOC(g->nH, n8);
+  ALLOC(g->xHI, n8);
+  ALLOC(g->xHII, n8);
+  ALLOC(g->nhi, ne);
+  ALLOC(g->K, ne);
+  ALLOC(g->G, ne);
+  ALLOC(g->acc, 4 * sizeof(double));
+  ALLOC(g->cnt, kCntWords * sizeof(unsigned long long));
+  ALLOC(g->inst_dev, sizeof(InstDev));
+  ALLOC(g->ts.ctl, CTL_N * sizeof(unsigned long long));
+#undef ALLOC
+  cudaStream_t st = g->stream;
+  if ((rc = upload(g->nH, d->n_H, n8, d->mem_kind, st)) != RT_OK) { delete g; return rc; }
+  if ((rc = upload(g->xHI, d->x_HI, n8, d->mem_kind, st)) != RT_OK) { delete g; return rc; }
+  if (d->x_HII) {
+    if ((rc = upload(g->xHII, d->x_HII, n8, d->mem_kind, st)) != RT_OK) { delete g; return rc; }
+  } else {
+    cudaError_t e = launch_complement(ncell, g->xHI, g->xHII, st);
+    if (e != cudaSuccess) { delete g; return fail(RT_ERR_CUDA, "complement: %s", cudaGetErrorString(e)); }
+    g_launches.fetch_add(1);
+  }
+  cudaError_t e = launch_refresh(g->precision, ncell, g->nH, g->xHI, g->nhi, st);
+  if (e != cudaSuccess) { delete g; return fail(RT_ERR_CUDA, "refresh: %s", cudaGetErrorString(e)); }
+  g_launches.fetch_add(1);
+  e = cudaMemsetAsync(g->ts.ctl, 0, CTL_N * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->K, 0, ne, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->G, 0, ne, st);
+  InstDev I;
+  I.nx = g->nx; I.ny = g->ny; I.nz = g->nz; I.pad = 0;
+  I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.K = g->K; I.G = g->G; I.acc = g->acc; I.cnt = g->cnt;
+  if (e == cudaSuccess) e = cudaMemcpy(g->inst_dev, &I, sizeof I, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMallocHost(&g->host_rb, 4096);
+  if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { delete g; return fail(RT_ERR_CUDA, "rt_create_grid: %s", cudaGetErrorString(e)); }
+  *out = g;
+  g_last_error.clear();
+  return RT_OK;
+}
+
+int rt_grid_destroy(rt_grid* g) {
+  if (!g) return RT_OK;
+  cudaStreamSynchronize(g->stream);
+  delete g;
+  return RT_OK;
+}
+
+int rt_add_sources(rt_grid* g, int n, const double* pos, const double* ndot, const double* e_ph,
+                   const double* sigma) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: grid is NULL");
+  if (n < 0) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: n = %d", n);
+  if (n == 0) return RT_OK;
+  if (!pos || !ndot || !e_ph || !sigma) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: NULL array");
+  const double ext[3] = {g->nx * g->dx, g->ny * g->dx, g->nz * g->dx};
+  for (int i = 0; i < n; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      const double p = pos[3 * i + a];
+      if (!(p >= 0 && p <= ext[a])) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: source %d axis %d at %g outside [0, %g]", i, a, p, ext[a]);
+    }
+    if (!(ndot[i] >= 0) || !isfinite(ndot[i])) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: ndot[%d] = %g", i, ndot[i]);
+    if (!(e_ph[i] >= kEHI) || !isfinite(e_ph[i])) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: e_ph_eV[%d] = %g < 13.6", i, e_ph[i]);
+    if (!(sigma[i] >= 0) || !isfinite(sigma[i])) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: sigma[%d] = %g", i, sigma[i]);
+  }
+  if (g->src.size() + (size_t)n > (1u << 23)) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: too many sources");
+  for (int i = 0; i < n; ++i) {
+    rt_grid::SrcIn S;
+    for (int a = 0; a < 3; ++a) S.pos[a] = pos[3 * i + a];
+    S.ndot = ndot[i];
+    S.e_ph = e_ph[i];
+    S.sigma = sigma[i];
+    g->src.push_back(S);
+  }
+  g->src_dirty = true;
+  return RT_OK;
+}
+
+int rt_clear_sources(rt_grid* g) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_clear_sources: grid is NULL");
+  g->src.clear();
+  g->src_dirty = true;
+  return RT_OK;
+}
+
+static bool exact_in_f32(double v) { return (double)(float)v == v && fabs(v) < 4194304.0; }
+
+// Build the per-source device table for a given initial level.
+static int prepare_sources(rt_grid* g, int level0) {
+  if (!g->src_dirty && g->last_level0 == level0) return RT_OK;
+  const double npix0 = 12.0 * ldexp(1.0, 2 * level0);
+  std::vector<SourceDev> v(g->src.size());
+  const double dx = g->dx, vol = dx * dx * dx;
+  for (size_t i = 0; i < v.size(); ++i) {
+    const rt_grid::SrcIn& H = g->src[i];
+    SourceDev S;
+    memset(&S, 0, sizeof S);
+    for (int a = 0; a < 3; ++a) S.s[a] = H.pos[a] / dx;  // cell units
+    S.sdx = H.sigma * dx;
+    S.heat = (H.e_ph - kEHI) * kEvErg;
+    S.unit = H.ndot / npix0;  // Step 1: luminosity spread equally over N_pix
+    S.w = S.unit * H.sigma / (dx * dx);
+    S.rw = S.unit / vol;
+    S.inst = 0;
+    S.local = (int)i;
+    int exact = 1;
+    for (int a = 0; a < 3; ++a) {
+      S.s32[a] = (float)S.s[a];
+      S.ds32[a] = (float)fabs((double)S.s32[a] - S.s[a]);
+      exact &= exact_in_f32(S.s[a]) ? 1 : 0;
+    }
+    S.exact32 = exact;
+    S.sdx32 = (float)S.sdx;
+    S.w32 = (float)S.w;
+    S.rw32 = (float)S.rw;
+    S.heat32 = (float)S.heat;
+    v[i] = S;
+  }
+  if (v.size() > g->src_dev_cap) {
+    if (g->src_dev) cudaFree(g->src_dev);
+    g->src_dev = nullptr;
+    const size_t cap = v.size() < 64 ? 64 : v.size();
+    CUDA_TRY(cudaMalloc((void**)&g->src_dev, cap * sizeof(SourceDev)));
+    g->src_dev_cap = cap;
+  }
+  if (!v.empty())
+    CUDA_TRY(cudaMemcpyAsync(g->src_dev, v.data(), v.size() * sizeof(SourceDev), cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));  // v goes out of scope
+  g->src_dirty = false;
+  g->last_level0 = level0;
+  return RT_OK;
+}
+
+static int check_params(const rt_trace_params* p) {
+  if (!p) return fail(RT_ERR_INVALID_ARG, "rt_trace: params is NULL");
+  if (p->level0 < 0 || p->level0 > RT_MAX_LEVEL) return fail(RT_ERR_INVALID_ARG, "rt_trace: level0 = %d", p->level0);
+  if (p->max_level < p->level0 || p->max_level > RT_MAX_LEVEL)
+    return fail(RT_ERR_INVALID_ARG, "rt_trace: max_level = %d", p->max_level);
+  if (!(p->phi_c > 0) || !isfinite(p->phi_c)) return fail(RT_ERR_INVALID_ARG, "rt_trace: phi_c = %g", p->phi_c);
+  if (!(p->f_term > 0 && p->f_term < 1)) return fail(RT_ERR_INVALID_ARG, "rt_trace: f_term = %g", p->f_term);
+  if (p->queue_capacity < 0) return fail(RT_ERR_INVALID_ARG, "rt_trace: queue_capacity < 0");
+  if (p->block_threads != 0 && (p->block_threads % 32 != 0 || p->block_threads > 256 || p->block_threads < 32))
+    return fail(RT_ERR_INVALID_ARG, "rt_trace: block_threads = %d", p->block_threads);
+  if (p->segs_per_iter < 0 || p->segs_per_iter > 1024) return fail(RT_ERR_INVALID_ARG, "rt_trace: segs_per_iter = %d", p->segs_per_iter);
+  return RT_OK;
+}
+
+static int ensure_queue(rt_grid* g, unsigned long long cap) {
+  const size_t rec = g->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+  if (g->ts.queue && g->ts.cap >= cap && g->ts.rec_bytes == rec) return RT_OK;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (g->ts.queue) cudaFree(g->ts.queue);
+  g->ts.queue = nullptr;
+  g->ts.cap = 0;
+  CUDA_TRY(cudaMalloc(&g->ts.queue, cap * rec));
+  // tags start at 0; epochs start at 1
+  CUDA_TRY(cudaMemset(g->ts.queue, 0, cap * rec));
+  g->ts.cap = cap;
+  g->ts.rec_bytes = rec;
+  return RT_OK;
+}
+
+static int enqueue_trace(rt_grid* g, const rt_trace_params* p) {
+  int rc = prepare_sources(g, p->level0);
+  if (rc) return rc;
+  cudaStream_t st = g->stream;
+  const size_t ne = (size_t)g->ncell * elem_bytes(g->precision);
+  CUDA_TRY(cudaMemsetAsync(g->K, 0, ne, st));  // Step 2
+  CUDA_TRY(cudaMemsetAsync(g->G, 0, ne, st));
+  CUDA_TRY(cudaMemsetAsync(g->acc, 0, 4 * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(g->cnt, 0, kCntWords * sizeof(unsigned long long), st));
+  const unsigned long long npix0 = 12ULL << (2 * p->level0);
+  const unsigned long long n_roots = npix0 * (unsigned long long)g->src.size();
+  LAUNCH_TRY(launch_trace_init(g->ts.ctl, n_roots, st));
+  if (n_roots == 0) {
+    g->traced = false;
+    return RT_OK;
+  }
+  TraceArgs A;
+  memset(&A, 0, sizeof A);
+  A.inst = g->inst_dev;
+  A.ninst = 1;
+  A.src = g->src_dev;
+  A.nsrc = (int)g->src.size();
+  A.level0 = p->level0;
+  A.max_level = p->max_level;
+  A.npix0 = (uint32_t)npix0;
+  A.n_roots = n_roots;
+  for (int l = 0; l < kLevels; ++l) {
+    // Eq. "split": Phi = N_pix dx^2 / (4 pi R^2) < Phi_c  <=>  R > R_split(l)
+    A.rsplit[l] = sqrt((12.0 * ldexp(1.0, 2 * l)) / (4.0 * M_PI * p->phi_c));
+    A.rsplit32[l] = (float)A.rsplit[l];
+  }
+  A.tau_term = -log(p->f_term);
+  A.tau_term32 = (float)A.tau_term;
+  A.queue = g->ts.queue;
+  A.cap = g->ts.cap;
+  A.ctl = g->ts.ctl;
+  A.timeout_ns = (long long)((p->timeout_s > 0 ? p->timeout_s : 2.0) * 1e9);
+  A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 4;
+  A.max_steps = 2 * (g->nx + g->ny + g->nz) + 16;
+  const int block = p->block_threads > 0 ? p->block_threads : 256;
+  int per_sm = 0;
+  CUDA_TRY(trace_occupancy(g->precision, block, &per_sm));
+  if (per_sm < 1) per_sm = 1;
+  CUDA_TRY(cudaEventRecord(g->ev0, st));
+  LAUNCH_TRY(launch_trace(g->precision, A, per_sm * g->ctx->num_sms, block, st));
+  CUDA_TRY(cudaEventRecord(g->ev1, st));
+  g->traced = true;
+  return RT_OK;
+}
+
+static int read_budget(rt_grid* g, rt_budget* out) {
+  double* hacc = (double*)g->host_rb;
+  unsigned long long* hcnt = (unsigned long long*)((char*)g->host_rb + 64);
+  unsigned long long* hctl = (unsigned long long*)((char*)g->host_rb + 64 + 8 * kCntWords);
+  cudaStream_t st = g->stream;
+  CUDA_TRY(cudaMemcpyAsync(hacc, g->acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hcnt, g->cnt, kCntWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hctl, g->ts.ctl, CTL_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  memset(out, 0, sizeof *out);
+  out->emitted = hacc[0];
+  out->absorbed = hacc[1];
+  out->escaped = hacc[2];
+  for (int l = 0; l < kLevels; ++l) {
+    out->counts[l] = hcnt[l];
+    out->hashes[l] = hcnt[kLevels + l];
+  }
+  out->segments = hcnt[kCntSegments];
+  out->fallbacks = hcnt[kCntFallbacks];
+  out->queue_pushed = hctl[CTL_TAIL];
+  out->status = (int)hctl[CTL_STATUS];
+  float ms = 0.f;
+  if (g->traced && cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) out->kernel_ms = ms;
+  else cudaGetLastError();
+  return RT_OK;
+}
+
+int rt_trace(rt_grid* g, const rt_trace_params* p, rt_budget* out) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_trace: grid is NULL");
+  int rc = check_params(p);
+  if (rc) return rc;
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  unsigned long long cap = (unsigned long long)p->queue_capacity;
+  const bool automatic = cap == 0;
+  if (automatic) {
+    cap = g->ts.cap;
+    if (cap == 0) {
+      cap = (unsigned long long)g->ncell * 4ULL;
+      if (cap < (1ULL << 20)) cap = 1ULL << 20;
+      if (cap > (1ULL << 26)) cap = 1ULL << 26;
+    }
+  }
+  for (int attempt = 0;; ++attempt) {
+    if ((rc = ensure_queue(g, cap))) return rc;
+    if ((rc = enqueue_trace(g, p))) return rc;
+    if (!out) return RT_OK;
+    if ((rc = read_budget(g, out))) return rc;
+    if (out->status == RT_ERR_QUEUE_OVERFLOW && automatic && attempt < 6) {
+      unsigned long long need = out->queue_pushed + out->queue_pushed / 4 + 1024;
+      cap = need > 4 * cap ? need : 4 * cap;
+      if (cap > (1ULL << 31)) cap = 1ULL << 31;
+      continue;
+    }
+    if (out->status != RT_OK)
+      return fail(out->status, "rt_trace: device status %d (queue capacity %llu, pushed %llu)", out->status,
+                  (unsigned long long)g->ts.cap, (unsigned long long)out->queue_pushed);
+    return RT_OK;
+  }
+}
+
+int rt_get_budget(rt_grid* g, rt_budget* out) {
+  if (!g || !out) return fail(RT_ERR_INVALID_ARG, "rt_get_budget: NULL argument");
+  int rc = read_budget(g, out);
+  if (rc) return rc;
+  if (out->status != RT_OK) return fail(out->status, "rt_get_budget: device status %d", out->status);
+  return RT_OK;
+}
+
+int rt_chem_update(rt_grid* g, double dt_s, int nsub, double alpha_B) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_chem_update: grid is NULL");
+  if (!(dt_s >= 0) || !isfinite(dt_s)) return fail(RT_ERR_INVALID_ARG, "rt_chem_update: dt_s = %g", dt_s);
+  if (nsub < 1) return fail(RT_ERR_INVALID_ARG, "rt_chem_update: nsub = %d", nsub);
+  if (!(alpha_B >= 0) || !isfinite(alpha_B)) return fail(RT_ERR_INVALID_ARG, "rt_chem_update: alpha_B = %g", alpha_B);
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  const double h = dt_s / nsub;
+  LAUNCH_TRY(launch_chem(g->precision, g->ncell, g->nH, g->xHI, g->xHII, g->K, g->nhi, h, nsub, alpha_B, g->stream));
+  return RT_OK;
+}
+
+int rt_set_state(rt_grid* g, const double* n_H, const double* x_HI, const double* x_HII, int mem_kind) {
+  if (!g || !x_HI) return fail(RT_ERR_INVALID_ARG, "rt_set_state: grid and x_HI are required");
+  if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE) return fail(RT_ERR_INVALID_ARG, "rt_set_state: mem_kind %d", mem_kind);
+  const long long ncell = g->ncell;
+  if (mem_kind == RT_MEM_HOST) {
+    for (long long c = 0; c < ncell; ++c) {
+      if (n_H && (!(n_H[c] >= 0) || !isfinite(n_H[c]))) return fail(RT_ERR_INVALID_ARG, "rt_set_state: n_H[%lld] = %g", c, n_H[c]);
+      if (!(x_HI[c] >= 0 && x_HI[c] <= 1)) return fail(RT_ERR_INVALID_ARG, "rt_set_state: x_HI[%lld] = %g", c, x_HI[c]);
+    }
+  }
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  const size_t n8 = (size_t)ncell * 8;
+  int rc;
+  cudaStream_t st = g->stream;
+  if (n_H && (rc = upload(g->nH, n_H, n8, mem_kind, st))) return rc;
+  if ((rc = upload(g->xHI, x_HI, n8, mem_kind, st))) return rc;
+  if (x_HII) {
+    if ((rc = upload(g->xHII, x_HII, n8, mem_kind, st))) return rc;
+  } else {
+    LAUNCH_TRY(launch_complement(ncell, g->xHI, g->xHII, st));
+  }
+  LAUNCH_TRY(launch_refresh(g->precision, ncell, g->nH, g->xHI, g->nhi, st));
+  if (mem_kind == RT_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+  return RT_OK;
+}
+
+static int copy_field(rt_grid* g, const void* src, int src_dtype, void* dst, int dtype, int mem_kind) {
+  if (!dst) return RT_OK;
+  const long long n = g->ncell;
+  const size_t eb = dtype == RT_DTYPE_F64 ? 8 : 4;
+  cudaStream_t st = g->stream;
+  if (mem_kind == RT_MEM_DEVICE) {
+    LAUNCH_TRY(launch_convert(n, src, src_dtype, dst, dtype, st));
+    return RT_OK;
+  }
+  void* tmp = nullptr;
+  CUDA_TRY(cudaMallocAsync(&tmp, (size_t)n * eb, st));
+  cudaError_t e = launch_convert(n, src, src_dtype, tmp, dtype, st);
+  if (e == cudaSuccess) {
+    g_launches.fetch_add(1);
+    e = cudaMemcpyAsync(dst, tmp, (size_t)n * eb, cudaMemcpyDeviceToHost, st);
+  }
+  cudaFreeAsync(tmp, st);
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, "copy_field: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+int rt_get_rates(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_get_rates: grid is NULL");
+  if (dtype != RT_DTYPE_F64 && dtype != RT_DTYPE_F32) return fail(RT_ERR_INVALID_ARG, "rt_get_rates: dtype %d", dtype);
+  if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE) return fail(RT_ERR_INVALID_ARG, "rt_get_rates: mem_kind %d", mem_kind);
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  const int kd = g->precision == RT_FP64 ? RT_DTYPE_F64 : RT_DTYPE_F32;
+  int rc;
+  if ((rc = copy_field(g, g->K, kd, kph, dtype, mem_kind))) return rc;
+  if ((rc = copy_field(g, g->G, kd, gamma, dtype, mem_kind))) return rc;
+  if ((rc = copy_field(g, g->xHI, RT_DTYPE_F64, x_HI, dtype, mem_kind))) return rc;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return RT_OK;
+}
+
+int rt_get_ionised(rt_grid* g, void* x_HII, int dtype, int mem_kind) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_get_ionised: grid is NULL");
+  if (dtype != RT_DTYPE_F64 && dtype != RT_DTYPE_F32) return fail(RT_ERR_INVALID_ARG, "rt_get_ionised: dtype %d", dtype);
+  if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE) return fail(RT_ERR_INVALID_ARG, "rt_get_ionised: mem_kind %d", mem_kind);
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  int rc = copy_field(g, g->xHII, RT_DTYPE_F64, x_HII, dtype, mem_kind);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return RT_OK;
+}
+
+int rt_synchronize(rt_grid* g) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_synchronize: grid is NULL");
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// chem.cu -- per-cell kernels around the trace: the hydrogen-only ionisation
+// update (Eq. "dndt", Step 6 of Sec. 3.1), the absorber-density refresh
+// n_HI = n_H x_HI, and conversion of the rates for the caller.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt_internal.cuh"
+
+namespace rtg {
+
+// Backward Euler on dx/dt = alpha_B n_H (1 - x)^2 - k x, x = x_HI,
+// z = x_HII, over nsub substeps h with k frozen.  With a = h alpha_B n_H and
+// b = 1 + h k the implicit step solves a x'^2 - (2a + b) x' + (a + x) = 0;
+// its physical root, written without cancellation, is
+//   x' = 2(a + x) / (2a + b + sqrt(D)),  z' = 2(z + hk) / (b + sqrt(D)),
+//   D = b^2 + 4a(z + hk),
+// and the smaller of x', z' is kept with the other as its complement, so both
+// fractions keep their relative accuracy as either tends to 0.  All FP64,
+// explicitly rounded (no FMA contraction).
+template <typename KT, typename NT>
+__global__ void chem_kernel(long long ncell, const double* __restrict__ nH, double* __restrict__ xHI,
+                            double* __restrict__ xHII, const KT* __restrict__ K, NT* __restrict__ nhi,
+                            double h, int nsub, double alpha) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    double x = xHI[c], z = xHII[c];
+    const double n = nH[c];
+    const double a = __dmul_rn(__dmul_rn(h, alpha), n);
+    const double hk = __dmul_rn(h, (double)K[c]);
+    const double b = __dadd_rn(1.0, hk);
+    for (int i = 0; i < nsub; ++i) {
+      const double D = __dadd_rn(__dmul_rn(b, b), __dmul_rn(__dmul_rn(4.0, a), __dadd_rn(z, hk)));
+      const double sq = __dsqrt_rn(D);
+      const double xn = __ddiv_rn(__dmul_rn(2.0, __dadd_rn(a, x)), __dadd_rn(__dadd_rn(__dmul_rn(2.0, a), b), sq));
+      const double zn = __ddiv_rn(__dmul_rn(2.0, __dadd_rn(z, hk)), __dadd_rn(b, sq));
+      if (xn <= zn) { x = xn; z = __dsub_rn(1.0, xn); }
+      else { z = zn; x = __dsub_rn(1.0, zn); }
+    }
+    xHI[c] = x;
+    xHII[c] = z;
+    nhi[c] = (NT)__dmul_rn(n, x);
+  }
+}
+
+template <typename NT>
+__global__ void refresh_nhi_kernel(long long ncell, const double* __restrict__ nH,
+                                   const double* __restrict__ xHI, NT* __restrict__ nhi) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x)
+    nhi[c] = (NT)__dmul_rn(nH[c], xHI[c]);
+}
+
+template <typename ST, typename DT>
+__global__ void convert_kernel(long long n, const ST* __restrict__ src, DT* __restrict__ dst) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x)
+    dst[c] = (DT)src[c];
+}
+
+__global__ void complement_kernel(long long n, const double* __restrict__ x, double* __restrict__ out) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x)
+    out[c] = __dsub_rn(1.0, x[c]);
+}
+
+static int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_chem(int precision, long long ncell, const double* nH, double* xHI, double* xHII,
+                        const void* K, void* nhi, double h, int nsub, double alpha, cudaStream_t st) {
+  const int block = 256, grid = grid_for(ncell, block);
+  if (precision == RT_FP64)
+    chem_kernel<double, double><<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const double*)K,
+                                                         (double*)nhi, h, nsub, alpha);
+  else
+    chem_kernel<float, float><<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const float*)K,
+                                                       (float*)nhi, h, nsub, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refresh(int precision, long long ncell, const double* nH, const double* xHI,
+                           void* nhi, cudaStream_t st) {
+  const int block = 256, grid = grid_for(ncell, block);
+  if (precision == RT_FP64)
+    refresh_nhi_kernel<double><<<grid, block, 0, st>>>(ncell, nH, xHI, (double*)nhi);
+  else
+    refresh_nhi_kernel<float><<<grid, block, 0, st>>>(ncell, nH, xHI, (float*)nhi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_complement(long long n, const double* x, double* out, cudaStream_t st) {
+  const int block = 256, grid = grid_for(n, block);
+  complement_kernel<<<grid, block, 0, st>>>(n, x, out);
+  return cudaGetLastError();
+}
+
+// src_dtype / dst_dtype: RT_DTYPE_F64 or RT_DTYPE_F32
+cudaError_t launch_convert(long long n, const void* src, int src_dtype, void* dst, int dst_dtype,
+                           cudaStream_t st) {
+  const int block = 256, grid = grid_for(n, block);
+  if (src_dtype == RT_DTYPE_F64 && dst_dtype == RT_DTYPE_F64)
+    convert_kernel<double, double><<<grid, block, 0, st>>>(n, (const double*)src, (double*)dst);
+  else if (src_dtype == RT_DTYPE_F64 && dst_dtype == RT_DTYPE_F32)
+    convert_kernel<double, float><<<grid, block, 0, st>>>(n, (const double*)src, (float*)dst);
+  else if (src_dtype == RT_DTYPE_F32 && dst_dtype == RT_DTYPE_F64)
+    convert_kernel<float, double><<<grid, block, 0, st>>>(n, (const float*)src, (double*)dst);
+  else
+    convert_kernel<float, float><<<grid, block, 0, st>>>(n, (const float*)src, (float*)dst);
+  return cudaGetLastError();
+}
+
+}  // namespace rtg

@@ -1,0 +1,138 @@
+// rt_internal.cuh -- device-side data layout and helpers shared by the
+// library's kernels (trace.cu, chem.cu) and its host code (api.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt.h"
+
+namespace rtg {
+
+constexpr int kLevels = RT_MAX_LEVEL + 1;
+constexpr double kEvErg = 1.602176634e-12;  // erg per eV
+constexpr double kEHI = 13.6;               // hydrogen threshold, eV (Sec. 2.2)
+
+// Control words of one trace (64-bit each), in device memory.
+enum CtlWord {
+  CTL_HEAD = 0,         // next ticket to hand out
+  CTL_TAIL = 1,         // queue slots reserved by producers
+  CTL_OUTSTANDING = 2,  // live packages (signed)
+  CTL_STATUS = 3,       // RT_OK or first device error (atomicCAS)
+  CTL_EPOCH = 4,        // tag of this trace's queue records
+  CTL_N = 8
+};
+
+// One point source, prepared on the host for the kernels.  P of a package is
+// carried in units of the root package's photon rate (root P = 1 exactly),
+// so every per-source constant below folds in unit = ndot / npix0.
+struct SourceDev {
+  double s[3];   // position in cell units (pos_cm / dx)
+  double sdx;    // sigma * dx: optical depth per unit n_HI per cell length
+  double w;      // unit * sigma / dx^2: k_ph per unit P per cell length (phi = 1)
+  double rw;     // unit / dx^3: k_ph per unit P per unit n_HI (residual absorption)
+  double heat;   // (E_ph - 13.6 eV) in erg
+  double unit;   // photons/s carried by P = 1
+  float s32[3];
+  float sdx32;
+  float w32;
+  float rw32;
+  float heat32;
+  float ds32[3];  // |s32 - s| per axis (0 for positions exact in FP32)
+  int inst;       // owning grid slot
+  int local;      // index of the source within its grid (checksum)
+  int exact32;    // s32 == s and plane offsets are exact in FP32
+  int pad;
+};
+
+// One grid (instance) as the trace kernel sees it.
+struct InstDev {
+  int nx, ny, nz, pad;
+  const void* nhi;          // absorber density n_HI (double or float), x fastest
+  const double* nH;         // hydrogen density, FP64 (decisions re-taken in FP64)
+  const double* xHI;        // neutral fraction, FP64
+  void* K;                  // k_ph accumulator (double or float)
+  void* G;                  // Gamma accumulator (double or float)
+  double* acc;              // [0] emitted [1] absorbed [2] escaped (photons/s)
+  unsigned long long* cnt;  // [0,15) counts, [15,30) hashes, [30] segments, [31] fallbacks
+};
+constexpr int kCntSegments = 2 * kLevels;
+constexpr int kCntFallbacks = 2 * kLevels + 1;
+constexpr int kCntWords = 2 * kLevels + 2;
+
+// Queue records.  The tag word is written last with release semantics and
+// equals the trace's epoch once the record is complete.
+struct __align__(16) Rec64 {
+  double r, P, tau;
+  uint32_t src, pix, level, tag;
+};
+struct __align__(16) Rec32 {
+  float r, P, tau;
+  uint32_t src;
+  uint32_t pix, level;
+  float tau_err;  // bound on |tau (FP32) - tau (FP64 path)|
+  uint32_t tag;
+};
+static_assert(sizeof(Rec64) == 48, "record layout");
+static_assert(sizeof(Rec32) == 32, "record layout");
+
+struct TraceArgs {
+  const InstDev* inst;
+  int ninst;
+  const SourceDev* src;
+  int nsrc;
+  int level0, max_level;
+  uint32_t npix0;
+  unsigned long long n_roots;
+  double rsplit[kLevels];
+  float rsplit32[kLevels];
+  double tau_term;
+  float tau_term32;
+  void* queue;
+  unsigned long long cap;
+  unsigned long long* ctl;
+  long long timeout_ns;
+  int segs_per_iter;
+  int max_steps;  // bound on segments of one package (guards the DDA loop)
+};
+
+// 64-bit finaliser used for the created-package checksum (documented in rt.h).
+__host__ __device__ __forceinline__ uint64_t pkg_hash(uint32_t src, uint32_t level, uint64_t pix) {
+  uint64_t x = ((uint64_t)src << 40) ^ ((uint64_t)level << 34) ^ pix;
+  x ^= x >> 31;
+  x *= 0x7fb5d329728ea185ULL;
+  x ^= x >> 27;
+  x *= 0x81dadef4bc2dd44dULL;
+  x ^= x >> 33;
+  return x;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ long long ld_acquire_s64(const unsigned long long* p) {
+  long long v;
+  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void set_status(unsigned long long* ctl, int code) {
+  atomicCAS(&ctl[CTL_STATUS], 0ULL, (unsigned long long)code);
+}
+#endif
+
+}  // namespace rtg

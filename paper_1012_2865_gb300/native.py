@@ -1,0 +1,283 @@
+"""ctypes binding of the C ABI in include/rt.h (argument marshalling only).
+
+Every computation happens in librt_gb300.so's CUDA kernels.  Loading fails
+loudly when the library has not been built; there is no fallback.
+
+Buffers may be numpy arrays (host memory) or torch CUDA tensors (device
+memory); torch is imported only when a tensor is passed.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from .build import LIB, ROOT
+
+RT_OK = 0
+RT_ERR_INVALID_ARG = 1
+RT_ERR_OOM = 2
+RT_ERR_CUDA = 3
+RT_ERR_QUEUE_OVERFLOW = 4
+RT_ERR_LEVEL_OVERFLOW = 5
+RT_ERR_TIMEOUT = 6
+RT_ERR_STATE = 7
+RT_FP64 = 0
+RT_FP32_MIXED = 1
+RT_MEM_HOST = 0
+RT_MEM_DEVICE = 1
+RT_DTYPE_F64 = 0
+RT_DTYPE_F32 = 1
+RT_MAX_LEVEL = 14
+NLEV = RT_MAX_LEVEL + 1
+
+PRECISIONS = {"fp64": RT_FP64, "fp32_mixed": RT_FP32_MIXED, "mixed": RT_FP32_MIXED}
+
+
+class RtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rt error {code}: {msg}")
+        self.code = code
+
+
+class rt_grid_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("box_len_cm", ctypes.c_double), ("precision", ctypes.c_int),
+                ("mem_kind", ctypes.c_int), ("n_H", ctypes.c_void_p), ("x_HI", ctypes.c_void_p),
+                ("x_HII", ctypes.c_void_p)]
+
+
+class rt_trace_params(ctypes.Structure):
+    _fields_ = [("level0", ctypes.c_int), ("phi_c", ctypes.c_double), ("f_term", ctypes.c_double),
+                ("max_level", ctypes.c_int), ("queue_capacity", ctypes.c_int64),
+                ("timeout_s", ctypes.c_double), ("block_threads", ctypes.c_int),
+                ("segs_per_iter", ctypes.c_int)]
+
+
+class rt_budget(ctypes.Structure):
+    _fields_ = [("emitted", ctypes.c_double), ("absorbed", ctypes.c_double),
+                ("escaped", ctypes.c_double), ("counts", ctypes.c_uint64 * NLEV),
+                ("hashes", ctypes.c_uint64 * NLEV), ("segments", ctypes.c_uint64),
+                ("fallbacks", ctypes.c_uint64), ("queue_pushed", ctypes.c_uint64),
+                ("status", ctypes.c_int), ("kernel_ms", ctypes.c_float)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_1012_2865_gb300.build.build()"
+                               " (the CUDA path has no fallback)")
+        L = ctypes.CDLL(LIB)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        sig = {
+            "rt_ctx_create": ([i, ctypes.POINTER(vp)], i),
+            "rt_ctx_destroy": ([vp], i),
+            "rt_create_grid": ([vp, ctypes.POINTER(rt_grid_desc), vp, ctypes.POINTER(vp)], i),
+            "rt_grid_destroy": ([vp], i),
+            "rt_add_sources": ([vp, i, vp, vp, vp, vp], i),
+            "rt_clear_sources": ([vp], i),
+            "rt_trace": ([vp, ctypes.POINTER(rt_trace_params), ctypes.POINTER(rt_budget)], i),
+            "rt_get_budget": ([vp, ctypes.POINTER(rt_budget)], i),
+            "rt_chem_update": ([vp, d, i, d], i),
+            "rt_get_rates": ([vp, vp, vp, vp, i, i], i),
+            "rt_set_state": ([vp, vp, vp, vp, i], i),
+            "rt_get_ionised": ([vp, vp, i, i], i),
+            "rt_synchronize": ([vp], i),
+            "rt_kernel_launches": ([], ctypes.c_uint64),
+            "rt_get_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def header_symbols() -> list:
+    """Function names declared in include/rt.h."""
+    with open(os.path.join(ROOT, "include", "rt.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(rt_[a-z_]+)\s*\(",
+                                 text, flags=re.M)))
+
+
+def check(code):
+    if code != RT_OK:
+        raise RtError(code, lib().rt_get_last_error().decode(errors="replace"))
+
+
+def _buf(a, dtype=np.float64):
+    """(pointer, mem_kind, keepalive) for a numpy array or a torch tensor."""
+    if a is None:
+        return None, RT_MEM_HOST, None
+    if type(a).__module__.startswith("torch"):
+        if a.is_cuda:
+            assert a.is_contiguous()
+            return a.data_ptr(), RT_MEM_DEVICE, a
+        a = a.numpy()
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, RT_MEM_HOST, arr
+
+
+def rt_ctx_create(device: int = 0):
+    h = ctypes.c_void_p()
+    check(lib().rt_ctx_create(int(device), ctypes.byref(h)))
+    return h
+
+
+def rt_ctx_destroy(ctx):
+    check(lib().rt_ctx_destroy(ctx))
+
+
+def rt_create_grid(ctx, dims, box_len_cm, n_H, x_HI, x_HII=None, precision="fp64", stream=None):
+    nx, ny, nz = (int(v) for v in dims)
+    pn, kn, kn_ = _buf(n_H)
+    px, kx, kx_ = _buf(x_HI)
+    pz, kz, kz_ = _buf(x_HII)
+    if len({k for k, p in ((kn, pn), (kx, px), (kz, pz)) if p is not None}) > 1:
+        raise ValueError("n_H, x_HI, x_HII must all live on the host or all on the device")
+    d = rt_grid_desc(nx, ny, nz, float(box_len_cm), PRECISIONS[precision] if isinstance(precision, str)
+                     else int(precision), kn, pn, px, pz)
+    h = ctypes.c_void_p()
+    check(lib().rt_create_grid(ctx, ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+    return h
+
+
+def rt_grid_destroy(grid):
+    check(lib().rt_grid_destroy(grid))
+
+
+def rt_add_sources(grid, pos_cm, ndot, e_ph_eV, sigma_cm2):
+    pos = np.ascontiguousarray(pos_cm, dtype=np.float64).reshape(-1)
+    nd = np.ascontiguousarray(ndot, dtype=np.float64).reshape(-1)
+    e = np.ascontiguousarray(e_ph_eV, dtype=np.float64).reshape(-1)
+    s = np.ascontiguousarray(sigma_cm2, dtype=np.float64).reshape(-1)
+    n = nd.size
+    if pos.size != 3 * n or e.size != n or s.size != n:
+        raise ValueError("source arrays disagree in length")
+    check(lib().rt_add_sources(grid, n, pos.ctypes.data, nd.ctypes.data, e.ctypes.data, s.ctypes.data))
+
+
+def rt_clear_sources(grid):
+    check(lib().rt_clear_sources(grid))
+
+
+def trace_params(level0=1, phi_c=5.1, f_term=1e-10, max_level=RT_MAX_LEVEL, queue_capacity=0,
+                 timeout_s=2.0, block_threads=0, segs_per_iter=0) -> rt_trace_params:
+    return rt_trace_params(int(level0), float(phi_c), float(f_term), int(max_level),
+                           int(queue_capacity), float(timeout_s), int(block_threads),
+                           int(segs_per_iter))
+
+
+def budget_dict(b: rt_budget) -> dict:
+    return dict(emitted=b.emitted, absorbed=b.absorbed, escaped=b.escaped,
+                counts=np.array(b.counts[:], dtype=np.uint64),
+                hashes=np.array(b.hashes[:], dtype=np.uint64), segments=int(b.segments),
+                fallbacks=int(b.fallbacks), queue_pushed=int(b.queue_pushed), status=int(b.status),
+                kernel_ms=float(b.kernel_ms))
+
+
+def rt_trace(grid, params: rt_trace_params, sync: bool = True):
+    if sync:
+        b = rt_budget()
+        check(lib().rt_trace(grid, ctypes.byref(params), ctypes.byref(b)))
+        return budget_dict(b)
+    check(lib().rt_trace(grid, ctypes.byref(params), None))
+    return None
+
+
+def rt_get_budget(grid) -> dict:
+    b = rt_budget()
+    check(lib().rt_get_budget(grid, ctypes.byref(b)))
+    return budget_dict(b)
+
+
+def rt_set_state(grid, x_HI, x_HII=None, n_H=None):
+    px, kx, kx_ = _buf(x_HI)
+    pz, kz, kz_ = _buf(x_HII)
+    pn, kn, kn_ = _buf(n_H)
+    check(lib().rt_set_state(grid, pn, px, pz, kx))
+
+
+def rt_chem_update(grid, dt_s, nsub, alpha_B):
+    check(lib().rt_chem_update(grid, float(dt_s), int(nsub), float(alpha_B)))
+
+
+def _out(n, dtype, where):
+    if where == "device":
+        import torch
+        return torch.empty(n, dtype=torch.float64 if dtype == RT_DTYPE_F64 else torch.float32,
+                           device="cuda")
+    return np.empty(n, dtype=np.float64 if dtype == RT_DTYPE_F64 else np.float32)
+
+
+def rt_get_rates(grid, ncell, dtype=RT_DTYPE_F64, where="host", want=("kph", "gamma", "x_HI")):
+    outs = {k: _out(ncell, dtype, where) if k in want else None for k in ("kph", "gamma", "x_HI")}
+    mk = RT_MEM_DEVICE if where == "device" else RT_MEM_HOST
+    ptr = {k: (None if v is None else (v.data_ptr() if where == "device" else v.ctypes.data))
+           for k, v in outs.items()}
+    check(lib().rt_get_rates(grid, ptr["kph"], ptr["gamma"], ptr["x_HI"], int(dtype), mk))
+    return outs
+
+
+def rt_get_ionised(grid, ncell, dtype=RT_DTYPE_F64, where="host"):
+    out = _out(ncell, dtype, where)
+    p = out.data_ptr() if where == "device" else out.ctypes.data
+    check(lib().rt_get_ionised(grid, p, int(dtype), RT_MEM_DEVICE if where == "device" else RT_MEM_HOST))
+    return out
+
+
+def rt_synchronize(grid):
+    check(lib().rt_synchronize(grid))
+
+
+def rt_kernel_launches() -> int:
+    return int(lib().rt_kernel_launches())
+
+
+def rt_get_last_error() -> str:
+    return lib().rt_get_last_error().decode(errors="replace")
+
+
+class Grid:
+    """Convenience owner of one grid handle (marshalling only)."""
+
+    def __init__(self, ctx, g: dict, precision="fp64", stream=None):
+        self.dims = tuple(g["dims"])
+        self.ncell = int(np.prod(self.dims))
+        self.h = rt_create_grid(ctx, self.dims, g["box_len_cm"], g["n_H"], g["x_HI"],
+                                g.get("x_HII"), precision, stream)
+        if len(g["ndot"]):
+            rt_add_sources(self.h, g["pos_cm"], g["ndot"], g["e_ph_eV"], g["sigma_cm2"])
+
+    def trace(self, sync=True, **kw):
+        return rt_trace(self.h, trace_params(**kw), sync=sync)
+
+    def chem(self, dt_s, nsub=10, alpha_B=2.59e-13):
+        rt_chem_update(self.h, dt_s, nsub, alpha_B)
+
+    def rates(self, dtype=RT_DTYPE_F64, where="host"):
+        return rt_get_rates(self.h, self.ncell, dtype, where)
+
+    def x_HII(self):
+        return rt_get_ionised(self.h, self.ncell)
+
+    def close(self):
+        if self.h:
+            rt_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -85,6 +85,30 @@ def stromgren(N: int = 128, box_kpc: float = 6.6, n_H: float = 1e-3, ndot: float
                  alpha_B=ALPHA_B)
 
 
+def stromgren_snapshot(N: int = 128, t_myr: float = 500.0, width_cells: float = 3.0,
+                       x_in: float = 1e-3) -> dict:
+    """Test 1 medium with an ionised octant sphere at the analytic I-front radius.
+
+    x_HI(r) = x_in + (1 - x_in) / (1 + exp(-(r - r_IF) / w)), r the distance of a
+    cell centre from the corner source, r_IF = R_s [1 - exp(-t/t_rec)]^(1/3)
+    (Eqs. "Rstr", "rstr"), w = width_cells * N / 128 cells.  A seeded-free,
+    deterministic stand-in for the coupled evolution's state at time t.
+    """
+    g = stromgren(N)
+    dx = g["box_len_cm"] / N
+    rs = (3 * 5e48 / (4 * np.pi * ALPHA_B * 1e-3 ** 2)) ** (1 / 3)
+    trec = 1.0 / (ALPHA_B * 1e-3)
+    r_if = rs * (1 - np.exp(-t_myr * MYR_S / trec)) ** (1 / 3) / dx
+    i = np.arange(N) + 0.5
+    r = np.sqrt(i[None, None, :] ** 2 + i[None, :, None] ** 2 + i[:, None, None] ** 2).reshape(-1)
+    w = width_cells * N / 128.0
+    x = x_in + (1.0 - x_in) / (1.0 + np.exp(-(r - r_if) / w))
+    g["x_HI"] = x
+    g["x_HII"] = (1.0 - x_in) - (1.0 - x_in) / (1.0 + np.exp(-(r - r_if) / w))
+    g["r_if_cells"] = r_if
+    return g
+
+
 def lognormal_density(N: int, sigma_ln: float = 1.0, mean: float = 1e-2, seed: int = BASE_SEED,
                       dims=None) -> np.ndarray:
     """Log-normal medium from a P(k) ~ k^-3 Gaussian field, flattened x-fastest."""

@@ -1,0 +1,54 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol rt.h declares.
+
+No compute call is made here (no GPU on the CPU runners)."""
+import ctypes
+
+from paper_1012_2865_gb300 import build, native
+
+
+def test_library_builds_and_exports_header_symbols():
+    path = build.build()
+    L = ctypes.CDLL(path)
+    syms = native.header_symbols()
+    assert len(syms) >= 14
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert not missing, missing
+    for core in ("rt_create_grid", "rt_add_sources", "rt_trace", "rt_chem_update", "rt_get_rates"):
+        assert core in syms
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of the rt.h structs have the C compiler's sizes and offsets."""
+    import os
+    import subprocess
+    src = tmp_path / "layout.c"
+    src.write_text(r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "rt.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(rt_grid_desc), offsetof(rt_grid_desc, box_len_cm),
+         offsetof(rt_grid_desc, n_H), offsetof(rt_grid_desc, x_HII));
+  printf("%zu %zu %zu %zu\n", sizeof(rt_trace_params), offsetof(rt_trace_params, phi_c),
+         offsetof(rt_trace_params, queue_capacity), offsetof(rt_trace_params, segs_per_iter));
+  printf("%zu %zu %zu %zu\n", sizeof(rt_budget), offsetof(rt_budget, counts),
+         offsetof(rt_budget, segments), offsetof(rt_budget, status));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(build.ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [list(map(int, l.split())) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                             check=True).stdout.strip().splitlines()]
+    D, T, B = native.rt_grid_desc, native.rt_trace_params, native.rt_budget
+    assert got[0] == [ctypes.sizeof(D), D.box_len_cm.offset, D.n_H.offset, D.x_HII.offset]
+    assert got[1] == [ctypes.sizeof(T), T.phi_c.offset, T.queue_capacity.offset, T.segs_per_iter.offset]
+    assert got[2] == [ctypes.sizeof(B), B.counts.offset, B.segments.offset, B.status.offset]
+
+
+def test_error_message_without_gpu_is_reported_not_raised_from_c():
+    L = native.lib()
+    h = ctypes.c_void_p()
+    rc = L.rt_ctx_create(-1, ctypes.byref(h))
+    assert rc != 0
+    assert len(L.rt_get_last_error()) > 0
