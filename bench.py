@@ -120,7 +120,7 @@ def run_native(args, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = native.rt_ctx_create(local)
-    g = synth.stromgren_snapshot(128)
+    g = synth.stromgren_snapshot(args.grid)
     params = dict(synth.DEFAULT_PARAMS)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
@@ -204,7 +204,7 @@ def run_native(args, rank, world, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
     value = r["segments"] * world / total_s
-    ee = e2e(head)
+    ee = e2e(head) if not args.no_e2e else dict(value=None, h2d=0, d2h=0)
     peaks, peak_kind = _peaks()
     ebytes = 8 if head == "fp64" else 4
     rec = 48 if head == "fp64" else 32
@@ -216,8 +216,9 @@ def run_native(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if head == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": head, "segments_per_step": r["seg_per_step"],
+        "dtype": "f64" if head == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.grid == 128 else WORKLOAD.replace("128^3", f"{args.grid}^3"),
+                   "precision": head, "segments_per_step": r["seg_per_step"],
                    "queue_records_per_step": r["pushed"], "l2": "flushed (512 MB write) between steps",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0),
@@ -293,9 +294,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precisions", default="fp64")
+    ap.add_argument("--precisions", default="fp32_mixed,fp64")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grid", type=int, default=128, help="cells per side (128 = the benchmark workload)")
     args = ap.parse_args()
     args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
     rank, world, local = _dist()

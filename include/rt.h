@@ -154,6 +154,12 @@ int rt_get_rates(rt_grid* grid, void* kph, void* gamma, void* x_HI, int dtype, i
 /* Copy x_HII likewise. */
 int rt_get_ionised(rt_grid* grid, void* x_HII, int dtype, int mem_kind);
 
+/* Self-check of the FP32-mixed path's direction bound: the largest
+ * |n32_i - n64_i| over all pixel centres of `level` (HEALPix, Step 3a),
+ * computed on the device, and the bound the mixed path's decision bands
+ * assume (*bound may be NULL).  Synchronous. */
+int rt_selfcheck_directions(rt_ctx* ctx, int level, double* max_abs_err, double* bound);
+
 /* Wait for all work enqueued on the grid's stream. */
 int rt_synchronize(rt_grid* grid);
 

@@ -7,10 +7,12 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "rt.h"
+#include "healpix.cuh"
 #include "rt_internal.cuh"
 
 namespace rtg {
@@ -24,6 +26,8 @@ cudaError_t launch_refresh(int precision, long long ncell, const double* nH, con
 cudaError_t launch_convert(long long n, const void* src, int src_dtype, void* dst, int dst_dtype,
                            cudaStream_t st);
 cudaError_t launch_complement(long long n, const double* x, double* out, cudaStream_t st);
+cudaError_t launch_direction_check(int level, unsigned long long* out, cudaStream_t st);
+cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st);
 }  // namespace rtg
 
 using namespace rtg;
@@ -59,7 +63,36 @@ static int fail(int code, const char* fmt, ...) {
 struct rt_ctx {
   int device;
   int num_sms;
+  // pixel directions as FP32 pairs (mixed path), levels 0..dir_levels
+  std::mutex dir_mu;
+  float4* dir_tab = nullptr;
+  int dir_levels = -1;
+  ~rt_ctx() {
+    if (dir_tab) cudaFree(dir_tab);
+  }
 };
+
+constexpr int kDirTableMaxLevel = 9;  // 4.2M pixels, 134 MB
+
+// Make sure the direction table holds levels 0..want (want <= 9).
+static int ensure_dir_table(rt_ctx* c, int want) {
+  std::lock_guard<std::mutex> lk(c->dir_mu);
+  if (want <= c->dir_levels) return RT_OK;
+  const size_t entries = (size_t)4 * (((size_t)1 << (2 * (want + 1))) - 1);
+  float4* t = nullptr;
+  CUDA_TRY(cudaMalloc(&t, entries * 2 * sizeof(float4)));
+  for (int l = 0; l <= want; ++l) {
+    cudaError_t e = launch_direction_table(l, t, 0);
+    if (e != cudaSuccess) { cudaFree(t); return fail(RT_ERR_CUDA, "direction table: %s", cudaGetErrorString(e)); }
+    g_launches.fetch_add(1);
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { cudaFree(t); return fail(RT_ERR_CUDA, "direction table: %s", cudaGetErrorString(e)); }
+  if (c->dir_tab) cudaFree(c->dir_tab);
+  c->dir_tab = t;
+  c->dir_levels = want;
+  return RT_OK;
+}
 
 // Per-trace device resources: queue, control words, descriptors.
 struct TraceState {
@@ -264,7 +297,11 @@ int rt_clear_sources(rt_grid* g) {
   return RT_OK;
 }
 
-static bool exact_in_f32(double v) { return (double)(float)v == v && fabs(v) < 4194304.0; }
+// A source coordinate for which the FP32 walker may treat equal FP32 crossing
+// distances of a 45-degree ray as an exact tie: a multiple of 1/16 no larger
+// than 4096 cells, so every plane offset b - s is exact in FP32 and distinct
+// offsets stay at least 1/16 apart.
+static bool exact_in_f32(double v) { return v == ldexp(floor(ldexp(v, 4)), -4) && fabs(v) <= 4096.0; }
 
 // Build the per-source device table for a given initial level.
 static int prepare_sources(rt_grid* g, int level0) {
@@ -287,10 +324,12 @@ static int prepare_sources(rt_grid* g, int level0) {
     int exact = 1;
     for (int a = 0; a < 3; ++a) {
       S.s32[a] = (float)S.s[a];
-      S.ds32[a] = (float)fabs((double)S.s32[a] - S.s[a]);
+      S.slo32[a] = (float)(S.s[a] - (double)S.s32[a]);
+      const bool pair_exact = (double)S.s32[a] + (double)S.slo32[a] == S.s[a];
+      S.sabs32[a] = pair_exact ? 0.0f : (float)(ldexp(fabs(S.s[a]), -46));
       exact &= exact_in_f32(S.s[a]) ? 1 : 0;
     }
-    S.exact32 = exact;
+    S.exact32 = exact && g->nx <= 4096 && g->ny <= 4096 && g->nz <= 4096;
     S.sdx32 = (float)S.sdx;
     S.w32 = (float)S.w;
     S.rw32 = (float)S.rw;
@@ -371,6 +410,20 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p) {
     // Eq. "split": Phi = N_pix dx^2 / (4 pi R^2) < Phi_c  <=>  R > R_split(l)
     A.rsplit[l] = sqrt((12.0 * ldexp(1.0, 2 * l)) / (4.0 * M_PI * p->phi_c));
     A.rsplit32[l] = (float)A.rsplit[l];
+    A.rsplit32lo[l] = (float)(A.rsplit[l] - (double)A.rsplit32[l]);
+  }
+  A.dir_tab = nullptr;
+  A.dir_levels = -1;
+  if (g->precision == RT_FP32_MIXED) {
+    // deepest level a package can reach: R_split(l) >= box diagonal stops splitting
+    const double diag = sqrt((double)g->nx * g->nx + (double)g->ny * g->ny + (double)g->nz * g->nz);
+    int need = p->level0;
+    while (need < p->max_level && A.rsplit[need] < diag) ++need;
+    const int want = need < kDirTableMaxLevel ? need : kDirTableMaxLevel;
+    int rc2 = ensure_dir_table(g->ctx, want);
+    if (rc2) return rc2;
+    A.dir_tab = g->ctx->dir_tab;
+    A.dir_levels = g->ctx->dir_levels;
   }
   A.tau_term = -log(p->f_term);
   A.tau_term32 = (float)A.tau_term;
@@ -539,6 +592,26 @@ int rt_get_ionised(rt_grid* g, void* x_HII, int dtype, int mem_kind) {
   int rc = copy_field(g, g->xHII, RT_DTYPE_F64, x_HII, dtype, mem_kind);
   if (rc) return rc;
   CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return RT_OK;
+}
+
+int rt_selfcheck_directions(rt_ctx* ctx, int level, double* max_abs_err, double* bound) {
+  if (!ctx || !max_abs_err || level < 0 || level > RT_MAX_LEVEL)
+    return fail(RT_ERR_INVALID_ARG, "rt_selfcheck_directions: bad argument");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  unsigned long long* d = nullptr;
+  CUDA_TRY(cudaMalloc(&d, sizeof *d));
+  cudaError_t e = cudaMemset(d, 0, sizeof *d);
+  if (e == cudaSuccess) e = launch_direction_check(level, d, 0);
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_selfcheck_directions: %s", cudaGetErrorString(e));
+  g_launches.fetch_add(1);
+  double v;
+  memcpy(&v, &h, sizeof v);
+  *max_abs_err = v;
+  if (bound) *bound = (double)kDirErr32;
   return RT_OK;
 }
 

@@ -37,7 +37,8 @@ struct SourceDev {
   float w32;
   float rw32;
   float heat32;
-  float ds32[3];  // |s32 - s| per axis (0 for positions exact in FP32)
+  float slo32[3];   // s - s32 rounded to FP32: (s32, slo32) is the position as an FP32 pair
+  float sabs32[3];  // 2^-46 |s| for positions the pair does not hold exactly, else 0
   int inst;       // owning grid slot
   int local;      // index of the source within its grid (checksum)
   int exact32;    // s32 == s and plane offsets are exact in FP32
@@ -67,10 +68,10 @@ struct __align__(16) Rec64 {
 };
 struct __align__(16) Rec32 {
   float r, P, tau;
-  uint32_t src;
-  uint32_t pix, level;
-  float tau_err;  // bound on |tau (FP32) - tau (FP64 path)|
-  uint32_t tag;
+  float tau_err;  // bound on |tau (FP32) - tau (FP64 evaluation)|
+  uint32_t src, pix;
+  float r_lo;     // radius as the FP32 pair (r, r_lo)
+  uint32_t tag;   // (epoch << 4) | level
 };
 static_assert(sizeof(Rec64) == 48, "record layout");
 static_assert(sizeof(Rec32) == 32, "record layout");
@@ -84,7 +85,10 @@ struct TraceArgs {
   uint32_t npix0;
   unsigned long long n_roots;
   double rsplit[kLevels];
-  float rsplit32[kLevels];
+  float rsplit32[kLevels];    // R_split as the FP32 pair (rsplit32, rsplit32lo)
+  float rsplit32lo[kLevels];
+  const float4* dir_tab;      // pixel directions as FP32 pairs, levels 0..dir_levels
+  int dir_levels;             // -1: no table
   double tau_term;
   float tau_term32;
   void* queue;

@@ -150,9 +150,11 @@ struct Walk64 {
     __stcg(&q->level, level + 1);
     st_release_u32(&q->tag, epoch);
   }
-  __device__ __forceinline__ static void read_rec(const Rec* q, Rec& o) {
+  __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
+    if (ld_acquire_u32(&q->tag) != epoch) return false;
     o.r = __ldcg(&q->r); o.P = __ldcg(&q->P); o.tau = __ldcg(&q->tau);
     o.src = __ldcg(&q->src); o.pix = __ldcg(&q->pix); o.level = __ldcg(&q->level);
+    return true;
   }
   __device__ __forceinline__ void set_root(uint32_t gsrc, uint32_t lvl, uint32_t p) {
     src = gsrc; level = lvl; pix = p; r = 0.0; P = 1.0; tau = 0.0;
@@ -210,6 +212,359 @@ struct Walk64 {
 };
 
 // ---------------------------------------------------------------------------
+// FP64 re-evaluation helpers for the mixed walker.  They reproduce exactly
+// the arithmetic of the FP64 walker above.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_of64(double u, double n) { return Walk64::cell_of(u, n); }
+__device__ __forceinline__ double next_t64(int c, double s, double n) { return Walk64::next_t(c, s, n); }
+
+// Optical depth that the FP64 evaluation accumulates along the lineage of
+// package (level, pix) of source src up to and including its segment in cell
+// (tc0, tc1, tc2).  Follows the FP64 path from the root: the root pixel at
+// level0 is pix >> 2 (level - level0); at each split the lineage continues
+// with the child on the path to pix.  *ok is false if the lineage does not
+// reach that cell at that level (then the caller keeps its FP32 decision).
+__device__ __noinline__ double retrace_tau64(const TraceArgs& A, uint32_t src, int level, uint32_t pix, int tc0,
+                                int tc1, int tc2, bool* ok) {
+  const SourceDev& S = A.src[src];
+  const InstDev& I = A.inst[S.inst];
+  const double s0 = S.s[0], s1 = S.s[1], s2 = S.s[2];
+  int l = A.level0;
+  double r = 0.0, tau = 0.0;
+  *ok = false;
+  for (int guard = 0; guard <= RT_MAX_LEVEL + 1; ++guard) {
+    const uint32_t p = pix >> (2 * (level - l));
+    double n[3];
+    pix2vec64(l, p, n);
+    int c0 = cell_of64(__dadd_rn(s0, __dmul_rn(r, n[0])), n[0]);
+    int c1 = cell_of64(__dadd_rn(s1, __dmul_rn(r, n[1])), n[1]);
+    int c2 = cell_of64(__dadd_rn(s2, __dmul_rn(r, n[2])), n[2]);
+    double t0 = next_t64(c0, s0, n[0]), t1 = next_t64(c1, s1, n[1]), t2 = next_t64(c2, s2, n[2]);
+    bool split = false;
+    for (int st = 0; st < A.max_steps; ++st) {
+      if (c0 < 0 || c0 >= I.nx || c1 < 0 || c1 >= I.ny || c2 < 0 || c2 >= I.nz) return tau;
+      const double rn = fmin(t0, fmin(t1, t2));
+      if (l < A.max_level && rn > A.rsplit[l]) { split = true; break; }
+      double dr = __dsub_rn(rn, r);
+      if (dr < 0) dr = 0;
+      const int idx = c0 + I.nx * (c1 + I.ny * c2);
+      const double nh = __dmul_rn(I.nH[idx], I.xHI[idx]);
+      tau = __dadd_rn(tau, __dmul_rn(__dmul_rn(S.sdx, nh), dr));
+      if (l == level && c0 == tc0 && c1 == tc1 && c2 == tc2) { *ok = true; return tau; }
+      if (tau > A.tau_term) return tau;
+      if (n[0] != 0 && t0 == rn) { c0 += n[0] > 0 ? 1 : -1; t0 = next_t64(c0, s0, n[0]); }
+      if (n[1] != 0 && t1 == rn) { c1 += n[1] > 0 ? 1 : -1; t1 = next_t64(c1, s1, n[1]); }
+      if (n[2] != 0 && t2 == rn) { c2 += n[2] > 0 ? 1 : -1; t2 = next_t64(c2, s2, n[2]); }
+      r = rn;
+    }
+    if (!split || l >= level) return tau;
+    ++l;
+  }
+  return tau;
+}
+
+// ---------------------------------------------------------------------------
+// FP32-mixed walker.
+//
+// All per-segment arithmetic is FP32.  Crossing distances t_i, the radius r
+// and segment lengths are carried as unevaluated FP32 pairs (hi + lo,
+// "double-float"), built from the pixel direction stored as an FP32 pair
+// (FP64 direction rounded twice) and from the source position as an FP32
+// pair, so each t carries ~44 correct bits while every instruction is FP32.
+// Optical depth, attenuation and the k_ph / Gamma deposits are plain FP32.
+//
+// Each decision that shapes the ray tree -- which cell plane is crossed next,
+// whether the package splits, whether it terminates -- is taken from the
+// FP32 values only when an error bound proves it equals the FP64 decision:
+//   |t_pair - t_FP64| <= 2^-40 t + 2^-46 |s| / |n|   (per axis),
+//   |tau_FP32 - tau_FP64| <= tau_err (accumulated per segment).
+// Inside a band the decision is re-taken in FP64: the crossing distances of
+// the current cell from the FP64 direction, or the FP64 optical depth of the
+// package's lineage.  Per-level counts therefore equal the FP64 path's.
+// ---------------------------------------------------------------------------
+constexpr float kEps32 = 5.9604645e-8f;   // 2^-24
+constexpr float kBandT = 9.094947e-13f;   // 2^-40
+constexpr float kBandS = 1.4210855e-14f;  // 2^-46
+
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, err};
+}
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  F2 s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+// a - b as FP32 (both pairs), accurate to ~2^-44 |a|
+__device__ __forceinline__ float f2_diff(F2 a, F2 b) {
+  const F2 d = two_sum(a.hi, -b.hi);
+  return __fadd_rn(d.hi, __fadd_rn(d.lo, __fsub_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ bool f2_less(F2 a, F2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool f2_eq(F2 a, F2 b) { return a.hi == b.hi && a.lo == b.lo; }
+// 1 / (n.hi + n.lo) as a pair (one Newton correction)
+__device__ __forceinline__ F2 f2_recip(F2 n) {
+  const float q = __frcp_rn(n.hi);
+  float e = fmaf(-n.hi, q, 1.0f);
+  e = fmaf(-n.lo, q, e);
+  return fast_two_sum(q, __fmul_rn(e, q));
+}
+// floor of hi + lo
+__device__ __forceinline__ int f2_floor(F2 u) {
+  const float f = floorf(u.hi);
+  if (u.hi == f && u.lo < 0.0f) return (int)f - 1;
+  return (int)f;
+}
+
+// Direction of (level, pix) as FP32 pairs: from the device table when the
+// level is tabulated, else from the FP64 evaluation.  Returns the
+// 45-degree-meridian flag.
+__device__ __forceinline__ int dir_pair(const TraceArgs& A, int level, uint32_t pix, F2 n[3]) {
+  if (level <= A.dir_levels) {
+    const size_t idx = (size_t)4 * (((size_t)1 << (2 * level)) - 1) + pix;
+    const float4 h = __ldg(&A.dir_tab[2 * idx]);
+    const float4 l = __ldg(&A.dir_tab[2 * idx + 1]);
+    n[0] = {h.x, l.x};
+    n[1] = {h.y, l.y};
+    n[2] = {h.z, l.z};
+    return h.w != 0.0f;
+  }
+  double v[3];
+  const int diag = pix2vec64(level, pix, v);
+  for (int i = 0; i < 3; ++i) {
+    const float hi = (float)v[i];
+    n[i] = {hi, (float)(v[i] - (double)hi)};
+  }
+  return diag;
+}
+
+struct Walk32 {
+  using Rec = Rec32;
+  uint32_t src, level, pix;
+  int inst, local;
+  F2 r;
+  float P, tau, Pstart, tau_err;
+  F2 s0, s1, s2;        // source position (cell units)
+  F2 iv0, iv1, iv2;     // 1 / n_i
+  F2 t0, t1, t2;        // distance to the next plane on each axis
+  float sg0, sg1, sg2;  // sign of n_i (0 for a vanishing component)
+  float ab0, ab1, ab2;  // absolute part of the crossing bands
+  int c0, c1, c2;
+  int nx, ny, nz, steps;
+  int diag_exact;       // |n_x| == |n_y| in both precisions and the source is exact
+  const float* nhi;
+  float* K;
+  float* G;
+  float sdx, w, rw, heat;
+  double unit;
+
+  __device__ __forceinline__ bool inside() const {
+    return c0 >= 0 && c0 < nx && c1 >= 0 && c1 < ny && c2 >= 0 && c2 < nz;
+  }
+  // distance from the source to the next plane of cell c along an axis
+  __device__ __forceinline__ static F2 next_t(int c, F2 s, float sg, F2 iv) {
+    if (sg == 0.0f) return {__int_as_float(0x7f800000), 0.0f};
+    const float b = (float)(sg > 0.0f ? c + 1 : c);
+    const F2 d0 = two_sum(b, -s.hi);
+    const F2 d = fast_two_sum(d0.hi, __fsub_rn(d0.lo, s.lo));
+    return f2_mul(d, iv);
+  }
+  // cell of coordinate u along an axis (tie rule: n > 0 floor, n < 0 ceil - 1)
+  __device__ __forceinline__ static int cell_of(F2 u, float sg) {
+    const int f = f2_floor(u);
+    if (sg < 0.0f && (float)f == u.hi && u.lo == 0.0f) return f - 1;
+    return f;
+  }
+  __device__ __forceinline__ float band(F2 t, float ab) const { return fmaf(t.hi, kBandT, ab); }
+
+  __device__ __forceinline__ bool start(const TraceArgs& A) {
+    const SourceDev& S = A.src[src];
+    inst = S.inst;
+    local = S.local;
+    s0 = {S.s32[0], S.slo32[0]};
+    s1 = {S.s32[1], S.slo32[1]};
+    s2 = {S.s32[2], S.slo32[2]};
+    sdx = S.sdx32; w = S.w32; rw = S.rw32; heat = S.heat32; unit = S.unit;
+    const InstDev& I = A.inst[inst];
+    nx = I.nx; ny = I.ny; nz = I.nz;
+    nhi = (const float*)I.nhi;
+    K = (float*)I.K;
+    G = (float*)I.G;
+    F2 n[3];
+    const int diag = dir_pair(A, (int)level, pix, n);
+    diag_exact = diag && S.exact32;
+    sg0 = n[0].hi > 0 ? 1.0f : (n[0].hi < 0 ? -1.0f : 0.0f);
+    sg1 = n[1].hi > 0 ? 1.0f : (n[1].hi < 0 ? -1.0f : 0.0f);
+    sg2 = n[2].hi > 0 ? 1.0f : (n[2].hi < 0 ? -1.0f : 0.0f);
+    iv0 = sg0 != 0.0f ? f2_recip(n[0]) : F2{0.0f, 0.0f};
+    iv1 = sg1 != 0.0f ? f2_recip(n[1]) : F2{0.0f, 0.0f};
+    iv2 = sg2 != 0.0f ? f2_recip(n[2]) : F2{0.0f, 0.0f};
+    ab0 = S.sabs32[0] * fabsf(iv0.hi);
+    ab1 = S.sabs32[1] * fabsf(iv1.hi);
+    ab2 = S.sabs32[2] * fabsf(iv2.hi);
+    c0 = cell_of(f2_add(s0, f2_mul(r, n[0])), sg0);
+    c1 = cell_of(f2_add(s1, f2_mul(r, n[1])), sg1);
+    c2 = cell_of(f2_add(s2, f2_mul(r, n[2])), sg2);
+    Pstart = P;
+    steps = 0;
+    if (!inside()) return false;
+    t0 = next_t(c0, s0, sg0, iv0);
+    t1 = next_t(c1, s1, sg1, iv1);
+    t2 = next_t(c2, s2, sg2, iv2);
+    return true;
+  }
+
+  __device__ __forceinline__ void load(const Rec& q) {
+    r = {q.r, q.r_lo}; P = q.P; tau = q.tau; tau_err = q.tau_err; src = q.src; pix = q.pix;
+    level = q.tag & 15u;
+  }
+  __device__ __forceinline__ void store_child(Rec* q, uint32_t cpix, uint32_t epoch) const {
+    __stcg(&q->r, r.hi);
+    __stcg(&q->P, P * 0.25f);
+    __stcg(&q->tau, tau);
+    __stcg(&q->tau_err, tau_err);
+    __stcg(&q->src, src);
+    __stcg(&q->pix, cpix);
+    __stcg(&q->r_lo, r.lo);
+    st_release_u32(&q->tag, (epoch << 4) | (level + 1));
+  }
+  __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
+    const uint32_t tg = ld_acquire_u32(&q->tag);
+    if ((tg >> 4) != (epoch & 0x0fffffffu)) return false;
+    o.r = __ldcg(&q->r); o.P = __ldcg(&q->P); o.tau = __ldcg(&q->tau);
+    o.tau_err = __ldcg(&q->tau_err); o.src = __ldcg(&q->src); o.pix = __ldcg(&q->pix);
+    o.r_lo = __ldcg(&q->r_lo);
+    o.tag = tg;
+    return true;
+  }
+  __device__ __forceinline__ void set_root(uint32_t gsrc, uint32_t lvl, uint32_t p) {
+    src = gsrc; level = lvl; pix = p; r = {0.0f, 0.0f}; P = 1.0f; tau = 0.0f; tau_err = 0.0f;
+  }
+  __device__ __forceinline__ void become_child0() {
+    level += 1; pix = 4u * pix; P = P * 0.25f;
+  }
+
+  // Exact (FP64) crossing decision for the current cell.
+  __device__ __noinline__ void decide64(const TraceArgs& A, bool& split, bool& m0, bool& m1, bool& m2) const {
+    const SourceDev& S = A.src[src];
+    double n[3];
+    pix2vec64((int)level, pix, n);
+    const double u0 = next_t64(c0, S.s[0], n[0]);
+    const double u1 = next_t64(c1, S.s[1], n[1]);
+    const double u2 = next_t64(c2, S.s[2], n[2]);
+    const double rn = fmin(u0, fmin(u1, u2));
+    split = (int)level < A.max_level && rn > A.rsplit[level];
+    m0 = n[0] != 0 && u0 == rn;
+    m1 = n[1] != 0 && u1 == rn;
+    m2 = n[2] != 0 && u2 == rn;
+  }
+
+  __device__ __forceinline__ int step(const TraceArgs& A, LaneAcc& acc) {
+    // next crossing: the smallest pair, and whether the order is provable
+    int imin = 0;
+    F2 rn = t0;
+    if (f2_less(t1, rn)) { rn = t1; imin = 1; }
+    if (f2_less(t2, rn)) { rn = t2; imin = 2; }
+    const float emin = imin == 0 ? band(t0, ab0) : (imin == 1 ? band(t1, ab1) : band(t2, ab2));
+    bool m0 = imin == 0, m1 = imin == 1, m2 = imin == 2;
+    bool unsure = false;
+    const bool xy_tie = diag_exact && f2_eq(t0, t1);
+    if (imin != 0 && sg0 != 0.0f && f2_diff(t0, rn) <= band(t0, ab0) + emin) {
+      if (imin == 1 && xy_tie) m0 = true; else unsure = true;
+    }
+    if (imin != 1 && sg1 != 0.0f && f2_diff(t1, rn) <= band(t1, ab1) + emin) {
+      if (imin == 0 && xy_tie) m1 = true; else unsure = true;
+    }
+    if (imin != 2 && sg2 != 0.0f && f2_diff(t2, rn) <= band(t2, ab2) + emin) unsure = true;
+    bool split = false;
+    if ((int)level < A.max_level) {
+      const float d = f2_diff(rn, F2{A.rsplit32[level], A.rsplit32lo[level]});
+      const float bnd = emin + A.rsplit32[level] * kBandT;
+      if (d > bnd) split = true;
+      else if (!(-d > bnd)) unsure = true;
+    }
+    if (unsure) {
+      decide64(A, split, m0, m1, m2);
+      acc.fallbacks++;
+    }
+    if (split) return EV_SPLIT;
+    float dr = f2_diff(rn, r);
+    if (dr < 0.0f) dr = 0.0f;
+    const int idx = c0 + nx * (c1 + ny * c2);
+    const float nh = __ldg(&nhi[idx]);
+    const float kap = sdx * nh;
+    const float dtau = kap * dr;
+    const float am = -expm1f(-dtau);
+    const float phi = dtau > 0.0f ? am / dtau : 1.0f;
+    const float kadd = P * w * dr * phi;
+    atomicAdd(&K[idx], kadd);
+    if (heat != 0.0f) atomicAdd(&G[idx], kadd * heat);
+    if (dr > 0.0f) acc.segments++;
+    // P e^-tau, not P - dP: in FP32 the difference cancels when tau is large
+    P = P * expf(-dtau);
+    tau = tau + dtau;
+    // tau_FP32 - tau_FP64: rounding of kappa, dr and the sum, plus the pair error of dr
+    tau_err = tau_err + dtau * (8.0f * kEps32) + kap * (2.0f * emin + 1e-30f) + tau * (2.0f * kEps32);
+    {
+      const float d = tau - A.tau_term32;
+      const float bnd = tau_err + A.tau_term32 * (4.0f * kEps32) + 1e-12f;
+      bool term;
+      if (d > bnd) term = true;
+      else if (-d > bnd) term = false;
+      else {
+        bool ok;
+        const double t64 = retrace_tau64(A, src, (int)level, pix, c0, c1, c2, &ok);
+        acc.fallbacks++;
+        term = ok ? (t64 > A.tau_term) : (d > 0.0f);
+      }
+      if (term) {
+        if (nh > 0.0f) {
+          const float kres = P * rw / nh;
+          atomicAdd(&K[idx], kres);
+          if (heat != 0.0f) atomicAdd(&G[idx], kres * heat);
+        }
+        acc.absorbed += (double)Pstart * unit;
+        return EV_DONE;
+      }
+    }
+    if (m0) { c0 += sg0 > 0 ? 1 : -1; t0 = next_t(c0, s0, sg0, iv0); }
+    if (m1) { c1 += sg1 > 0 ? 1 : -1; t1 = next_t(c1, s1, sg1, iv1); }
+    if (m2) { c2 += sg2 > 0 ? 1 : -1; t2 = next_t(c2, s2, sg2, iv2); }
+    r = rn;
+    if (!inside()) {
+      acc.absorbed += ((double)Pstart - (double)P) * unit;
+      acc.escaped += (double)P * unit;
+      return EV_DONE;
+    }
+    if (++steps > A.max_steps) {
+      set_status(A.ctl, RT_ERR_STATE);
+      acc.absorbed += ((double)Pstart - (double)P) * unit;
+      acc.escaped += (double)P * unit;
+      return EV_DONE;
+    }
+    return EV_NONE;
+  }
+  __device__ __forceinline__ void on_split(LaneAcc& acc) const {
+    acc.absorbed += ((double)Pstart - (double)P) * unit;
+  }
+  __device__ __forceinline__ void on_start_outside(LaneAcc& acc) const { acc.escaped += (double)P * unit; }
+};
+
+// ---------------------------------------------------------------------------
 // The persistent kernel, generic over the walker.
 // ---------------------------------------------------------------------------
 template <class W>
@@ -263,11 +618,12 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A) {
         LC.add(A, S.inst, S.local, A.level0, p);
       } else {
         const unsigned long long slot = tk - A.n_roots;
-        if (slot < A.cap && ld_acquire_u32(&queue[slot].tag) == epoch) {
+        if (slot < A.cap) {
           Rec q;
-          W::read_rec(&queue[slot], q);
-          w.load(q);
-          got = true;
+          if (W::poll(&queue[slot], epoch, q)) {
+            w.load(q);
+            got = true;
+          }
         }
       }
       if (got) {
@@ -387,15 +743,60 @@ cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_root
 cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm) {
   if (precision == RT_FP64)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<Walk64>, block, 0);
-  return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<Walk32>, block, 0);
 }
 
 cudaError_t launch_trace(int precision, const TraceArgs& A, int grid, int block, cudaStream_t st) {
-  if (precision == RT_FP64) {
-    trace_kernel<Walk64><<<grid, block, 0, st>>>(A);
-    return cudaGetLastError();
+  if (precision == RT_FP64) trace_kernel<Walk64><<<grid, block, 0, st>>>(A);
+  else trace_kernel<Walk32><<<grid, block, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+// Self-check of the FP32 direction bound: max over the pixels of `level` of
+// max_i |n32_i - n64_i|, written to out[0] (as the bit pattern of a positive
+// double, so atomicMax on the integer view orders it correctly).
+__global__ void direction_error_kernel(int level, unsigned long long* out) {
+  const unsigned long long npix = 12ULL << (2 * level);
+  double worst = 0.0;
+  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < npix;
+       p += (unsigned long long)gridDim.x * blockDim.x) {
+    double n64[3];
+    float n32[3];
+    pix2vec64(level, (uint32_t)p, n64);
+    pix2vec32(level, (uint32_t)p, n32);
+    for (int i = 0; i < 3; ++i) worst = fmax(worst, fabs((double)n32[i] - n64[i]));
   }
-  return cudaErrorInvalidValue;
+  atomicMax(out, (unsigned long long)__double_as_longlong(worst));
+}
+
+// Direction table: for each pixel of levels 0..L (level l starts at entry
+// 4 (4^l - 1)), two float4: (hi.x, hi.y, hi.z, diag) and (lo.x, lo.y, lo.z, 0)
+// with hi + lo the FP64 direction of pix2vec64.
+__global__ void direction_table_kernel(int level, float4* tab) {
+  const unsigned long long npix = 12ULL << (2 * level);
+  const size_t base = (size_t)4 * (((size_t)1 << (2 * level)) - 1);
+  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < npix;
+       p += (unsigned long long)gridDim.x * blockDim.x) {
+    double v[3];
+    const int diag = pix2vec64(level, (uint32_t)p, v);
+    float hi[3], lo[3];
+    for (int i = 0; i < 3; ++i) {
+      hi[i] = (float)v[i];
+      lo[i] = (float)(v[i] - (double)hi[i]);
+    }
+    tab[2 * (base + p)] = make_float4(hi[0], hi[1], hi[2], diag ? 1.0f : 0.0f);
+    tab[2 * (base + p) + 1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+  }
+}
+
+cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st) {
+  direction_table_kernel<<<152 * 8, 256, 0, st>>>(level, tab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_direction_check(int level, unsigned long long* out, cudaStream_t st) {
+  direction_error_kernel<<<152 * 8, 256, 0, st>>>(level, out);
+  return cudaGetLastError();
 }
 
 }  // namespace rtg

@@ -90,6 +90,7 @@ def lib():
             "rt_set_state": ([vp, vp, vp, vp, i], i),
             "rt_get_ionised": ([vp, vp, i, i], i),
             "rt_synchronize": ([vp], i),
+            "rt_selfcheck_directions": ([vp, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
             "rt_kernel_launches": ([], ctypes.c_uint64),
             "rt_get_last_error": ([], ctypes.c_char_p),
         }
@@ -234,6 +235,13 @@ def rt_get_ionised(grid, ncell, dtype=RT_DTYPE_F64, where="host"):
     p = out.data_ptr() if where == "device" else out.ctypes.data
     check(lib().rt_get_ionised(grid, p, int(dtype), RT_MEM_DEVICE if where == "device" else RT_MEM_HOST))
     return out
+
+
+def rt_selfcheck_directions(ctx, level: int):
+    e = ctypes.c_double()
+    b = ctypes.c_double()
+    check(lib().rt_selfcheck_directions(ctx, int(level), ctypes.byref(e), ctypes.byref(b)))
+    return e.value, b.value
 
 
 def rt_synchronize(grid):
