@@ -80,7 +80,8 @@ typedef struct {
   int max_level;         /* no split beyond this level (level0..RT_MAX_LEVEL) */
   int64_t queue_capacity;/* package records in the device queue; 0 = automatic */
   double timeout_s;      /* bound on any device-side wait; <= 0 = 2 s */
-  int block_threads;     /* threads per block of the trace kernel; 0 = tuned */
+  int blocks_per_sm;     /* resident 256-thread blocks of the trace kernel per SM;
+                            0 = as many as fit (lower it to share the GPU) */
   int segs_per_iter;     /* segments a lane traces between queue visits; 0 = tuned */
 } rt_trace_params;
 
@@ -93,7 +94,8 @@ typedef struct {
   uint64_t hashes[RT_MAX_LEVEL + 1];   /* order-free checksum of the created
                                           (source, level, pixel) set, see below */
   uint64_t segments;                   /* cell segments with length > 0 */
-  uint64_t fallbacks;                  /* FP32 decisions re-taken in FP64 */
+  uint64_t fallbacks;                  /* FP32 crossing/split decisions re-taken in FP64 */
+  uint64_t fallbacks_tau;              /* FP32 termination decisions re-taken in FP64 */
   uint64_t queue_pushed;               /* records written to the queue */
   int status;                          /* RT_OK or the device-side error */
   float kernel_ms;                     /* duration of the trace kernel itself

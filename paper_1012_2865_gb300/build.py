@@ -22,6 +22,8 @@ LIB = os.path.join(PKG, "librt_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
            "--expt-relaxed-constexpr"]
+# resident blocks of 256 threads per SM the FP32 trace kernel is compiled for
+TRACE_MIN_BLOCKS = int(os.environ.get("RT_TRACE_MIN_BLOCKS", "2"))
 
 
 def _nvcc() -> str:
@@ -52,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *NVFLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVFLAGS, f"-DTRACE_MIN_BLOCKS={TRACE_MIN_BLOCKS}", *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -322,18 +322,19 @@ static int prepare_sources(rt_grid* g, int level0) {
     S.inst = 0;
     S.local = (int)i;
     int exact = 1;
+    float s32[3], slo[3], sab[3];
     for (int a = 0; a < 3; ++a) {
-      S.s32[a] = (float)S.s[a];
-      S.slo32[a] = (float)(S.s[a] - (double)S.s32[a]);
-      const bool pair_exact = (double)S.s32[a] + (double)S.slo32[a] == S.s[a];
-      S.sabs32[a] = pair_exact ? 0.0f : (float)(ldexp(fabs(S.s[a]), -46));
+      s32[a] = (float)S.s[a];
+      slo[a] = (float)(S.s[a] - (double)s32[a]);
+      const bool pair_exact = (double)s32[a] + (double)slo[a] == S.s[a];
+      sab[a] = pair_exact ? 0.0f : (float)(ldexp(fabs(S.s[a]), -46));
       exact &= exact_in_f32(S.s[a]) ? 1 : 0;
     }
     S.exact32 = exact && g->nx <= 4096 && g->ny <= 4096 && g->nz <= 4096;
-    S.sdx32 = (float)S.sdx;
-    S.w32 = (float)S.w;
-    S.rw32 = (float)S.rw;
-    S.heat32 = (float)S.heat;
+    S.k32 = make_float4((float)S.sdx, (float)S.w, (float)S.rw, (float)S.heat);
+    S.s32 = make_float4(s32[0], s32[1], s32[2], S.exact32 ? 1.0f : 0.0f);
+    S.slo32 = make_float4(slo[0], slo[1], slo[2], 0.0f);
+    S.sabs32 = make_float4(sab[0], sab[1], sab[2], 0.0f);
     v[i] = S;
   }
   if (v.size() > g->src_dev_cap) {
@@ -359,8 +360,8 @@ static int check_params(const rt_trace_params* p) {
   if (!(p->phi_c > 0) || !isfinite(p->phi_c)) return fail(RT_ERR_INVALID_ARG, "rt_trace: phi_c = %g", p->phi_c);
   if (!(p->f_term > 0 && p->f_term < 1)) return fail(RT_ERR_INVALID_ARG, "rt_trace: f_term = %g", p->f_term);
   if (p->queue_capacity < 0) return fail(RT_ERR_INVALID_ARG, "rt_trace: queue_capacity < 0");
-  if (p->block_threads != 0 && (p->block_threads % 32 != 0 || p->block_threads > 256 || p->block_threads < 32))
-    return fail(RT_ERR_INVALID_ARG, "rt_trace: block_threads = %d", p->block_threads);
+  if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32)
+    return fail(RT_ERR_INVALID_ARG, "rt_trace: blocks_per_sm = %d", p->blocks_per_sm);
   if (p->segs_per_iter < 0 || p->segs_per_iter > 1024) return fail(RT_ERR_INVALID_ARG, "rt_trace: segs_per_iter = %d", p->segs_per_iter);
   return RT_OK;
 }
@@ -431,12 +432,13 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p) {
   A.cap = g->ts.cap;
   A.ctl = g->ts.ctl;
   A.timeout_ns = (long long)((p->timeout_s > 0 ? p->timeout_s : 2.0) * 1e9);
-  A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 4;
+  A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 8;
   A.max_steps = 2 * (g->nx + g->ny + g->nz) + 16;
-  const int block = p->block_threads > 0 ? p->block_threads : 256;
+  const int block = 256;  // the trace kernel is compiled for 256-thread blocks
   int per_sm = 0;
   CUDA_TRY(trace_occupancy(g->precision, block, &per_sm));
   if (per_sm < 1) per_sm = 1;
+  if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
   CUDA_TRY(cudaEventRecord(g->ev0, st));
   LAUNCH_TRY(launch_trace(g->precision, A, per_sm * g->ctx->num_sms, block, st));
   CUDA_TRY(cudaEventRecord(g->ev1, st));
@@ -447,7 +449,7 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p) {
 static int read_budget(rt_grid* g, rt_budget* out) {
   double* hacc = (double*)g->host_rb;
   unsigned long long* hcnt = (unsigned long long*)((char*)g->host_rb + 64);
-  unsigned long long* hctl = (unsigned long long*)((char*)g->host_rb + 64 + 8 * kCntWords);
+  unsigned long long* hctl = (unsigned long long*)((char*)g->host_rb + 512);
   cudaStream_t st = g->stream;
   CUDA_TRY(cudaMemcpyAsync(hacc, g->acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hcnt, g->cnt, kCntWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -463,6 +465,7 @@ static int read_budget(rt_grid* g, rt_budget* out) {
   }
   out->segments = hcnt[kCntSegments];
   out->fallbacks = hcnt[kCntFallbacks];
+  out->fallbacks_tau = hcnt[kCntFallbacksTau];
   out->queue_pushed = hctl[CTL_TAIL];
   out->status = (int)hctl[CTL_STATUS];
   float ms = 0.f;

@@ -24,9 +24,12 @@ __global__ void chem_kernel(long long ncell, const double* __restrict__ nH, doub
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
     double x = xHI[c], z = xHII[c];
+    const KT kc = K[c];
+    // no radiation and fully neutral: every substep returns (1, 0) exactly
+    if (kc == (KT)0 && z == 0.0 && x == 1.0) continue;
     const double n = nH[c];
     const double a = __dmul_rn(__dmul_rn(h, alpha), n);
-    const double hk = __dmul_rn(h, (double)K[c]);
+    const double hk = __dmul_rn(h, (double)kc);
     const double b = __dadd_rn(1.0, hk);
     for (int i = 0; i < nsub; ++i) {
       const double D = __dadd_rn(__dmul_rn(b, b), __dmul_rn(__dmul_rn(4.0, a), __dadd_rn(z, hk)));
@@ -39,6 +42,55 @@ __global__ void chem_kernel(long long ncell, const double* __restrict__ nH, doub
     xHI[c] = x;
     xHII[c] = z;
     nhi[c] = (NT)__dmul_rn(n, x);
+  }
+}
+
+// Same backward-Euler step for the FP32-mixed path, solved by FP32 +
+// one FP64 Newton correction: the smaller fraction is first obtained in FP32
+// from its cancellation-free formula, then corrected once with the residual
+// of the implicit equation evaluated in FP64,
+//   x-form: g(x') = a x'^2 - (2a + b) x' + (a + x),  g' = 2a x' - (2a + b),
+//   z-form: f(z') = a z'^2 + b z' - (z + hk),         f' = 2a z' + b.
+// From a ~1e-7 relative guess one Newton step leaves ~1e-15, so the state
+// stays FP64-accurate while the step costs a few FP64 operations instead of
+// two FP64 divisions and a square root.
+__global__ void chem_mixed_kernel(long long ncell, const double* __restrict__ nH, double* __restrict__ xHI,
+                                  double* __restrict__ xHII, const float* __restrict__ K,
+                                  float* __restrict__ nhi, double h, int nsub, double alpha) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    double x = xHI[c], z = xHII[c];
+    const float kc = K[c];
+    if (kc == 0.0f && z == 0.0 && x == 1.0) continue;
+    const double n = nH[c];
+    const double a = h * alpha * n;
+    const double hk = h * (double)kc;
+    const double b = 1.0 + hk;
+    const double two_a_b = 2.0 * a + b;
+    const float af = (float)a, bf = (float)b, hkf = (float)hk;
+    for (int i = 0; i < nsub; ++i) {
+      const float xf = (float)x, zf = (float)z;
+      const float wf = zf + hkf;
+      const float sq = sqrtf(fmaf(4.0f * af, wf, bf * bf));
+      if (xf < 0.5f) {
+        const float xg = 2.0f * (af + xf) / (2.0f * af + bf + sq);
+        const double xd = (double)xg;
+        const double g = fma(fma(a, xd, -two_a_b), xd, a + x);
+        const float gp = fmaf(2.0f * af, xg, -(2.0f * af + bf));
+        x = xd - (double)((float)g / gp);
+        z = 1.0 - x;
+      } else {
+        const float zg = 2.0f * wf / (bf + sq);
+        const double zd = (double)zg;
+        const double f = fma(fma(a, zd, b), zd, -(z + hk));
+        const float fp = fmaf(2.0f * af, zg, bf);
+        z = zd - (double)((float)f / fp);
+        x = 1.0 - z;
+      }
+    }
+    xHI[c] = x;
+    xHII[c] = z;
+    nhi[c] = (float)(n * x);
   }
 }
 
@@ -77,8 +129,8 @@ cudaError_t launch_chem(int precision, long long ncell, const double* nH, double
     chem_kernel<double, double><<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const double*)K,
                                                          (double*)nhi, h, nsub, alpha);
   else
-    chem_kernel<float, float><<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const float*)K,
-                                                       (float*)nhi, h, nsub, alpha);
+    chem_mixed_kernel<<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const float*)K, (float*)nhi, h, nsub,
+                                              alpha);
   return cudaGetLastError();
 }
 

@@ -25,23 +25,22 @@ enum CtlWord {
 // One point source, prepared on the host for the kernels.  P of a package is
 // carried in units of the root package's photon rate (root P = 1 exactly),
 // so every per-source constant below folds in unit = ndot / npix0.
-struct SourceDev {
-  double s[3];   // position in cell units (pos_cm / dx)
-  double sdx;    // sigma * dx: optical depth per unit n_HI per cell length
-  double w;      // unit * sigma / dx^2: k_ph per unit P per cell length (phi = 1)
-  double rw;     // unit / dx^3: k_ph per unit P per unit n_HI (residual absorption)
-  double heat;   // (E_ph - 13.6 eV) in erg
-  double unit;   // photons/s carried by P = 1
-  float s32[3];
-  float sdx32;
-  float w32;
-  float rw32;
-  float heat32;
-  float slo32[3];   // s - s32 rounded to FP32: (s32, slo32) is the position as an FP32 pair
-  float sabs32[3];  // 2^-46 |s| for positions the pair does not hold exactly, else 0
+struct __align__(16) SourceDev {
+  // FP32 view (mixed path), one 16-byte load each
+  float4 k32;     // sdx, w, rw, heat (see the FP64 fields)
+  float4 s32;     // position as FP32 pair, high part; .w = 1 if exact32
+  float4 slo32;   // low part (s - s32)
+  float4 sabs32;  // 2^-46 |s| where the pair does not hold s exactly, else 0
+  // FP64 view
+  double s[3];    // position in cell units (pos_cm / dx)
+  double sdx;     // sigma * dx: optical depth per unit n_HI per cell length
+  double w;       // unit * sigma / dx^2: k_ph per unit P per cell length (phi = 1)
+  double rw;      // unit / dx^3: k_ph per unit P per unit n_HI (residual absorption)
+  double heat;    // (E_ph - 13.6 eV) in erg
+  double unit;    // photons/s carried by P = 1
   int inst;       // owning grid slot
   int local;      // index of the source within its grid (checksum)
-  int exact32;    // s32 == s and plane offsets are exact in FP32
+  int exact32;    // position on a 1/16-cell lattice within 4096 cells (see api.cu)
   int pad;
 };
 
@@ -54,11 +53,12 @@ struct InstDev {
   void* K;                  // k_ph accumulator (double or float)
   void* G;                  // Gamma accumulator (double or float)
   double* acc;              // [0] emitted [1] absorbed [2] escaped (photons/s)
-  unsigned long long* cnt;  // [0,15) counts, [15,30) hashes, [30] segments, [31] fallbacks
+  unsigned long long* cnt;  // [0,15) counts, [15,30) hashes, [30] segments, [31], [32] fallbacks
 };
 constexpr int kCntSegments = 2 * kLevels;
 constexpr int kCntFallbacks = 2 * kLevels + 1;
-constexpr int kCntWords = 2 * kLevels + 2;
+constexpr int kCntFallbacksTau = 2 * kLevels + 2;
+constexpr int kCntWords = 2 * kLevels + 3;
 
 // Queue records.  The tag word is written last with release semantics and
 // equals the trace's epoch once the record is complete.
@@ -114,6 +114,11 @@ __host__ __device__ __forceinline__ uint64_t pkg_hash(uint32_t src, uint32_t lev
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {

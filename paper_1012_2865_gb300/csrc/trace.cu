@@ -28,18 +28,24 @@
 #include "healpix.cuh"
 #include "rt_internal.cuh"
 
+#ifndef TRACE_MIN_BLOCKS
+#define TRACE_MIN_BLOCKS 2
+#endif
+
 namespace rtg {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kShInst = 16;  // grids whose level counters are kept in shared memory
+constexpr int kBlock = 256;  // threads per block of the trace kernel
 
 enum Event { EV_NONE = 0, EV_SPLIT = 1, EV_DONE = 2 };
 
+// Photon budget of one lane for the grid it is working on; lives in shared
+// memory (one slot per thread) and is touched only at package events.
 struct LaneAcc {
-  int inst;
   double emitted, absorbed, escaped;
-  unsigned int segments;
-  unsigned int fallbacks;
+  unsigned int segments, fallbacks, fallbacks_tau;
+  int inst;
 };
 
 __device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A) {
@@ -50,14 +56,20 @@ __device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A) {
     if (a.escaped != 0.0) atomicAdd(&I.acc[2], a.escaped);
     if (a.segments) atomicAdd(&I.cnt[kCntSegments], (unsigned long long)a.segments);
     if (a.fallbacks) atomicAdd(&I.cnt[kCntFallbacks], (unsigned long long)a.fallbacks);
+    if (a.fallbacks_tau) atomicAdd(&I.cnt[kCntFallbacksTau], (unsigned long long)a.fallbacks_tau);
   }
   a.emitted = a.absorbed = a.escaped = 0.0;
   a.segments = 0;
   a.fallbacks = 0;
+  a.fallbacks_tau = 0;
 }
 
-__device__ __forceinline__ void acc_switch(LaneAcc& a, int inst, const TraceArgs& A) {
+// Switch the lane's budget to grid `inst`, flushing the previous grid's sums
+// (with the segments counted since the last switch).
+__device__ __forceinline__ void acc_switch(LaneAcc& a, unsigned& nseg, int inst, const TraceArgs& A) {
   if (a.inst != inst) {
+    a.segments += nseg;
+    nseg = 0;
     acc_flush(a, A);
     a.inst = inst;
   }
@@ -83,42 +95,44 @@ struct LevelCounters {
 // termination) is evaluated with explicitly rounded FP64 operations in the
 // order a plain FP64 evaluation of the method's formulas uses.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_of64(double u, double n) {
+  if (n > 0) return (int)floor(u);
+  if (n < 0) return (int)ceil(u) - 1;
+  return (int)floor(u);
+}
+__device__ __forceinline__ double next_t64(int c, double s, double n) {
+  if (n > 0) return __ddiv_rn(__dsub_rn((double)(c + 1), s), n);
+  if (n < 0) return __ddiv_rn(__dsub_rn((double)c, s), n);
+  return __longlong_as_double(0x7ff0000000000000LL);  // +inf
+}
+
 struct Walk64 {
   using Rec = Rec64;
   uint32_t src, level, pix;
-  int inst, local;
   double r, P, tau, Pstart;
   double s0, s1, s2, n0, n1, n2, t0, t1, t2;
   int c0, c1, c2;
   int nx, ny, nz, steps;
+  unsigned nseg;
   const double* nhi;
   double* K;
   double* G;
-  double sdx, w, rw, heat, unit;
+  double sdx, w, rw, heat;
 
-  __device__ __forceinline__ static int cell_of(double u, double n) {
-    if (n > 0) return (int)floor(u);
-    if (n < 0) return (int)ceil(u) - 1;
-    return (int)floor(u);
-  }
-  __device__ __forceinline__ static double next_t(int c, double s, double n) {
-    if (n > 0) return __ddiv_rn(__dsub_rn((double)(c + 1), s), n);
-    if (n < 0) return __ddiv_rn(__dsub_rn((double)c, s), n);
-    return __longlong_as_double(0x7ff0000000000000LL);  // +inf
-  }
   __device__ __forceinline__ bool inside() const {
     return c0 >= 0 && c0 < nx && c1 >= 0 && c1 < ny && c2 >= 0 && c2 < nz;
   }
+  __device__ __forceinline__ int inst(const TraceArgs& A) const { return A.src[src].inst; }
+  __device__ __forceinline__ double unit(const TraceArgs& A) const { return A.src[src].unit; }
+  __device__ __forceinline__ int lvl() const { return (int)level; }
 
   // Steps 3a-3b: direction and cell at radius r.  Returns false if the
   // package starts outside the box.
   __device__ __forceinline__ bool start(const TraceArgs& A) {
     const SourceDev& S = A.src[src];
-    inst = S.inst;
-    local = S.local;
     s0 = S.s[0]; s1 = S.s[1]; s2 = S.s[2];
-    sdx = S.sdx; w = S.w; rw = S.rw; heat = S.heat; unit = S.unit;
-    const InstDev& I = A.inst[inst];
+    sdx = S.sdx; w = S.w; rw = S.rw; heat = S.heat;
+    const InstDev& I = A.inst[S.inst];
     nx = I.nx; ny = I.ny; nz = I.nz;
     nhi = (const double*)I.nhi;
     K = (double*)I.K;
@@ -126,15 +140,15 @@ struct Walk64 {
     double n[3];
     pix2vec64((int)level, pix, n);
     n0 = n[0]; n1 = n[1]; n2 = n[2];
-    c0 = cell_of(__dadd_rn(s0, __dmul_rn(r, n0)), n0);
-    c1 = cell_of(__dadd_rn(s1, __dmul_rn(r, n1)), n1);
-    c2 = cell_of(__dadd_rn(s2, __dmul_rn(r, n2)), n2);
+    c0 = cell_of64(__dadd_rn(s0, __dmul_rn(r, n0)), n0);
+    c1 = cell_of64(__dadd_rn(s1, __dmul_rn(r, n1)), n1);
+    c2 = cell_of64(__dadd_rn(s2, __dmul_rn(r, n2)), n2);
     Pstart = P;
     steps = 0;
     if (!inside()) return false;
-    t0 = next_t(c0, s0, n0);
-    t1 = next_t(c1, s1, n1);
-    t2 = next_t(c2, s2, n2);
+    t0 = next_t64(c0, s0, n0);
+    t1 = next_t64(c1, s1, n1);
+    t2 = next_t64(c2, s2, n2);
     return true;
   }
 
@@ -151,18 +165,18 @@ struct Walk64 {
     st_release_u32(&q->tag, epoch);
   }
   __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
-    if (ld_acquire_u32(&q->tag) != epoch) return false;
+    if (ld_relaxed_u32(&q->tag) != epoch) return false;
+    __threadfence();
     o.r = __ldcg(&q->r); o.P = __ldcg(&q->P); o.tau = __ldcg(&q->tau);
     o.src = __ldcg(&q->src); o.pix = __ldcg(&q->pix); o.level = __ldcg(&q->level);
     return true;
   }
-  __device__ __forceinline__ void set_root(uint32_t gsrc, uint32_t lvl, uint32_t p) {
-    src = gsrc; level = lvl; pix = p; r = 0.0; P = 1.0; tau = 0.0;
+  __device__ __forceinline__ void set_root(uint32_t gsrc, uint32_t lvl0, uint32_t p) {
+    src = gsrc; level = lvl0; pix = p; r = 0.0; P = 1.0; tau = 0.0;
   }
   __device__ __forceinline__ void become_child0() {
     level += 1; pix = 4u * pix; P = P * 0.25;
   }
-  __device__ __forceinline__ double p_physical(double p) const { return p * unit; }
 
   // One segment.  Returns EV_SPLIT before traversing a cell whose exit radius
   // exceeds R_split, EV_DONE when the package is absorbed or leaves the box.
@@ -179,59 +193,58 @@ struct Walk64 {
     const double kadd = P * w * dr * phi;
     atomicAdd(&K[idx], kadd);
     if (heat != 0.0) atomicAdd(&G[idx], kadd * heat);
-    if (dr > 0) acc.segments++;
+    if (dr > 0) nseg++;
     P = P - P * am;
     tau = __dadd_rn(tau, dtau);
     if (tau > A.tau_term) {
       const double kres = P * rw / nh;
       atomicAdd(&K[idx], kres);
       if (heat != 0.0) atomicAdd(&G[idx], kres * heat);
-      acc.absorbed += Pstart * unit;
+      acc.absorbed += Pstart * unit(A);
       return EV_DONE;
     }
-    if (n0 != 0 && t0 == rn) { c0 += n0 > 0 ? 1 : -1; t0 = next_t(c0, s0, n0); }
-    if (n1 != 0 && t1 == rn) { c1 += n1 > 0 ? 1 : -1; t1 = next_t(c1, s1, n1); }
-    if (n2 != 0 && t2 == rn) { c2 += n2 > 0 ? 1 : -1; t2 = next_t(c2, s2, n2); }
+    if (n0 != 0 && t0 == rn) { c0 += n0 > 0 ? 1 : -1; t0 = next_t64(c0, s0, n0); }
+    if (n1 != 0 && t1 == rn) { c1 += n1 > 0 ? 1 : -1; t1 = next_t64(c1, s1, n1); }
+    if (n2 != 0 && t2 == rn) { c2 += n2 > 0 ? 1 : -1; t2 = next_t64(c2, s2, n2); }
     r = rn;
     if (!inside()) {
-      acc.absorbed += (Pstart - P) * unit;
-      acc.escaped += P * unit;
+      const double u = unit(A);
+      acc.absorbed += (Pstart - P) * u;
+      acc.escaped += P * u;
       return EV_DONE;
     }
     if (++steps > A.max_steps) {
       set_status(A.ctl, RT_ERR_STATE);
-      acc.absorbed += (Pstart - P) * unit;
-      acc.escaped += P * unit;
+      const double u = unit(A);
+      acc.absorbed += (Pstart - P) * u;
+      acc.escaped += P * u;
       return EV_DONE;
     }
     return EV_NONE;
   }
   // Budget of the parent's run when it splits (children carry P/4 each).
-  __device__ __forceinline__ void on_split(LaneAcc& acc) const { acc.absorbed += (Pstart - P) * unit; }
-  __device__ __forceinline__ void on_start_outside(LaneAcc& acc) const { acc.escaped += P * unit; }
+  __device__ __forceinline__ void on_split(const TraceArgs& A, LaneAcc& acc) const {
+    acc.absorbed += (Pstart - P) * unit(A);
+  }
+  __device__ __forceinline__ void on_start_outside(const TraceArgs& A, LaneAcc& acc) const {
+    acc.escaped += P * unit(A);
+  }
 };
-
-// ---------------------------------------------------------------------------
-// FP64 re-evaluation helpers for the mixed walker.  They reproduce exactly
-// the arithmetic of the FP64 walker above.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int cell_of64(double u, double n) { return Walk64::cell_of(u, n); }
-__device__ __forceinline__ double next_t64(int c, double s, double n) { return Walk64::next_t(c, s, n); }
 
 // Optical depth that the FP64 evaluation accumulates along the lineage of
 // package (level, pix) of source src up to and including its segment in cell
 // (tc0, tc1, tc2).  Follows the FP64 path from the root: the root pixel at
 // level0 is pix >> 2 (level - level0); at each split the lineage continues
-// with the child on the path to pix.  *ok is false if the lineage does not
-// reach that cell at that level (then the caller keeps its FP32 decision).
+// with the child on the path to pix.  If the lineage does not
+// reach that cell at that level (returns NaN; the caller then keeps its FP32
+// decision).  Takes values only, like decide64.
 __device__ __noinline__ double retrace_tau64(const TraceArgs& A, uint32_t src, int level, uint32_t pix, int tc0,
-                                int tc1, int tc2, bool* ok) {
+                                             int tc1, int tc2) {
   const SourceDev& S = A.src[src];
   const InstDev& I = A.inst[S.inst];
   const double s0 = S.s[0], s1 = S.s[1], s2 = S.s[2];
   int l = A.level0;
   double r = 0.0, tau = 0.0;
-  *ok = false;
   for (int guard = 0; guard <= RT_MAX_LEVEL + 1; ++guard) {
     const uint32_t p = pix >> (2 * (level - l));
     double n[3];
@@ -242,7 +255,7 @@ __device__ __noinline__ double retrace_tau64(const TraceArgs& A, uint32_t src, i
     double t0 = next_t64(c0, s0, n[0]), t1 = next_t64(c1, s1, n[1]), t2 = next_t64(c2, s2, n[2]);
     bool split = false;
     for (int st = 0; st < A.max_steps; ++st) {
-      if (c0 < 0 || c0 >= I.nx || c1 < 0 || c1 >= I.ny || c2 < 0 || c2 >= I.nz) return tau;
+      if (c0 < 0 || c0 >= I.nx || c1 < 0 || c1 >= I.ny || c2 < 0 || c2 >= I.nz) return nan("");
       const double rn = fmin(t0, fmin(t1, t2));
       if (l < A.max_level && rn > A.rsplit[l]) { split = true; break; }
       double dr = __dsub_rn(rn, r);
@@ -250,17 +263,17 @@ __device__ __noinline__ double retrace_tau64(const TraceArgs& A, uint32_t src, i
       const int idx = c0 + I.nx * (c1 + I.ny * c2);
       const double nh = __dmul_rn(I.nH[idx], I.xHI[idx]);
       tau = __dadd_rn(tau, __dmul_rn(__dmul_rn(S.sdx, nh), dr));
-      if (l == level && c0 == tc0 && c1 == tc1 && c2 == tc2) { *ok = true; return tau; }
-      if (tau > A.tau_term) return tau;
+      if (l == level && c0 == tc0 && c1 == tc1 && c2 == tc2) return tau;
+      if (tau > A.tau_term) return nan("");
       if (n[0] != 0 && t0 == rn) { c0 += n[0] > 0 ? 1 : -1; t0 = next_t64(c0, s0, n[0]); }
       if (n[1] != 0 && t1 == rn) { c1 += n[1] > 0 ? 1 : -1; t1 = next_t64(c1, s1, n[1]); }
       if (n[2] != 0 && t2 == rn) { c2 += n[2] > 0 ? 1 : -1; t2 = next_t64(c2, s2, n[2]); }
       r = rn;
     }
-    if (!split || l >= level) return tau;
+    if (!split || l >= level) return nan("");
     ++l;
   }
-  return tau;
+  return nan("");
 }
 
 // ---------------------------------------------------------------------------
@@ -284,7 +297,7 @@ __device__ __noinline__ double retrace_tau64(const TraceArgs& A, uint32_t src, i
 // ---------------------------------------------------------------------------
 constexpr float kEps32 = 5.9604645e-8f;   // 2^-24
 constexpr float kBandT = 9.094947e-13f;   // 2^-40
-constexpr float kBandS = 1.4210855e-14f;  // 2^-46
+constexpr float kClose = 4.76837158e-7f;  // 2^-21: high parts farther apart are ordered
 
 struct F2 {
   float hi, lo;
@@ -323,7 +336,6 @@ __device__ __forceinline__ F2 f2_recip(F2 n) {
   e = fmaf(-n.lo, q, e);
   return fast_two_sum(q, __fmul_rn(e, q));
 }
-// floor of hi + lo
 __device__ __forceinline__ int f2_floor(F2 u) {
   const float f = floorf(u.hi);
   if (u.hi == f && u.lo < 0.0f) return (int)f - 1;
@@ -352,79 +364,93 @@ __device__ __forceinline__ int dir_pair(const TraceArgs& A, int level, uint32_t 
   return diag;
 }
 
+// Exact (FP64) crossing decision for cell (c0, c1, c2) of package (level,
+// pix) of source src: bit 3 = split, bits 0-2 = axes that reach the next
+// plane first.  A free function taking values, so that calling it does not
+// force the caller's walker state into local memory.
+__device__ __noinline__ int decide64(const TraceArgs& A, uint32_t src, int level, uint32_t pix, int c0, int c1,
+                                     int c2) {
+  const SourceDev& S = A.src[src];
+  double n[3];
+  pix2vec64(level, pix, n);
+  const double u0 = next_t64(c0, S.s[0], n[0]);
+  const double u1 = next_t64(c1, S.s[1], n[1]);
+  const double u2 = next_t64(c2, S.s[2], n[2]);
+  const double rn = fmin(u0, fmin(u1, u2));
+  int out = 0;
+  if (level < A.max_level && rn > A.rsplit[level]) out |= 8;
+  if (n[0] != 0 && u0 == rn) out |= 1;
+  if (n[1] != 0 && u1 == rn) out |= 2;
+  if (n[2] != 0 && u2 == rn) out |= 4;
+  return out;
+}
+
 struct Walk32 {
   using Rec = Rec32;
-  uint32_t src, level, pix;
-  int inst, local;
+  uint32_t src, pix;
+  uint32_t level;       // bits 0-3 level, bit 8: 45-degree ray of an exact source
   F2 r;
   float P, tau, Pstart, tau_err;
-  F2 s0, s1, s2;        // source position (cell units)
-  F2 iv0, iv1, iv2;     // 1 / n_i
+  F2 iv0, iv1, iv2;     // 1 / n_i (0 for a vanishing component)
   F2 t0, t1, t2;        // distance to the next plane on each axis
-  float sg0, sg1, sg2;  // sign of n_i (0 for a vanishing component)
-  float ab0, ab1, ab2;  // absolute part of the crossing bands
   int c0, c1, c2;
   int nx, ny, nz, steps;
-  int diag_exact;       // |n_x| == |n_y| in both precisions and the source is exact
+  unsigned nseg;
   const float* nhi;
   float* K;
   float* G;
-  float sdx, w, rw, heat;
-  double unit;
 
+  __device__ __forceinline__ int lvl() const { return (int)(level & 15u); }
+  __device__ __forceinline__ bool diag_exact() const { return (level & 256u) != 0; }
+  __device__ __forceinline__ int inst(const TraceArgs& A) const { return A.src[src].inst; }
+  __device__ __forceinline__ double unit(const TraceArgs& A) const { return A.src[src].unit; }
   __device__ __forceinline__ bool inside() const {
     return c0 >= 0 && c0 < nx && c1 >= 0 && c1 < ny && c2 >= 0 && c2 < nz;
   }
   // distance from the source to the next plane of cell c along an axis
-  __device__ __forceinline__ static F2 next_t(int c, F2 s, float sg, F2 iv) {
-    if (sg == 0.0f) return {__int_as_float(0x7f800000), 0.0f};
-    const float b = (float)(sg > 0.0f ? c + 1 : c);
-    const F2 d0 = two_sum(b, -s.hi);
-    const F2 d = fast_two_sum(d0.hi, __fsub_rn(d0.lo, s.lo));
+  __device__ __forceinline__ static F2 next_t(int c, float s_hi, float s_lo, F2 iv) {
+    if (iv.hi == 0.0f) return {__int_as_float(0x7f800000), 0.0f};
+    const float b = (float)(iv.hi > 0.0f ? c + 1 : c);
+    const F2 d0 = two_sum(b, -s_hi);
+    const F2 d = fast_two_sum(d0.hi, __fsub_rn(d0.lo, s_lo));
     return f2_mul(d, iv);
   }
   // cell of coordinate u along an axis (tie rule: n > 0 floor, n < 0 ceil - 1)
-  __device__ __forceinline__ static int cell_of(F2 u, float sg) {
+  __device__ __forceinline__ static int cell_of(F2 u, float n) {
     const int f = f2_floor(u);
-    if (sg < 0.0f && (float)f == u.hi && u.lo == 0.0f) return f - 1;
+    if (n < 0.0f && (float)f == u.hi && u.lo == 0.0f) return f - 1;
     return f;
   }
-  __device__ __forceinline__ float band(F2 t, float ab) const { return fmaf(t.hi, kBandT, ab); }
+  __device__ __forceinline__ float band(const TraceArgs& A, F2 t, int axis) const {
+    const float4 sa = __ldg(&A.src[src].sabs32);
+    const float ab = axis == 0 ? sa.x * fabsf(iv0.hi) : (axis == 1 ? sa.y * fabsf(iv1.hi) : sa.z * fabsf(iv2.hi));
+    return fmaf(t.hi, kBandT, ab);
+  }
 
   __device__ __forceinline__ bool start(const TraceArgs& A) {
     const SourceDev& S = A.src[src];
-    inst = S.inst;
-    local = S.local;
-    s0 = {S.s32[0], S.slo32[0]};
-    s1 = {S.s32[1], S.slo32[1]};
-    s2 = {S.s32[2], S.slo32[2]};
-    sdx = S.sdx32; w = S.w32; rw = S.rw32; heat = S.heat32; unit = S.unit;
-    const InstDev& I = A.inst[inst];
+    const float4 sh = __ldg(&S.s32);
+    const float4 sl = __ldg(&S.slo32);
+    const InstDev& I = A.inst[S.inst];
     nx = I.nx; ny = I.ny; nz = I.nz;
     nhi = (const float*)I.nhi;
     K = (float*)I.K;
     G = (float*)I.G;
     F2 n[3];
-    const int diag = dir_pair(A, (int)level, pix, n);
-    diag_exact = diag && S.exact32;
-    sg0 = n[0].hi > 0 ? 1.0f : (n[0].hi < 0 ? -1.0f : 0.0f);
-    sg1 = n[1].hi > 0 ? 1.0f : (n[1].hi < 0 ? -1.0f : 0.0f);
-    sg2 = n[2].hi > 0 ? 1.0f : (n[2].hi < 0 ? -1.0f : 0.0f);
-    iv0 = sg0 != 0.0f ? f2_recip(n[0]) : F2{0.0f, 0.0f};
-    iv1 = sg1 != 0.0f ? f2_recip(n[1]) : F2{0.0f, 0.0f};
-    iv2 = sg2 != 0.0f ? f2_recip(n[2]) : F2{0.0f, 0.0f};
-    ab0 = S.sabs32[0] * fabsf(iv0.hi);
-    ab1 = S.sabs32[1] * fabsf(iv1.hi);
-    ab2 = S.sabs32[2] * fabsf(iv2.hi);
-    c0 = cell_of(f2_add(s0, f2_mul(r, n[0])), sg0);
-    c1 = cell_of(f2_add(s1, f2_mul(r, n[1])), sg1);
-    c2 = cell_of(f2_add(s2, f2_mul(r, n[2])), sg2);
+    const int diag = dir_pair(A, lvl(), pix, n);
+    level = (level & 15u) | ((diag && sh.w != 0.0f) ? 256u : 0u);
+    iv0 = n[0].hi != 0.0f ? f2_recip(n[0]) : F2{0.0f, 0.0f};
+    iv1 = n[1].hi != 0.0f ? f2_recip(n[1]) : F2{0.0f, 0.0f};
+    iv2 = n[2].hi != 0.0f ? f2_recip(n[2]) : F2{0.0f, 0.0f};
+    c0 = cell_of(f2_add(F2{sh.x, sl.x}, f2_mul(r, n[0])), n[0].hi);
+    c1 = cell_of(f2_add(F2{sh.y, sl.y}, f2_mul(r, n[1])), n[1].hi);
+    c2 = cell_of(f2_add(F2{sh.z, sl.z}, f2_mul(r, n[2])), n[2].hi);
     Pstart = P;
     steps = 0;
     if (!inside()) return false;
-    t0 = next_t(c0, s0, sg0, iv0);
-    t1 = next_t(c1, s1, sg1, iv1);
-    t2 = next_t(c2, s2, sg2, iv2);
+    t0 = next_t(c0, sh.x, sl.x, iv0);
+    t1 = next_t(c1, sh.y, sl.y, iv1);
+    t2 = next_t(c2, sh.z, sl.z, iv2);
     return true;
   }
 
@@ -440,37 +466,26 @@ struct Walk32 {
     __stcg(&q->src, src);
     __stcg(&q->pix, cpix);
     __stcg(&q->r_lo, r.lo);
-    st_release_u32(&q->tag, (epoch << 4) | (level + 1));
+    st_release_u32(&q->tag, (epoch << 4) | (uint32_t)(lvl() + 1));
   }
+  // Poll with a relaxed load; only a successful poll pays for the fence that
+  // orders the payload reads after the tag (acquire loads in the polling loop
+  // were measurably slower).
   __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
-    const uint32_t tg = ld_acquire_u32(&q->tag);
+    const uint32_t tg = ld_relaxed_u32(&q->tag);
     if ((tg >> 4) != (epoch & 0x0fffffffu)) return false;
+    __threadfence();
     o.r = __ldcg(&q->r); o.P = __ldcg(&q->P); o.tau = __ldcg(&q->tau);
     o.tau_err = __ldcg(&q->tau_err); o.src = __ldcg(&q->src); o.pix = __ldcg(&q->pix);
     o.r_lo = __ldcg(&q->r_lo);
     o.tag = tg;
     return true;
   }
-  __device__ __forceinline__ void set_root(uint32_t gsrc, uint32_t lvl, uint32_t p) {
-    src = gsrc; level = lvl; pix = p; r = {0.0f, 0.0f}; P = 1.0f; tau = 0.0f; tau_err = 0.0f;
+  __device__ __forceinline__ void set_root(uint32_t gsrc, uint32_t l, uint32_t p) {
+    src = gsrc; level = l; pix = p; r = {0.0f, 0.0f}; P = 1.0f; tau = 0.0f; tau_err = 0.0f;
   }
   __device__ __forceinline__ void become_child0() {
-    level += 1; pix = 4u * pix; P = P * 0.25f;
-  }
-
-  // Exact (FP64) crossing decision for the current cell.
-  __device__ __noinline__ void decide64(const TraceArgs& A, bool& split, bool& m0, bool& m1, bool& m2) const {
-    const SourceDev& S = A.src[src];
-    double n[3];
-    pix2vec64((int)level, pix, n);
-    const double u0 = next_t64(c0, S.s[0], n[0]);
-    const double u1 = next_t64(c1, S.s[1], n[1]);
-    const double u2 = next_t64(c2, S.s[2], n[2]);
-    const double rn = fmin(u0, fmin(u1, u2));
-    split = (int)level < A.max_level && rn > A.rsplit[level];
-    m0 = n[0] != 0 && u0 == rn;
-    m1 = n[1] != 0 && u1 == rn;
-    m2 = n[2] != 0 && u2 == rn;
+    level = (uint32_t)(lvl() + 1); pix = 4u * pix; P = P * 0.25f;
   }
 
   __device__ __forceinline__ int step(const TraceArgs& A, LaneAcc& acc) {
@@ -479,103 +494,130 @@ struct Walk32 {
     F2 rn = t0;
     if (f2_less(t1, rn)) { rn = t1; imin = 1; }
     if (f2_less(t2, rn)) { rn = t2; imin = 2; }
-    const float emin = imin == 0 ? band(t0, ab0) : (imin == 1 ? band(t1, ab1) : band(t2, ab2));
     bool m0 = imin == 0, m1 = imin == 1, m2 = imin == 2;
     bool unsure = false;
-    const bool xy_tie = diag_exact && f2_eq(t0, t1);
-    if (imin != 0 && sg0 != 0.0f && f2_diff(t0, rn) <= band(t0, ab0) + emin) {
-      if (imin == 1 && xy_tie) m0 = true; else unsure = true;
-    }
-    if (imin != 1 && sg1 != 0.0f && f2_diff(t1, rn) <= band(t1, ab1) + emin) {
-      if (imin == 0 && xy_tie) m1 = true; else unsure = true;
-    }
-    if (imin != 2 && sg2 != 0.0f && f2_diff(t2, rn) <= band(t2, ab2) + emin) unsure = true;
-    bool split = false;
-    if ((int)level < A.max_level) {
-      const float d = f2_diff(rn, F2{A.rsplit32[level], A.rsplit32lo[level]});
-      const float bnd = emin + A.rsplit32[level] * kBandT;
-      if (d > bnd) split = true;
-      else if (!(-d > bnd)) unsure = true;
-    }
-    if (unsure) {
-      decide64(A, split, m0, m1, m2);
-      acc.fallbacks++;
+    const float close = fmaf(rn.hi, kClose, rn.hi) + 1e-30f;
+    const bool c_0 = imin != 0 && iv0.hi != 0.0f && t0.hi <= close;
+    const bool c_1 = imin != 1 && iv1.hi != 0.0f && t1.hi <= close;
+    const bool c_2 = imin != 2 && iv2.hi != 0.0f && t2.hi <= close;
+    const int l = lvl();
+    const float R = A.rsplit32[l];
+    const bool can_split = l < A.max_level;
+    const bool split_close = can_split && !(rn.hi > fmaf(R, kClose, R)) && !(rn.hi < fmaf(R, -kClose, R));
+    bool split = can_split && rn.hi > R;
+    if (c_0 || c_1 || c_2 || split_close) {
+      // a close pair: compare exactly, re-take the decision in FP64 if unprovable
+      const float emin = band(A, rn, imin);
+      const bool xy_tie = diag_exact() && f2_eq(t0, t1);
+      if (c_0 && f2_diff(t0, rn) <= band(A, t0, 0) + emin) { if (imin == 1 && xy_tie) m0 = true; else unsure = true; }
+      if (c_1 && f2_diff(t1, rn) <= band(A, t1, 1) + emin) { if (imin == 0 && xy_tie) m1 = true; else unsure = true; }
+      if (c_2 && f2_diff(t2, rn) <= band(A, t2, 2) + emin) unsure = true;
+      if (split_close) {
+        const float d = f2_diff(rn, F2{R, A.rsplit32lo[l]});
+        const float bnd = emin + R * kBandT;
+        if (d > bnd) split = true;
+        else if (-d > bnd) split = false;
+        else unsure = true;
+      }
+      if (unsure) {
+        const int d64 = decide64(A, src, l, pix, c0, c1, c2);
+        split = (d64 & 8) != 0;
+        m0 = (d64 & 1) != 0;
+        m1 = (d64 & 2) != 0;
+        m2 = (d64 & 4) != 0;
+        acc.fallbacks++;
+      }
     }
     if (split) return EV_SPLIT;
     float dr = f2_diff(rn, r);
     if (dr < 0.0f) dr = 0.0f;
     const int idx = c0 + nx * (c1 + ny * c2);
     const float nh = __ldg(&nhi[idx]);
-    const float kap = sdx * nh;
+    const float4 k32 = __ldg(&A.src[src].k32);  // sdx, w, rw, heat
+    const float kap = k32.x * nh;
     const float dtau = kap * dr;
-    const float am = -expm1f(-dtau);
-    const float phi = dtau > 0.0f ? am / dtau : 1.0f;
-    const float kadd = P * w * dr * phi;
+    // absorbed fraction am = 1 - e^-tau and transmitted fraction tr = e^-tau,
+    // each from the form that does not cancel
+    float am, tr;
+    if (dtau < 0.5f) { am = -expm1f(-dtau); tr = 1.0f - am; }
+    else { tr = expf(-dtau); am = 1.0f - tr; }
+    const float phi = dtau > 0.0f ? __fdividef(am, dtau) : 1.0f;
+    const float kadd = P * k32.y * dr * phi;
     atomicAdd(&K[idx], kadd);
-    if (heat != 0.0f) atomicAdd(&G[idx], kadd * heat);
-    if (dr > 0.0f) acc.segments++;
-    // P e^-tau, not P - dP: in FP32 the difference cancels when tau is large
-    P = P * expf(-dtau);
+    if (k32.w != 0.0f) atomicAdd(&G[idx], kadd * k32.w);
+    if (dr > 0.0f) nseg++;
+    P = P * tr;
     tau = tau + dtau;
-    // tau_FP32 - tau_FP64: rounding of kappa, dr and the sum, plus the pair error of dr
-    tau_err = tau_err + dtau * (8.0f * kEps32) + kap * (2.0f * emin + 1e-30f) + tau * (2.0f * kEps32);
+    // tau_FP32 - tau_FP64: roundings of kappa, dr and the sum, plus the pair
+    // error of dr (2 x 2^-40 rn, with margin)
+    tau_err = tau_err + dtau * (8.0f * kEps32) + kap * fmaf(rn.hi, 4.0f * kBandT, 1e-30f) + tau * (2.0f * kEps32);
     {
       const float d = tau - A.tau_term32;
       const float bnd = tau_err + A.tau_term32 * (4.0f * kEps32) + 1e-12f;
-      bool term;
-      if (d > bnd) term = true;
-      else if (-d > bnd) term = false;
-      else {
-        bool ok;
-        const double t64 = retrace_tau64(A, src, (int)level, pix, c0, c1, c2, &ok);
-        acc.fallbacks++;
-        term = ok ? (t64 > A.tau_term) : (d > 0.0f);
+      bool term = d > bnd;
+      if (!term && !(-d > bnd)) {
+        const double t64 = retrace_tau64(A, src, l, pix, c0, c1, c2);
+        acc.fallbacks_tau++;
+        term = isnan(t64) ? (d > 0.0f) : (t64 > A.tau_term);
       }
       if (term) {
         if (nh > 0.0f) {
-          const float kres = P * rw / nh;
+          const float kres = P * k32.z / nh;
           atomicAdd(&K[idx], kres);
-          if (heat != 0.0f) atomicAdd(&G[idx], kres * heat);
+          if (k32.w != 0.0f) atomicAdd(&G[idx], kres * k32.w);
         }
-        acc.absorbed += (double)Pstart * unit;
+        acc.absorbed += (double)Pstart * unit(A);
         return EV_DONE;
       }
     }
-    if (m0) { c0 += sg0 > 0 ? 1 : -1; t0 = next_t(c0, s0, sg0, iv0); }
-    if (m1) { c1 += sg1 > 0 ? 1 : -1; t1 = next_t(c1, s1, sg1, iv1); }
-    if (m2) { c2 += sg2 > 0 ? 1 : -1; t2 = next_t(c2, s2, sg2, iv2); }
+    if (m0 || m1 || m2) {
+      const float4 sh = __ldg(&A.src[src].s32);
+      const float4 sl = __ldg(&A.src[src].slo32);
+      if (m0) { c0 += iv0.hi > 0.0f ? 1 : -1; t0 = next_t(c0, sh.x, sl.x, iv0); }
+      if (m1) { c1 += iv1.hi > 0.0f ? 1 : -1; t1 = next_t(c1, sh.y, sl.y, iv1); }
+      if (m2) { c2 += iv2.hi > 0.0f ? 1 : -1; t2 = next_t(c2, sh.z, sl.z, iv2); }
+    }
     r = rn;
     if (!inside()) {
-      acc.absorbed += ((double)Pstart - (double)P) * unit;
-      acc.escaped += (double)P * unit;
+      const double u = unit(A);
+      acc.absorbed += ((double)Pstart - (double)P) * u;
+      acc.escaped += (double)P * u;
       return EV_DONE;
     }
     if (++steps > A.max_steps) {
       set_status(A.ctl, RT_ERR_STATE);
-      acc.absorbed += ((double)Pstart - (double)P) * unit;
-      acc.escaped += (double)P * unit;
+      const double u = unit(A);
+      acc.absorbed += ((double)Pstart - (double)P) * u;
+      acc.escaped += (double)P * u;
       return EV_DONE;
     }
     return EV_NONE;
   }
-  __device__ __forceinline__ void on_split(LaneAcc& acc) const {
-    acc.absorbed += ((double)Pstart - (double)P) * unit;
+  __device__ __forceinline__ void on_split(const TraceArgs& A, LaneAcc& acc) const {
+    acc.absorbed += ((double)Pstart - (double)P) * unit(A);
   }
-  __device__ __forceinline__ void on_start_outside(LaneAcc& acc) const { acc.escaped += (double)P * unit; }
+  __device__ __forceinline__ void on_start_outside(const TraceArgs& A, LaneAcc& acc) const {
+    acc.escaped += (double)P * unit(A);
+  }
 };
 
 // ---------------------------------------------------------------------------
 // The persistent kernel, generic over the walker.
 // ---------------------------------------------------------------------------
-template <class W>
-__global__ void __launch_bounds__(256) trace_kernel(TraceArgs A) {
+template <class W, int MinBlocks>
+__global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   using Rec = typename W::Rec;
   __shared__ unsigned int sh_cnt[kShInst * kLevels];
   __shared__ unsigned long long sh_hsh[kShInst * kLevels];
+  __shared__ LaneAcc sh_acc[kBlock];
   for (int i = threadIdx.x; i < kShInst * kLevels; i += blockDim.x) {
     sh_cnt[i] = 0;
     sh_hsh[i] = 0;
   }
+  LaneAcc& acc = sh_acc[threadIdx.x];
+  acc.emitted = acc.absorbed = acc.escaped = 0.0;
+  acc.segments = acc.fallbacks = acc.fallbacks_tau = 0;
+  acc.inst = -1;
   __syncthreads();
   LevelCounters LC{sh_cnt, sh_hsh};
 
@@ -585,9 +627,9 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A) {
   Rec* queue = (Rec*)A.queue;
 
   W w;
+  w.nseg = 0;
   bool active = false;
   long long ticket = -1;
-  LaneAcc acc{-1, 0.0, 0.0, 0.0, 0u, 0u};
   long long seen_out = -1;
   uint64_t seen_ns = global_ns();
 
@@ -613,7 +655,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A) {
         w.set_root(gsrc, (uint32_t)A.level0, p);
         got = true;
         const SourceDev& S = A.src[gsrc];
-        acc_switch(acc, S.inst, A);
+        acc_switch(acc, w.nseg, S.inst, A);
         acc.emitted += S.unit;
         LC.add(A, S.inst, S.local, A.level0, p);
       } else {
@@ -629,12 +671,10 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A) {
       if (got) {
         ticket = -1;
         active = true;
+        acc_switch(acc, w.nseg, w.inst(A), A);
         if (!w.start(A)) {
-          acc_switch(acc, w.inst, A);
-          w.on_start_outside(acc);
+          w.on_start_outside(A, acc);
           ev = EV_DONE;
-        } else {
-          acc_switch(acc, w.inst, A);
         }
       }
     }
@@ -642,7 +682,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A) {
     const unsigned am = __ballot_sync(kFull, active && ev == EV_NONE);
     if (am == 0 && __ballot_sync(kFull, ev == EV_DONE) == 0) {
       long long outst = 0;
-      if (lane == 0) outst = ld_acquire_s64(&A.ctl[CTL_OUTSTANDING]);
+      if (lane == 0) outst = (long long)ld_relaxed_u64(&A.ctl[CTL_OUTSTANDING]);
       outst = __shfl_sync(kFull, outst, 0);
       if (outst <= 0) break;
       const uint64_t now = global_ns();
@@ -682,10 +722,11 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A) {
       }
       base = __shfl_sync(kFull, base, leader);
       if (split) {
-        w.on_split(acc);
+        w.on_split(A, acc);
         const unsigned long long my = base + 3ULL * __popc(sm & lt_mask);
-        const uint32_t cl = w.level + 1;
-        for (uint32_t k = 0; k < 4; ++k) LC.add(A, w.inst, w.local, (int)cl, 4u * w.pix + k);
+        const SourceDev& S = A.src[w.src];
+        const int cl = w.lvl() + 1;
+        for (uint32_t k = 0; k < 4; ++k) LC.add(A, S.inst, S.local, cl, 4u * w.pix + k);
         unsigned dropped = 0;
         for (uint32_t k = 1; k < 4; ++k) {
           const unsigned long long slot = my + (k - 1);
@@ -699,7 +740,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A) {
         w.become_child0();
         if (w.start(A)) ev = EV_NONE;
         else {
-          w.on_start_outside(acc);
+          w.on_start_outside(A, acc);
           ev = EV_DONE;
         }
       }
@@ -713,6 +754,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A) {
       if (done) active = false;
     }
   }
+  acc.segments += w.nseg;
   acc_flush(acc, A);
   __syncthreads();
   for (int i = threadIdx.x; i < kShInst * kLevels; i += blockDim.x) {
@@ -740,33 +782,23 @@ cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_root
   return cudaGetLastError();
 }
 
+constexpr int kMinBlocks64 = 2;
+constexpr int kMinBlocks32 = TRACE_MIN_BLOCKS;
+
 cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm) {
+  if (block != kBlock) return cudaErrorInvalidValue;
   if (precision == RT_FP64)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<Walk64>, block, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<Walk32>, block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<Walk64, kMinBlocks64>,
+                                                         block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<Walk32, kMinBlocks32>, block,
+                                                       0);
 }
 
 cudaError_t launch_trace(int precision, const TraceArgs& A, int grid, int block, cudaStream_t st) {
-  if (precision == RT_FP64) trace_kernel<Walk64><<<grid, block, 0, st>>>(A);
-  else trace_kernel<Walk32><<<grid, block, 0, st>>>(A);
+  if (block != kBlock) return cudaErrorInvalidValue;
+  if (precision == RT_FP64) trace_kernel<Walk64, kMinBlocks64><<<grid, block, 0, st>>>(A);
+  else trace_kernel<Walk32, kMinBlocks32><<<grid, block, 0, st>>>(A);
   return cudaGetLastError();
-}
-
-// Self-check of the FP32 direction bound: max over the pixels of `level` of
-// max_i |n32_i - n64_i|, written to out[0] (as the bit pattern of a positive
-// double, so atomicMax on the integer view orders it correctly).
-__global__ void direction_error_kernel(int level, unsigned long long* out) {
-  const unsigned long long npix = 12ULL << (2 * level);
-  double worst = 0.0;
-  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < npix;
-       p += (unsigned long long)gridDim.x * blockDim.x) {
-    double n64[3];
-    float n32[3];
-    pix2vec64(level, (uint32_t)p, n64);
-    pix2vec32(level, (uint32_t)p, n32);
-    for (int i = 0; i < 3; ++i) worst = fmax(worst, fabs((double)n32[i] - n64[i]));
-  }
-  atomicMax(out, (unsigned long long)__double_as_longlong(worst));
 }
 
 // Direction table: for each pixel of levels 0..L (level l starts at entry
@@ -792,6 +824,23 @@ __global__ void direction_table_kernel(int level, float4* tab) {
 cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st) {
   direction_table_kernel<<<152 * 8, 256, 0, st>>>(level, tab);
   return cudaGetLastError();
+}
+
+// Self-check of the FP32 direction bound: max over the pixels of `level` of
+// max_i |n32_i - n64_i|, written to out[0] (as the bit pattern of a positive
+// double, so atomicMax on the integer view orders it correctly).
+__global__ void direction_error_kernel(int level, unsigned long long* out) {
+  const unsigned long long npix = 12ULL << (2 * level);
+  double worst = 0.0;
+  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < npix;
+       p += (unsigned long long)gridDim.x * blockDim.x) {
+    double n64[3];
+    float n32[3];
+    pix2vec64(level, (uint32_t)p, n64);
+    pix2vec32(level, (uint32_t)p, n32);
+    for (int i = 0; i < 3; ++i) worst = fmax(worst, fabs((double)n32[i] - n64[i]));
+  }
+  atomicMax(out, (unsigned long long)__double_as_longlong(worst));
 }
 
 cudaError_t launch_direction_check(int level, unsigned long long* out, cudaStream_t st) {

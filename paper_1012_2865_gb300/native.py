@@ -52,7 +52,7 @@ class rt_grid_desc(ctypes.Structure):
 class rt_trace_params(ctypes.Structure):
     _fields_ = [("level0", ctypes.c_int), ("phi_c", ctypes.c_double), ("f_term", ctypes.c_double),
                 ("max_level", ctypes.c_int), ("queue_capacity", ctypes.c_int64),
-                ("timeout_s", ctypes.c_double), ("block_threads", ctypes.c_int),
+                ("timeout_s", ctypes.c_double), ("blocks_per_sm", ctypes.c_int),
                 ("segs_per_iter", ctypes.c_int)]
 
 
@@ -60,7 +60,8 @@ class rt_budget(ctypes.Structure):
     _fields_ = [("emitted", ctypes.c_double), ("absorbed", ctypes.c_double),
                 ("escaped", ctypes.c_double), ("counts", ctypes.c_uint64 * NLEV),
                 ("hashes", ctypes.c_uint64 * NLEV), ("segments", ctypes.c_uint64),
-                ("fallbacks", ctypes.c_uint64), ("queue_pushed", ctypes.c_uint64),
+                ("fallbacks", ctypes.c_uint64), ("fallbacks_tau", ctypes.c_uint64),
+                ("queue_pushed", ctypes.c_uint64),
                 ("status", ctypes.c_int), ("kernel_ms", ctypes.c_float)]
 
 
@@ -173,9 +174,9 @@ def rt_clear_sources(grid):
 
 
 def trace_params(level0=1, phi_c=5.1, f_term=1e-10, max_level=RT_MAX_LEVEL, queue_capacity=0,
-                 timeout_s=2.0, block_threads=0, segs_per_iter=0) -> rt_trace_params:
+                 timeout_s=2.0, blocks_per_sm=0, segs_per_iter=0) -> rt_trace_params:
     return rt_trace_params(int(level0), float(phi_c), float(f_term), int(max_level),
-                           int(queue_capacity), float(timeout_s), int(block_threads),
+                           int(queue_capacity), float(timeout_s), int(blocks_per_sm),
                            int(segs_per_iter))
 
 
@@ -183,7 +184,8 @@ def budget_dict(b: rt_budget) -> dict:
     return dict(emitted=b.emitted, absorbed=b.absorbed, escaped=b.escaped,
                 counts=np.array(b.counts[:], dtype=np.uint64),
                 hashes=np.array(b.hashes[:], dtype=np.uint64), segments=int(b.segments),
-                fallbacks=int(b.fallbacks), queue_pushed=int(b.queue_pushed), status=int(b.status),
+                fallbacks=int(b.fallbacks), fallbacks_tau=int(b.fallbacks_tau),
+                queue_pushed=int(b.queue_pushed), status=int(b.status),
                 kernel_ms=float(b.kernel_ms))
 
 

@@ -38,6 +38,16 @@ BASE_SEED = 20101
 DEFAULT_PARAMS = dict(level0=1, phi_c=5.1, f_term=1e-10, max_level=14)
 
 
+def box_cm(N: int, box_kpc: float = 6.6) -> float:
+    """Box length near box_kpc whose cell width box/N has at most 20 significant
+    bits, so every cell centre (i + 1/2) dx is an exact double and divides back
+    to exactly i + 1/2 (the relative change of the box is below 1e-6)."""
+    dx = box_kpc * KPC_CM / N
+    e = np.floor(np.log2(dx)) - 19
+    dx = np.round(dx / 2.0 ** e) * 2.0 ** e
+    return float(dx * N)
+
+
 def round_f32(a) -> np.ndarray:
     """float64 array whose values are exactly representable in FP32."""
     return np.asarray(a, dtype=np.float32).astype(np.float64)
@@ -81,7 +91,7 @@ def _grid(N, box_len_cm, n_H, x_HI, pos_cm, ndot, e_ph, sigma, **extra):
 
 def stromgren(N: int = 128, box_kpc: float = 6.6, n_H: float = 1e-3, ndot: float = 5e48) -> dict:
     """Test 1 (Sec. 4.1) on an N^3 grid; source at the domain corner."""
-    return _grid(N, box_kpc * KPC_CM, n_H, 1.0, [[0.0, 0.0, 0.0]], [ndot], [13.6], [SIGMA_HI],
+    return _grid(N, box_cm(N, box_kpc), n_H, 1.0, [[0.0, 0.0, 0.0]], [ndot], [13.6], [SIGMA_HI],
                  alpha_B=ALPHA_B)
 
 
@@ -144,7 +154,7 @@ def random_sources(dims, dx: float, nsrc: int, ndot_lo: float, ndot_hi: float, r
 def clumpy(N: int = 256, nsrc: int = 1000, seed: int = BASE_SEED + 2, box_kpc: float = 6.6) -> dict:
     """Clumpy multi-source medium (log-normal density, many sources)."""
     rng = np.random.default_rng(seed)
-    box = box_kpc * KPC_CM
+    box = box_cm(N, box_kpc)
     dx = box / N
     n = lognormal_density(N, seed=seed)
     pos, ndot, e, sg = random_sources((N, N, N), dx, nsrc, 1e48, 1e50, rng)
@@ -162,7 +172,7 @@ def batch(n_inst: int = 64, seed: int = BASE_SEED + 3, box_kpc: float = 6.6,
     for i in range(n_inst):
         N = int(rng.choice(BATCH_SIDES))
         nsrc = int(rng.integers(1, max_src + 1))
-        box = box_kpc * KPC_CM
+        box = box_cm(N, box_kpc)
         n = lognormal_density(N, seed=seed * 1000 + i)
         pos, ndot, e, sg = random_sources((N, N, N), box / N, nsrc, 1e47, 1e50, rng)
         out.append(_grid(N, box, n, 1.0, pos, ndot, e, sg, alpha_B=ALPHA_B))
@@ -191,7 +201,7 @@ def request_grid(req: dict, box_kpc: float = 6.6) -> dict:
     """Materialise the grid of one request from the stream."""
     rng = np.random.default_rng(req["seed"])
     N = req["N"]
-    box = box_kpc * KPC_CM
+    box = box_cm(N, box_kpc)
     n = lognormal_density(N, seed=req["seed"])
     pos, ndot, e, sg = random_sources((N, N, N), box / N, req["nsrc"], 1e47, 1e50, rng)
     return _grid(N, box, n, 1.0, pos, ndot, e, sg, alpha_B=ALPHA_B)
