@@ -162,6 +162,49 @@ int rt_get_ionised(rt_grid* grid, void* x_HII, int dtype, int mem_kind);
  * assume (*bound may be NULL).  Synchronous. */
 int rt_selfcheck_directions(rt_ctx* ctx, int level, double* max_abs_err, double* bound);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free trace.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- applications
+ * whose device memory is owned by a host framework (an arena or a caching
+ * allocator with a fixed budget) and callers that must not let cudaMalloc or
+ * cudaFree synchronise the device or change its memory footprint.
+ *
+ * It runs the same FP32-mixed trace as rt_trace on a grid the caller holds in
+ * device memory, and keeps all scratch (package queue, control words, budget
+ * sums, source records, a table of pixel directions) in one static device
+ * array of about 10 MiB that every device loading the library holds until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Limits: at most RT_NOALLOC_MAX_SOURCES sources and
+ * RT_NOALLOC_MAX_RECORDS queue records per call (a larger trace returns
+ * RT_ERR_QUEUE_OVERFLOW); queue_capacity, if set, must not exceed the latter.
+ *
+ * Every call shares the static array, and each call clears what must start
+ * at zero; calls whose work overlaps on the GPU (other streams or host
+ * threads) race on it and must be serialised by the caller.  The first call
+ * on a device sets that device up (finds the array's device address, fills
+ * the direction table) and synchronises the device: make it before any
+ * stream capture.  The call is synchronous: it waits for the trace on
+ * `stream` (cudaStream_t as void*, NULL = legacy default stream) and fills
+ * *out.  Errors: rt_noalloc_last_error() gives the message.
+ * ------------------------------------------------------------------------- */
+#define RT_NOALLOC_MAX_SOURCES 1024
+#define RT_NOALLOC_MAX_RECORDS 262144
+
+typedef struct {
+  int nx, ny, nz;        /* cells per axis, as in rt_grid_desc */
+  double box_len_cm;     /* x extent of the box */
+  const float* n_HI;     /* device [ncell]: FP32 rounding of n_H * x_HI */
+  const double* n_H;     /* device [ncell]: hydrogen density (FP64 decisions) */
+  const double* x_HI;    /* device [ncell]: neutral fraction (FP64 decisions) */
+  float* kph;            /* device [ncell] output: k_ph, s^-1 (overwritten) */
+  float* gamma;          /* device [ncell] output: Gamma, erg/s (overwritten) */
+} rt_noalloc_grid;
+
+int rt_trace_noalloc(const rt_noalloc_grid* grid, int nsrc, const double* pos_cm, const double* ndot,
+                     const double* e_ph_eV, const double* sigma_cm2, const rt_trace_params* params,
+                     void* stream, rt_budget* out);
+const char* rt_noalloc_last_error(void);
+
 /* Wait for all work enqueued on the grid's stream. */
 int rt_synchronize(rt_grid* grid);
 

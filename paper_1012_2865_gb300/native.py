@@ -65,6 +65,12 @@ class rt_budget(ctypes.Structure):
                 ("status", ctypes.c_int), ("kernel_ms", ctypes.c_float)]
 
 
+class rt_noalloc_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("box_len_cm", ctypes.c_double), ("n_HI", ctypes.c_void_p), ("n_H", ctypes.c_void_p),
+                ("x_HI", ctypes.c_void_p), ("kph", ctypes.c_void_p), ("gamma", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -94,6 +100,9 @@ def lib():
             "rt_selfcheck_directions": ([vp, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
             "rt_kernel_launches": ([], ctypes.c_uint64),
             "rt_get_last_error": ([], ctypes.c_char_p),
+            "rt_trace_noalloc": ([ctypes.POINTER(rt_noalloc_grid), i, vp, vp, vp, vp,
+                                  ctypes.POINTER(rt_trace_params), vp, ctypes.POINTER(rt_budget)], i),
+            "rt_noalloc_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -291,3 +300,22 @@ class Grid:
             self.close()
         except Exception:
             pass
+
+
+def rt_trace_noalloc(dims, box_len_cm, n_HI, n_H, x_HI, kph, gamma, pos_cm, ndot, e_ph_eV, sigma_cm2,
+                     params: rt_trace_params, stream=None) -> dict:
+    """Allocation-free trace; every grid array is a CUDA tensor (n_HI, kph, gamma float32)."""
+    nx, ny, nz = (int(v) for v in dims)
+    g = rt_noalloc_grid(nx, ny, nz, float(box_len_cm), n_HI.data_ptr(), n_H.data_ptr(), x_HI.data_ptr(),
+                        kph.data_ptr(), gamma.data_ptr())
+    pos = np.ascontiguousarray(pos_cm, dtype=np.float64).reshape(-1)
+    nd = np.ascontiguousarray(ndot, dtype=np.float64).reshape(-1)
+    e = np.ascontiguousarray(e_ph_eV, dtype=np.float64).reshape(-1)
+    sg = np.ascontiguousarray(sigma_cm2, dtype=np.float64).reshape(-1)
+    b = rt_budget()
+    code = lib().rt_trace_noalloc(ctypes.byref(g), nd.size, pos.ctypes.data, nd.ctypes.data, e.ctypes.data,
+                                  sg.ctypes.data, ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                                  ctypes.byref(b))
+    if code != RT_OK:
+        raise RtError(code, lib().rt_noalloc_last_error().decode(errors="replace"))
+    return budget_dict(b)
