@@ -83,7 +83,9 @@ typedef struct {
   int blocks_per_sm;     /* resident 256-thread blocks of the trace kernel per SM;
                             0 = as many as fit (lower it to share the GPU) */
   int segs_per_iter;     /* segments a lane traces between queue visits; 0 = tuned */
+  int flags;             /* RT_TRACE_CHECKSUMS: also fill rt_budget.hashes */
 } rt_trace_params;
+#define RT_TRACE_CHECKSUMS 1
 
 /* Result of a trace, per grid. */
 typedef struct {
@@ -92,7 +94,8 @@ typedef struct {
   double escaped;                      /* photons/s leaving the box */
   uint64_t counts[RT_MAX_LEVEL + 1];   /* packages created per HEALPix level */
   uint64_t hashes[RT_MAX_LEVEL + 1];   /* order-free checksum of the created
-                                          (source, level, pixel) set, see below */
+                                          (source, level, pixel) set, see below;
+                                          0 unless RT_TRACE_CHECKSUMS is set */
   uint64_t segments;                   /* cell segments with length > 0 */
   uint64_t fallbacks;                  /* FP32 crossing/split decisions re-taken in FP64 */
   uint64_t fallbacks_tau;              /* FP32 termination decisions re-taken in FP64 */
@@ -155,6 +158,42 @@ int rt_set_state(rt_grid* grid, const double* n_H, const double* x_HI, const dou
 int rt_get_rates(rt_grid* grid, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind);
 /* Copy x_HII likewise. */
 int rt_get_ionised(rt_grid* grid, void* x_HII, int dtype, int mem_kind);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many grids traced by one persistent launch that shares one
+ * package queue (Steps 1-5 for every grid at once), and one launch of the
+ * ionisation update (Step 6) for every grid.  Each grid keeps its own fields,
+ * photon budget and counters; results equal those of the grid traced alone
+ * (up to the order of floating-point sums).  All grids of a batch have the
+ * same precision and context; while a grid is in a batch, use it only
+ * through the batch (its own stream is not used).
+ * ------------------------------------------------------------------------- */
+/* stream: cudaStream_t for the batch's work; NULL = the batch creates its own
+ * (a blocking stream).  Per-grid calls on a grid in a batch wait for the
+ * batch's stream first. */
+int rt_batch_create(rt_ctx* ctx, void* stream, rt_batch** out);
+int rt_batch_destroy(rt_batch* batch);
+/* Add a grid; *slot receives its slot number (reused after removal). */
+int rt_batch_add(rt_batch* batch, rt_grid* grid, int* slot);
+int rt_batch_remove(rt_batch* batch, int slot);
+/* Number of grids in the batch. */
+int rt_batch_size(rt_batch* batch);
+/* One trace of every grid (as rt_trace; sync != 0 waits and retries a queue
+ * overflow with a larger queue). */
+int rt_batch_trace(rt_batch* batch, const rt_trace_params* params, int sync);
+/* Ionisation update of every grid (as rt_chem_update).  Asynchronous. */
+int rt_batch_chem(rt_batch* batch, double dt_s, int nsub, double alpha_B);
+/* nsteps coupled steps (trace, then update) of every grid.  One step is
+ * captured once as a CUDA graph (after a synchronous sizing trace) and
+ * replayed; it is captured again when the grids or arguments change.
+ * Asynchronous after the capture. */
+int rt_batch_step(rt_batch* batch, const rt_trace_params* params, double dt_s, int nsub, double alpha_B,
+                  int nsteps);
+/* Result of the last trace for the grid in `slot` (synchronises). */
+int rt_batch_get_budget(rt_batch* batch, int slot, rt_budget* out);
+/* Pick segs_per_iter and blocks_per_sm for this batch by timing traces
+ * (CUDA events); writes them into *params. */
+int rt_batch_autotune(rt_batch* batch, rt_trace_params* params);
 
 /* Self-check of the FP32-mixed path's direction bound: the largest
  * |n32_i - n64_i| over all pixel centres of `level` (HEALPix, Step 3a),

@@ -28,6 +28,9 @@ cudaError_t launch_convert(long long n, const void* src, int src_dtype, void* ds
 cudaError_t launch_complement(long long n, const double* x, double* out, cudaStream_t st);
 cudaError_t launch_direction_check(int level, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st);
+cudaError_t launch_batch_zero(const InstDev* inst, int ninst, int precision, long long max_cells, cudaStream_t st);
+cudaError_t launch_batch_chem(const InstDev* inst, int ninst, int precision, long long max_cells, double h,
+                              int nsub, double alpha, cudaStream_t st);
 }  // namespace rtg
 
 using namespace rtg;
@@ -133,6 +136,7 @@ struct rt_grid {
   void* host_rb = nullptr;
   bool traced = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last trace kernel
+  cudaStream_t batch_stream = nullptr;       // set while the grid is in a batch
   ~rt_grid() {
     cudaFree(nH); cudaFree(xHI); cudaFree(xHII); cudaFree(nhi); cudaFree(K); cudaFree(G);
     cudaFree(acc); cudaFree(cnt); cudaFree(inst_dev); cudaFree(src_dev);
@@ -143,6 +147,13 @@ struct rt_grid {
 };
 
 static size_t elem_bytes(int precision) { return precision == RT_FP64 ? 8 : 4; }
+
+// A grid in a batch is updated on the batch's stream: per-grid calls first
+// wait for that work.
+static int wait_batch(rt_grid* g) {
+  if (g->batch_stream) CUDA_TRY(cudaStreamSynchronize(g->batch_stream));
+  return RT_OK;
+}
 
 extern "C" {
 
@@ -242,7 +253,8 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
   if (e == cudaSuccess) e = cudaMemsetAsync(g->G, 0, ne, st);
   InstDev I;
   I.nx = g->nx; I.ny = g->ny; I.nz = g->nz; I.pad = 0;
-  I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.K = g->K; I.G = g->G; I.acc = g->acc; I.cnt = g->cnt;
+  I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.xHII = g->xHII; I.K = g->K; I.G = g->G; I.acc = g->acc;
+  I.cnt = g->cnt;
   if (e == cudaSuccess) e = cudaMemcpy(g->inst_dev, &I, sizeof I, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMallocHost(&g->host_rb, 4096);
   if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
@@ -256,6 +268,7 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
 
 int rt_grid_destroy(rt_grid* g) {
   if (!g) return RT_OK;
+  wait_batch(g);
   cudaStreamSynchronize(g->stream);
   delete g;
   return RT_OK;
@@ -303,23 +316,22 @@ int rt_clear_sources(rt_grid* g) {
 // offsets stay at least 1/16 apart.
 static bool exact_in_f32(double v) { return v == ldexp(floor(ldexp(v, 4)), -4) && fabs(v) <= 4096.0; }
 
-// Build the per-source device table for a given initial level.
-static int prepare_sources(rt_grid* g, int level0) {
-  if (!g->src_dirty && g->last_level0 == level0) return RT_OK;
+// Source records of grid g for a given initial level (Step 1: Ndot spread
+// over 12 * 4^level0 root packages), attributed to instance slot `inst`.
+static void build_sources(const rt_grid* g, int level0, int inst, std::vector<SourceDev>& v) {
   const double npix0 = 12.0 * ldexp(1.0, 2 * level0);
-  std::vector<SourceDev> v(g->src.size());
   const double dx = g->dx, vol = dx * dx * dx;
-  for (size_t i = 0; i < v.size(); ++i) {
+  for (size_t i = 0; i < g->src.size(); ++i) {
     const rt_grid::SrcIn& H = g->src[i];
     SourceDev S;
     memset(&S, 0, sizeof S);
     for (int a = 0; a < 3; ++a) S.s[a] = H.pos[a] / dx;  // cell units
     S.sdx = H.sigma * dx;
     S.heat = (H.e_ph - kEHI) * kEvErg;
-    S.unit = H.ndot / npix0;  // Step 1: luminosity spread equally over N_pix
+    S.unit = H.ndot / npix0;
     S.w = S.unit * H.sigma / (dx * dx);
     S.rw = S.unit / vol;
-    S.inst = 0;
+    S.inst = inst;
     S.local = (int)i;
     int exact = 1;
     float s32[3], slo[3], sab[3];
@@ -335,8 +347,15 @@ static int prepare_sources(rt_grid* g, int level0) {
     S.s32 = make_float4(s32[0], s32[1], s32[2], S.exact32 ? 1.0f : 0.0f);
     S.slo32 = make_float4(slo[0], slo[1], slo[2], 0.0f);
     S.sabs32 = make_float4(sab[0], sab[1], sab[2], 0.0f);
-    v[i] = S;
+    v.push_back(S);
   }
+}
+
+// Build the per-source device table of a single grid for a given initial level.
+static int prepare_sources(rt_grid* g, int level0) {
+  if (!g->src_dirty && g->last_level0 == level0) return RT_OK;
+  std::vector<SourceDev> v;
+  build_sources(g, level0, 0, v);
   if (v.size() > g->src_dev_cap) {
     if (g->src_dev) cudaFree(g->src_dev);
     g->src_dev = nullptr;
@@ -434,6 +453,7 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p) {
   A.timeout_ns = (long long)((p->timeout_s > 0 ? p->timeout_s : 2.0) * 1e9);
   A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 8;
   A.max_steps = 2 * (g->nx + g->ny + g->nz) + 16;
+  A.checksums = (p->flags & RT_TRACE_CHECKSUMS) != 0;
   const int block = 256;  // the trace kernel is compiled for 256-thread blocks
   int per_sm = 0;
   CUDA_TRY(trace_occupancy(g->precision, block, &per_sm));
@@ -476,6 +496,7 @@ static int read_budget(rt_grid* g, rt_budget* out) {
 
 int rt_trace(rt_grid* g, const rt_trace_params* p, rt_budget* out) {
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_trace: grid is NULL");
+  if (int rcw = wait_batch(g)) return rcw;
   int rc = check_params(p);
   if (rc) return rc;
   CUDA_TRY(cudaSetDevice(g->ctx->device));
@@ -509,6 +530,7 @@ int rt_trace(rt_grid* g, const rt_trace_params* p, rt_budget* out) {
 
 int rt_get_budget(rt_grid* g, rt_budget* out) {
   if (!g || !out) return fail(RT_ERR_INVALID_ARG, "rt_get_budget: NULL argument");
+  if (int rcw = wait_batch(g)) return rcw;
   int rc = read_budget(g, out);
   if (rc) return rc;
   if (out->status != RT_OK) return fail(out->status, "rt_get_budget: device status %d", out->status);
@@ -517,6 +539,7 @@ int rt_get_budget(rt_grid* g, rt_budget* out) {
 
 int rt_chem_update(rt_grid* g, double dt_s, int nsub, double alpha_B) {
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_chem_update: grid is NULL");
+  if (int rcw = wait_batch(g)) return rcw;
   if (!(dt_s >= 0) || !isfinite(dt_s)) return fail(RT_ERR_INVALID_ARG, "rt_chem_update: dt_s = %g", dt_s);
   if (nsub < 1) return fail(RT_ERR_INVALID_ARG, "rt_chem_update: nsub = %d", nsub);
   if (!(alpha_B >= 0) || !isfinite(alpha_B)) return fail(RT_ERR_INVALID_ARG, "rt_chem_update: alpha_B = %g", alpha_B);
@@ -528,6 +551,7 @@ int rt_chem_update(rt_grid* g, double dt_s, int nsub, double alpha_B) {
 
 int rt_set_state(rt_grid* g, const double* n_H, const double* x_HI, const double* x_HII, int mem_kind) {
   if (!g || !x_HI) return fail(RT_ERR_INVALID_ARG, "rt_set_state: grid and x_HI are required");
+  if (int rcw = wait_batch(g)) return rcw;
   if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE) return fail(RT_ERR_INVALID_ARG, "rt_set_state: mem_kind %d", mem_kind);
   const long long ncell = g->ncell;
   if (mem_kind == RT_MEM_HOST) {
@@ -575,6 +599,7 @@ static int copy_field(rt_grid* g, const void* src, int src_dtype, void* dst, int
 
 int rt_get_rates(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind) {
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_get_rates: grid is NULL");
+  if (int rcw = wait_batch(g)) return rcw;
   if (dtype != RT_DTYPE_F64 && dtype != RT_DTYPE_F32) return fail(RT_ERR_INVALID_ARG, "rt_get_rates: dtype %d", dtype);
   if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE) return fail(RT_ERR_INVALID_ARG, "rt_get_rates: mem_kind %d", mem_kind);
   CUDA_TRY(cudaSetDevice(g->ctx->device));
@@ -589,6 +614,7 @@ int rt_get_rates(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype, int 
 
 int rt_get_ionised(rt_grid* g, void* x_HII, int dtype, int mem_kind) {
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_get_ionised: grid is NULL");
+  if (int rcw = wait_batch(g)) return rcw;
   if (dtype != RT_DTYPE_F64 && dtype != RT_DTYPE_F32) return fail(RT_ERR_INVALID_ARG, "rt_get_ionised: dtype %d", dtype);
   if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE) return fail(RT_ERR_INVALID_ARG, "rt_get_ionised: mem_kind %d", mem_kind);
   CUDA_TRY(cudaSetDevice(g->ctx->device));
@@ -620,7 +646,463 @@ int rt_selfcheck_directions(rt_ctx* ctx, int level, double* max_abs_err, double*
 
 int rt_synchronize(rt_grid* g) {
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_synchronize: grid is NULL");
+  if (int rcw = wait_batch(g)) return rcw;
   CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return RT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many grids traced by one persistent launch (one global queue; each
+// grid keeps its own fields, budget and counters).
+// ---------------------------------------------------------------------------
+struct rt_batch {
+  rt_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int precision = -1;
+  std::vector<rt_grid*> slots;  // nullptr = free slot
+  // device tables of the active grids (compact, in slot order)
+  std::vector<int> dev_slot;    // device instance index -> slot
+  InstDev* inst_dev = nullptr;
+  size_t inst_cap = 0;
+  SourceDev* src_dev = nullptr;
+  size_t src_cap = 0;
+  int nsrc = 0;
+  unsigned long long n_roots = 0;
+  long long max_cells = 0;
+  int max_dims = 0;
+  double max_diag = 0;
+  bool dirty = true;
+  int built_level0 = -1;
+  TraceState ts;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool traced = false;
+  void* host_rb = nullptr;
+  // captured step graph and the arguments it was captured with
+  cudaGraphExec_t graph = nullptr;
+  bool graph_ok = false;
+  rt_trace_params gp;
+  double g_dt = 0, g_alpha = 0;
+  int g_nsub = 0;
+  ~rt_batch() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (inst_dev) cudaFree(inst_dev);
+    if (src_dev) cudaFree(src_dev);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (host_rb) cudaFreeHost(host_rb);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+static void fill_common_args(TraceArgs& A, const rt_trace_params* p) {
+  for (int l = 0; l < kLevels; ++l) {
+    // Eq. "split": Phi = N_pix dx^2 / (4 pi R^2) < Phi_c  <=>  R > R_split(l)
+    A.rsplit[l] = sqrt((12.0 * ldexp(1.0, 2 * l)) / (4.0 * M_PI * p->phi_c));
+    A.rsplit32[l] = (float)A.rsplit[l];
+    A.rsplit32lo[l] = (float)(A.rsplit[l] - (double)A.rsplit32[l]);
+  }
+  A.level0 = p->level0;
+  A.max_level = p->max_level;
+  A.tau_term = -log(p->f_term);
+  A.tau_term32 = (float)A.tau_term;
+  A.timeout_ns = (long long)((p->timeout_s > 0 ? p->timeout_s : 2.0) * 1e9);
+  A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 8;
+  A.checksums = (p->flags & RT_TRACE_CHECKSUMS) != 0;
+}
+
+static int batch_rebuild(rt_batch* b, int level0) {
+  if (!b->dirty && b->built_level0 == level0) return RT_OK;
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  std::vector<InstDev> inst;
+  std::vector<SourceDev> src;
+  b->dev_slot.clear();
+  b->max_cells = 0;
+  b->max_dims = 0;
+  double diag = 0;
+  for (size_t s = 0; s < b->slots.size(); ++s) {
+    rt_grid* g = b->slots[s];
+    if (!g) continue;
+    InstDev I;
+    memset(&I, 0, sizeof I);
+    I.nx = g->nx; I.ny = g->ny; I.nz = g->nz;
+    I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.xHII = g->xHII; I.K = g->K; I.G = g->G;
+    I.acc = g->acc; I.cnt = g->cnt;
+    build_sources(g, level0, (int)inst.size(), src);
+    inst.push_back(I);
+    b->dev_slot.push_back((int)s);
+    if (g->ncell > b->max_cells) b->max_cells = g->ncell;
+    const int ds = g->nx + g->ny + g->nz;
+    if (ds > b->max_dims) b->max_dims = ds;
+    const double d = sqrt((double)g->nx * g->nx + (double)g->ny * g->ny + (double)g->nz * g->nz);
+    if (d > diag) diag = d;
+  }
+  if (inst.size() > b->inst_cap) {
+    if (b->inst_dev) cudaFree(b->inst_dev);
+    b->inst_dev = nullptr;
+    b->inst_cap = 0;
+    CUDA_TRY(cudaMalloc((void**)&b->inst_dev, inst.size() * sizeof(InstDev)));
+    b->inst_cap = inst.size();
+  }
+  if (src.size() > b->src_cap) {
+    if (b->src_dev) cudaFree(b->src_dev);
+    b->src_dev = nullptr;
+    b->src_cap = 0;
+    CUDA_TRY(cudaMalloc((void**)&b->src_dev, src.size() * sizeof(SourceDev)));
+    b->src_cap = src.size();
+  }
+  if (!inst.empty()) CUDA_TRY(cudaMemcpy(b->inst_dev, inst.data(), inst.size() * sizeof(InstDev), cudaMemcpyHostToDevice));
+  if (!src.empty()) CUDA_TRY(cudaMemcpy(b->src_dev, src.data(), src.size() * sizeof(SourceDev), cudaMemcpyHostToDevice));
+  b->nsrc = (int)src.size();
+  b->n_roots = (12ULL << (2 * level0)) * (unsigned long long)src.size();
+  b->max_diag = diag;
+  b->dirty = false;
+  b->built_level0 = level0;
+  b->graph_ok = false;
+  return RT_OK;
+}
+
+static int batch_enqueue(rt_batch* b, const rt_trace_params* p) {
+  int rc = batch_rebuild(b, p->level0);
+  if (rc) return rc;
+  const int ninst = (int)b->dev_slot.size();
+  cudaStream_t st = b->stream;
+  LAUNCH_TRY(launch_batch_zero(b->inst_dev, ninst, b->precision, b->max_cells, st));  // Step 2
+  LAUNCH_TRY(launch_trace_init(b->ts.ctl, b->n_roots, st));
+  if (b->n_roots == 0) {
+    b->traced = false;
+    return RT_OK;
+  }
+  TraceArgs A;
+  memset(&A, 0, sizeof A);
+  fill_common_args(A, p);
+  A.inst = b->inst_dev;
+  A.ninst = ninst;
+  A.src = b->src_dev;
+  A.nsrc = b->nsrc;
+  A.npix0 = (uint32_t)(12u << (2 * p->level0));
+  A.n_roots = b->n_roots;
+  A.queue = b->ts.queue;
+  A.cap = b->ts.cap;
+  A.ctl = b->ts.ctl;
+  A.max_steps = 2 * b->max_dims + 16;
+  A.dir_tab = nullptr;
+  A.dir_levels = -1;
+  if (b->precision == RT_FP32_MIXED) {
+    // deepest level a package can reach in the largest grid
+    int want = p->level0;
+    while (want < p->max_level && A.rsplit[want] < b->max_diag) ++want;
+    if (want > kDirTableMaxLevel) want = kDirTableMaxLevel;
+    if ((rc = ensure_dir_table(b->ctx, want))) return rc;
+    A.dir_tab = b->ctx->dir_tab;
+    A.dir_levels = b->ctx->dir_levels;
+  }
+  int per_sm = 0;
+  CUDA_TRY(trace_occupancy(b->precision, 256, &per_sm));
+  if (per_sm < 1) per_sm = 1;
+  if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
+  CUDA_TRY(cudaEventRecord(b->ev0, st));
+  LAUNCH_TRY(launch_trace(b->precision, A, per_sm * b->ctx->num_sms, 256, st));
+  CUDA_TRY(cudaEventRecord(b->ev1, st));
+  b->traced = true;
+  return RT_OK;
+}
+
+static int batch_ensure_queue(rt_batch* b, unsigned long long cap) {
+  const size_t rec = b->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+  if (b->ts.queue && b->ts.cap >= cap && b->ts.rec_bytes == rec) return RT_OK;
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  if (b->ts.queue) cudaFree(b->ts.queue);
+  b->ts.queue = nullptr;
+  b->ts.cap = 0;
+  CUDA_TRY(cudaMalloc(&b->ts.queue, cap * rec));
+  CUDA_TRY(cudaMemset(b->ts.queue, 0, cap * rec));
+  b->ts.cap = cap;
+  b->ts.rec_bytes = rec;
+  b->graph_ok = false;
+  return RT_OK;
+}
+
+// status and queue use of the batch's last trace (synchronises)
+static int batch_status(rt_batch* b, int* status, unsigned long long* pushed, float* ms) {
+  unsigned long long* hctl = (unsigned long long*)b->host_rb;
+  CUDA_TRY(cudaMemcpyAsync(hctl, b->ts.ctl, CTL_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  *status = (int)hctl[CTL_STATUS];
+  *pushed = hctl[CTL_TAIL];
+  *ms = 0.f;
+  if (b->traced && cudaEventElapsedTime(ms, b->ev0, b->ev1) != cudaSuccess) {
+    *ms = 0.f;
+    cudaGetLastError();
+  }
+  return RT_OK;
+}
+
+extern "C" {
+
+int rt_batch_create(rt_ctx* ctx, void* stream, rt_batch** out) {
+  if (!ctx || !out) return fail(RT_ERR_INVALID_ARG, "rt_batch_create: NULL argument");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  rt_batch* b = new rt_batch;
+  b->ctx = ctx;
+  cudaError_t e = cudaSuccess;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreate(&b->stream);  // blocking: ordered with the legacy default stream
+    b->own_stream = true;
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->ts.ctl, CTL_N * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(b->ts.ctl, 0, CTL_N * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->host_rb, 4096);
+  if (e != cudaSuccess) {
+    delete b;
+    return fail(RT_ERR_CUDA, "rt_batch_create: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return RT_OK;
+}
+
+int rt_batch_destroy(rt_batch* b) {
+  if (!b) return RT_OK;
+  cudaStreamSynchronize(b->stream);
+  for (rt_grid* g : b->slots)
+    if (g) g->batch_stream = nullptr;
+  delete b;
+  return RT_OK;
+}
+
+int rt_batch_add(rt_batch* b, rt_grid* g, int* slot) {
+  if (!b || !g || !slot) return fail(RT_ERR_INVALID_ARG, "rt_batch_add: NULL argument");
+  if (g->ctx != b->ctx) return fail(RT_ERR_INVALID_ARG, "rt_batch_add: grid belongs to another context");
+  if (b->precision >= 0 && g->precision != b->precision)
+    return fail(RT_ERR_INVALID_ARG, "rt_batch_add: every grid of a batch has the same precision");
+  for (rt_grid* h : b->slots)
+    if (h == g) return fail(RT_ERR_STATE, "rt_batch_add: grid is already in the batch");
+  CUDA_TRY(cudaStreamSynchronize(g->stream));  // work already queued on the grid's own stream
+  b->precision = g->precision;
+  int s = -1;
+  for (size_t i = 0; i < b->slots.size(); ++i)
+    if (!b->slots[i]) { s = (int)i; break; }
+  if (s < 0) {
+    s = (int)b->slots.size();
+    b->slots.push_back(nullptr);
+  }
+  b->slots[s] = g;
+  g->batch_stream = b->stream;
+  b->dirty = true;
+  *slot = s;
+  return RT_OK;
+}
+
+int rt_batch_remove(rt_batch* b, int slot) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot])
+    return fail(RT_ERR_INVALID_ARG, "rt_batch_remove: no grid in slot %d", slot);
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  b->slots[slot]->batch_stream = nullptr;
+  b->slots[slot] = nullptr;
+  b->dirty = true;
+  bool any = false;
+  for (rt_grid* h : b->slots) any |= h != nullptr;
+  if (!any) b->precision = -1;
+  return RT_OK;
+}
+
+int rt_batch_size(rt_batch* b) {
+  if (!b) return 0;
+  int n = 0;
+  for (rt_grid* h : b->slots) n += h != nullptr;
+  return n;
+}
+
+int rt_batch_trace(rt_batch* b, const rt_trace_params* p, int sync) {
+  if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_trace: batch is NULL");
+  int rc = check_params(p);
+  if (rc) return rc;
+  CUDA_TRY(cudaSetDevice(b->ctx->device));
+  if (rt_batch_size(b) == 0) return RT_OK;
+  unsigned long long cap = (unsigned long long)p->queue_capacity;
+  const bool automatic = cap == 0;
+  if (automatic) {
+    cap = b->ts.cap;
+    if (cap == 0) {
+      long long cells = 0;
+      for (rt_grid* g : b->slots) if (g) cells += g->ncell;
+      cap = (unsigned long long)cells * 2ULL;
+      if (cap < (1ULL << 20)) cap = 1ULL << 20;
+      if (cap > (1ULL << 26)) cap = 1ULL << 26;
+    }
+  }
+  for (int attempt = 0;; ++attempt) {
+    if ((rc = batch_ensure_queue(b, cap))) return rc;
+    if ((rc = batch_enqueue(b, p))) return rc;
+    if (!sync) return RT_OK;
+    int status;
+    unsigned long long pushed;
+    float ms;
+    if ((rc = batch_status(b, &status, &pushed, &ms))) return rc;
+    if (status == RT_ERR_QUEUE_OVERFLOW && automatic && attempt < 6) {
+      unsigned long long need = pushed + pushed / 4 + 1024;
+      cap = need > 4 * cap ? need : 4 * cap;
+      if (cap > (1ULL << 31)) cap = 1ULL << 31;
+      continue;
+    }
+    if (status != RT_OK)
+      return fail(status, "rt_batch_trace: device status %d (queue capacity %llu, pushed %llu)", status,
+                  (unsigned long long)b->ts.cap, pushed);
+    return RT_OK;
+  }
+}
+
+int rt_batch_chem(rt_batch* b, double dt_s, int nsub, double alpha_B) {
+  if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_chem: batch is NULL");
+  if (!(dt_s >= 0) || !isfinite(dt_s) || nsub < 1 || !(alpha_B >= 0) || !isfinite(alpha_B))
+    return fail(RT_ERR_INVALID_ARG, "rt_batch_chem: bad dt_s / nsub / alpha_B");
+  CUDA_TRY(cudaSetDevice(b->ctx->device));
+  if (rt_batch_size(b) == 0) return RT_OK;
+  if (b->dirty) {
+    int rc = batch_rebuild(b, b->built_level0 >= 0 ? b->built_level0 : 1);
+    if (rc) return rc;
+  }
+  LAUNCH_TRY(launch_batch_chem(b->inst_dev, (int)b->dev_slot.size(), b->precision, b->max_cells, dt_s / nsub, nsub,
+                               alpha_B, b->stream));
+  return RT_OK;
+}
+
+static bool same_params(const rt_trace_params& a, const rt_trace_params& b) {
+  return a.level0 == b.level0 && a.phi_c == b.phi_c && a.f_term == b.f_term && a.max_level == b.max_level &&
+         a.queue_capacity == b.queue_capacity && a.timeout_s == b.timeout_s && a.blocks_per_sm == b.blocks_per_sm &&
+         a.segs_per_iter == b.segs_per_iter && a.flags == b.flags;
+}
+
+int rt_batch_step(rt_batch* b, const rt_trace_params* p, double dt_s, int nsub, double alpha_B, int nsteps) {
+  if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_step: batch is NULL");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (nsteps < 0 || !(dt_s >= 0) || !isfinite(dt_s) || nsub < 1 || !(alpha_B >= 0) || !isfinite(alpha_B))
+    return fail(RT_ERR_INVALID_ARG, "rt_batch_step: bad nsteps / dt_s / nsub / alpha_B");
+  CUDA_TRY(cudaSetDevice(b->ctx->device));
+  if (rt_batch_size(b) == 0 || nsteps == 0) return RT_OK;
+  const bool reuse = b->graph_ok && !b->dirty && b->built_level0 == p->level0 && same_params(b->gp, *p) &&
+                     b->g_dt == dt_s && b->g_nsub == nsub && b->g_alpha == alpha_B;
+  if (!reuse) {
+    // size the queue (and build tables) with one synchronous trace, then
+    // capture one step -- zero, emit, trace, update -- as a graph
+    rt_trace_params q = *p;
+    if ((rc = rt_batch_trace(b, &q, 1))) return rc;
+    if (q.queue_capacity == 0) {
+      int status;
+      unsigned long long pushed;
+      float ms;
+      if ((rc = batch_status(b, &status, &pushed, &ms))) return rc;
+      unsigned long long need = pushed + pushed / 2 + (1ULL << 16);
+      if (need > b->ts.cap && (rc = batch_ensure_queue(b, need))) return rc;
+      q.queue_capacity = (int64_t)b->ts.cap;
+    }
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    const unsigned long long launches_before = g_launches.load();
+    CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc1 = batch_enqueue(b, &q);
+    cudaError_t e1 = launch_batch_chem(b->inst_dev, (int)b->dev_slot.size(), b->precision, b->max_cells,
+                                       dt_s / nsub, nsub, alpha_B, b->stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    g_launches.store(launches_before);  // captured kernels count when the graph runs
+    if (rc1) { if (graph) cudaGraphDestroy(graph); return rc1; }
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(RT_ERR_CUDA, "rt_batch_step: capture: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) return fail(RT_ERR_CUDA, "rt_batch_step: instantiate: %s", cudaGetErrorString(e3));
+    b->graph_ok = true;
+    b->gp = *p;
+    b->g_dt = dt_s;
+    b->g_nsub = nsub;
+    b->g_alpha = alpha_B;
+  }
+  for (int i = 0; i < nsteps; ++i) {
+    CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+    g_launches.fetch_add(4);  // zero, init, trace, chemistry
+  }
+  return RT_OK;
+}
+
+int rt_batch_get_budget(rt_batch* b, int slot, rt_budget* out) {
+  if (!b || !out || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot])
+    return fail(RT_ERR_INVALID_ARG, "rt_batch_get_budget: no grid in slot %d", slot);
+  int status;
+  unsigned long long pushed;
+  float ms;
+  int rc = batch_status(b, &status, &pushed, &ms);
+  if (rc) return rc;
+  rt_grid* g = b->slots[slot];
+  double* hacc = (double*)g->host_rb;
+  unsigned long long* hcnt = (unsigned long long*)((char*)g->host_rb + 64);
+  CUDA_TRY(cudaMemcpyAsync(hacc, g->acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaMemcpyAsync(hcnt, g->cnt, kCntWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  memset(out, 0, sizeof *out);
+  out->emitted = hacc[0];
+  out->absorbed = hacc[1];
+  out->escaped = hacc[2];
+  for (int l = 0; l < kLevels; ++l) {
+    out->counts[l] = hcnt[l];
+    out->hashes[l] = hcnt[kLevels + l];
+  }
+  out->segments = hcnt[kCntSegments];
+  out->fallbacks = hcnt[kCntFallbacks];
+  out->fallbacks_tau = hcnt[kCntFallbacksTau];
+  out->queue_pushed = pushed;
+  out->status = status;
+  out->kernel_ms = ms;
+  if (status != RT_OK) return fail(status, "rt_batch_get_budget: device status %d", status);
+  return RT_OK;
+}
+
+int rt_batch_autotune(rt_batch* b, rt_trace_params* p) {
+  if (!b || !p) return fail(RT_ERR_INVALID_ARG, "rt_batch_autotune: NULL argument");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (rt_batch_size(b) == 0) return RT_OK;
+  rt_trace_params q = *p;
+  q.segs_per_iter = 8;
+  q.blocks_per_sm = 0;
+  if ((rc = rt_batch_trace(b, &q, 1))) return rc;  // sizes the queue, warms up
+  const int spi[] = {4, 8, 16, 32};
+  int per_sm_max = 0;
+  CUDA_TRY(trace_occupancy(b->precision, 256, &per_sm_max));
+  float best = 1e30f;
+  rt_trace_params bestp = q;
+  for (int bps = 1; bps <= (per_sm_max > 0 ? per_sm_max : 1); ++bps) {
+    for (int s : spi) {
+      q.segs_per_iter = s;
+      q.blocks_per_sm = bps;
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        if ((rc = rt_batch_trace(b, &q, 1))) return rc;
+        int status;
+        unsigned long long pushed;
+        float ms;
+        if ((rc = batch_status(b, &status, &pushed, &ms))) return rc;
+        if (ms < tmin) tmin = ms;
+      }
+      if (tmin < best) {
+        best = tmin;
+        bestp = q;
+      }
+    }
+  }
+  p->segs_per_iter = bestp.segs_per_iter;
+  p->blocks_per_sm = bestp.blocks_per_sm;
   return RT_OK;
 }
 

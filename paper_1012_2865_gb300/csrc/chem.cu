@@ -8,6 +8,53 @@
 
 namespace rtg {
 
+// One cell, FP64 path: the backward-Euler substeps below, explicitly rounded.
+__device__ __forceinline__ void chem_cell_fp64(double& x, double& z, double n, double kc, double h, int nsub,
+                                               double alpha) {
+  const double a = __dmul_rn(__dmul_rn(h, alpha), n);
+  const double hk = __dmul_rn(h, kc);
+  const double b = __dadd_rn(1.0, hk);
+  for (int i = 0; i < nsub; ++i) {
+    const double D = __dadd_rn(__dmul_rn(b, b), __dmul_rn(__dmul_rn(4.0, a), __dadd_rn(z, hk)));
+    const double sq = __dsqrt_rn(D);
+    const double xn = __ddiv_rn(__dmul_rn(2.0, __dadd_rn(a, x)), __dadd_rn(__dadd_rn(__dmul_rn(2.0, a), b), sq));
+    const double zn = __ddiv_rn(__dmul_rn(2.0, __dadd_rn(z, hk)), __dadd_rn(b, sq));
+    if (xn <= zn) { x = xn; z = __dsub_rn(1.0, xn); }
+    else { z = zn; x = __dsub_rn(1.0, zn); }
+  }
+}
+
+// One cell, FP32-mixed path: FP32 solution + one FP64 Newton correction per
+// substep (see chem_mixed_kernel).
+__device__ __forceinline__ void chem_cell_mixed(double& x, double& z, double n, float kc, double h, int nsub,
+                                                double alpha) {
+  const double a = h * alpha * n;
+  const double hk = h * (double)kc;
+  const double b = 1.0 + hk;
+  const double two_a_b = 2.0 * a + b;
+  const float af = (float)a, bf = (float)b, hkf = (float)hk;
+  for (int i = 0; i < nsub; ++i) {
+    const float xf = (float)x, zf = (float)z;
+    const float wf = zf + hkf;
+    const float sq = sqrtf(fmaf(4.0f * af, wf, bf * bf));
+    if (xf < 0.5f) {
+      const float xg = 2.0f * (af + xf) / (2.0f * af + bf + sq);
+      const double xd = (double)xg;
+      const double g = fma(fma(a, xd, -two_a_b), xd, a + x);
+      const float gp = fmaf(2.0f * af, xg, -(2.0f * af + bf));
+      x = xd - (double)((float)g / gp);
+      z = 1.0 - x;
+    } else {
+      const float zg = 2.0f * wf / (bf + sq);
+      const double zd = (double)zg;
+      const double f = fma(fma(a, zd, b), zd, -(z + hk));
+      const float fp = fmaf(2.0f * af, zg, bf);
+      z = zd - (double)((float)f / fp);
+      x = 1.0 - z;
+    }
+  }
+}
+
 // Backward Euler on dx/dt = alpha_B n_H (1 - x)^2 - k x, x = x_HI,
 // z = x_HII, over nsub substeps h with k frozen.  With a = h alpha_B n_H and
 // b = 1 + h k the implicit step solves a x'^2 - (2a + b) x' + (a + x) = 0;
@@ -28,17 +75,7 @@ __global__ void chem_kernel(long long ncell, const double* __restrict__ nH, doub
     // no radiation and fully neutral: every substep returns (1, 0) exactly
     if (kc == (KT)0 && z == 0.0 && x == 1.0) continue;
     const double n = nH[c];
-    const double a = __dmul_rn(__dmul_rn(h, alpha), n);
-    const double hk = __dmul_rn(h, (double)kc);
-    const double b = __dadd_rn(1.0, hk);
-    for (int i = 0; i < nsub; ++i) {
-      const double D = __dadd_rn(__dmul_rn(b, b), __dmul_rn(__dmul_rn(4.0, a), __dadd_rn(z, hk)));
-      const double sq = __dsqrt_rn(D);
-      const double xn = __ddiv_rn(__dmul_rn(2.0, __dadd_rn(a, x)), __dadd_rn(__dadd_rn(__dmul_rn(2.0, a), b), sq));
-      const double zn = __ddiv_rn(__dmul_rn(2.0, __dadd_rn(z, hk)), __dadd_rn(b, sq));
-      if (xn <= zn) { x = xn; z = __dsub_rn(1.0, xn); }
-      else { z = zn; x = __dsub_rn(1.0, zn); }
-    }
+    chem_cell_fp64(x, z, n, (double)kc, h, nsub, alpha);
     xHI[c] = x;
     xHII[c] = z;
     nhi[c] = (NT)__dmul_rn(n, x);
@@ -63,31 +100,7 @@ __global__ void chem_mixed_kernel(long long ncell, const double* __restrict__ nH
     const float kc = K[c];
     if (kc == 0.0f && z == 0.0 && x == 1.0) continue;
     const double n = nH[c];
-    const double a = h * alpha * n;
-    const double hk = h * (double)kc;
-    const double b = 1.0 + hk;
-    const double two_a_b = 2.0 * a + b;
-    const float af = (float)a, bf = (float)b, hkf = (float)hk;
-    for (int i = 0; i < nsub; ++i) {
-      const float xf = (float)x, zf = (float)z;
-      const float wf = zf + hkf;
-      const float sq = sqrtf(fmaf(4.0f * af, wf, bf * bf));
-      if (xf < 0.5f) {
-        const float xg = 2.0f * (af + xf) / (2.0f * af + bf + sq);
-        const double xd = (double)xg;
-        const double g = fma(fma(a, xd, -two_a_b), xd, a + x);
-        const float gp = fmaf(2.0f * af, xg, -(2.0f * af + bf));
-        x = xd - (double)((float)g / gp);
-        z = 1.0 - x;
-      } else {
-        const float zg = 2.0f * wf / (bf + sq);
-        const double zd = (double)zg;
-        const double f = fma(fma(a, zd, b), zd, -(z + hk));
-        const float fp = fmaf(2.0f * af, zg, bf);
-        z = zd - (double)((float)f / fp);
-        x = 1.0 - z;
-      }
-    }
+    chem_cell_mixed(x, z, n, kc, h, nsub, alpha);
     xHI[c] = x;
     xHII[c] = z;
     nhi[c] = (float)(n * x);
@@ -147,6 +160,80 @@ cudaError_t launch_refresh(int precision, long long ncell, const double* nH, con
 cudaError_t launch_complement(long long n, const double* x, double* out, cudaStream_t st) {
   const int block = 256, grid = grid_for(n, block);
   complement_kernel<<<grid, block, 0, st>>>(n, x, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms: one launch for every grid of a batch.  blockIdx.y selects the
+// grid (its descriptor in `inst`), blocks of a row stride over its cells.
+// ---------------------------------------------------------------------------
+
+// Step 2 for every grid: zero k_ph, Gamma (element size esz), the budget
+// sums and the counters.
+__global__ void batch_zero_kernel(const InstDev* __restrict__ inst, int esz) {
+  const InstDev I = inst[blockIdx.y];
+  const long long n = (long long)I.nx * I.ny * I.nz;
+  const long long words = n * esz / 4;
+  unsigned int* K = (unsigned int*)I.K;
+  unsigned int* G = (unsigned int*)I.G;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < words;
+       c += (long long)gridDim.x * blockDim.x) {
+    K[c] = 0u;
+    G[c] = 0u;
+  }
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < 4; i += blockDim.x) I.acc[i] = 0.0;
+    for (int i = threadIdx.x; i < kCntWords; i += blockDim.x) I.cnt[i] = 0ULL;
+  }
+}
+
+template <bool MIXED>
+__global__ void batch_chem_kernel(const InstDev* __restrict__ inst, double h, int nsub, double alpha) {
+  const InstDev I = inst[blockIdx.y];
+  const long long n = (long long)I.nx * I.ny * I.nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    double x = I.xHI[c], z = I.xHII[c];
+    if (MIXED) {
+      const float kc = ((const float*)I.K)[c];
+      if (kc == 0.0f && z == 0.0 && x == 1.0) continue;
+      const double nh = I.nH[c];
+      chem_cell_mixed(x, z, nh, kc, h, nsub, alpha);
+      ((double*)I.xHI)[c] = x;
+      I.xHII[c] = z;
+      ((float*)I.nhi)[c] = (float)(nh * x);
+    } else {
+      const double kc = ((const double*)I.K)[c];
+      if (kc == 0.0 && z == 0.0 && x == 1.0) continue;
+      const double nh = I.nH[c];
+      chem_cell_fp64(x, z, nh, kc, h, nsub, alpha);
+      ((double*)I.xHI)[c] = x;
+      I.xHII[c] = z;
+      ((double*)I.nhi)[c] = __dmul_rn(nh, x);
+    }
+  }
+}
+
+cudaError_t launch_batch_zero(const InstDev* inst, int ninst, int precision, long long max_cells, cudaStream_t st) {
+  if (ninst <= 0) return cudaSuccess;
+  const int esz = precision == RT_FP64 ? 8 : 4;
+  long long bx = (max_cells * esz / 4 + 255) / 256;
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  batch_zero_kernel<<<dim3((unsigned)bx, (unsigned)ninst), 256, 0, st>>>(inst, esz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_chem(const InstDev* inst, int ninst, int precision, long long max_cells, double h,
+                              int nsub, double alpha, cudaStream_t st) {
+  if (ninst <= 0) return cudaSuccess;
+  long long bx = (max_cells + 255) / 256;
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  if (precision == RT_FP64)
+    batch_chem_kernel<false><<<dim3((unsigned)bx, (unsigned)ninst), 256, 0, st>>>(inst, h, nsub, alpha);
+  else
+    batch_chem_kernel<true><<<dim3((unsigned)bx, (unsigned)ninst), 256, 0, st>>>(inst, h, nsub, alpha);
   return cudaGetLastError();
 }
 

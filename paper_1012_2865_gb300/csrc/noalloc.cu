@@ -227,6 +227,7 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
     A.timeout_ns = (long long)((p->timeout_s > 0 ? p->timeout_s : 2.0) * 1e9);
     A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 8;
     A.max_steps = 2 * (g->nx + g->ny + g->nz) + 16;
+    A.checksums = (p->flags & RT_TRACE_CHECKSUMS) != 0;
     int per_sm = 0;
     if ((e = trace_occupancy(RT_FP32_MIXED, 256, &per_sm)) != cudaSuccess) return na_fail(RT_ERR_CUDA, "occupancy", e);
     if (per_sm < 1) per_sm = 1;

@@ -50,6 +50,7 @@ struct InstDev {
   const void* nhi;          // absorber density n_HI (double or float), x fastest
   const double* nH;         // hydrogen density, FP64 (decisions re-taken in FP64)
   const double* xHI;        // neutral fraction, FP64
+  double* xHII;             // ionised fraction, FP64 (chemistry)
   void* K;                  // k_ph accumulator (double or float)
   void* G;                  // Gamma accumulator (double or float)
   double* acc;              // [0] emitted [1] absorbed [2] escaped (photons/s)
@@ -97,6 +98,7 @@ struct TraceArgs {
   long long timeout_ns;
   int segs_per_iter;
   int max_steps;  // bound on segments of one package (guards the DDA loop)
+  int checksums;  // accumulate the created-set checksum
 };
 
 // 64-bit finaliser used for the created-package checksum (documented in rt.h).

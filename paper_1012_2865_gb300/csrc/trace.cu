@@ -78,14 +78,19 @@ __device__ __forceinline__ void acc_switch(LaneAcc& a, unsigned& nseg, int inst,
 struct LevelCounters {
   unsigned int* cnt;        // [kShInst][kLevels]
   unsigned long long* hsh;  // [kShInst][kLevels]
-  __device__ __forceinline__ void add(const TraceArgs& A, int inst, int local, int level, uint32_t pix) {
-    const unsigned long long h = pkg_hash((uint32_t)local, (uint32_t)level, pix);
+  // Count n packages (level, pix0 .. pix0 + n - 1) of a source; the
+  // checksum terms only when requested.
+  __device__ __forceinline__ void add(const TraceArgs& A, int inst, int local, int level, uint32_t pix0,
+                                      uint32_t n) {
+    unsigned long long h = 0;
+    if (A.checksums)
+      for (uint32_t k = 0; k < n; ++k) h += pkg_hash((uint32_t)local, (uint32_t)level, pix0 + k);
     if (inst < kShInst) {
-      atomicAdd(&cnt[inst * kLevels + level], 1u);
-      atomicAdd(&hsh[inst * kLevels + level], h);
+      atomicAdd(&cnt[inst * kLevels + level], n);
+      if (A.checksums) atomicAdd(&hsh[inst * kLevels + level], h);
     } else {
-      atomicAdd(&A.inst[inst].cnt[level], 1ULL);
-      atomicAdd(&A.inst[inst].cnt[kLevels + level], h);
+      atomicAdd(&A.inst[inst].cnt[level], (unsigned long long)n);
+      if (A.checksums) atomicAdd(&A.inst[inst].cnt[kLevels + level], h);
     }
   }
 };
@@ -125,6 +130,7 @@ struct Walk64 {
   __device__ __forceinline__ int inst(const TraceArgs& A) const { return A.src[src].inst; }
   __device__ __forceinline__ double unit(const TraceArgs& A) const { return A.src[src].unit; }
   __device__ __forceinline__ int lvl() const { return (int)level; }
+  __device__ __forceinline__ bool is_root() const { return P == 1.0 && r == 0.0 && tau == 0.0; }
 
   // Steps 3a-3b: direction and cell at radius r.  Returns false if the
   // package starts outside the box.
@@ -155,24 +161,40 @@ struct Walk64 {
   __device__ __forceinline__ void load(const Rec& q) {
     r = q.r; P = q.P; tau = q.tau; src = q.src; pix = q.pix; level = q.level;
   }
-  __device__ __forceinline__ void store_child(Rec* q, uint32_t cpix, uint32_t epoch) const {
-    __stcg(&q->r, r);
-    __stcg(&q->P, P * 0.25);
-    __stcg(&q->tau, tau);
-    __stcg(&q->src, src);
-    __stcg(&q->pix, cpix);
-    __stcg(&q->level, level + 1);
+  // Record of child cpix (level + 1, P/4, same radius and optical depth).
+  __device__ __forceinline__ Rec make_child(uint32_t cpix) const {
+    Rec c;
+    c.r = r; c.P = P * 0.25; c.tau = tau; c.src = src; c.pix = cpix; c.level = level + 1; c.tag = 0;
+    return c;
+  }
+  // Publish a record in the global queue: payload first, then the tag with
+  // release semantics.
+  __device__ __forceinline__ static void publish(Rec* q, const Rec& c, uint32_t epoch) {
+    __stcg(reinterpret_cast<double2*>(&q->r), make_double2(c.r, c.P));
+    __stcg(reinterpret_cast<double*>(&q->tau), c.tau);
+    __stcg(reinterpret_cast<uint2*>(&q->src), make_uint2(c.src, c.pix));
+    __stcg(&q->level, c.level);
     st_release_u32(&q->tag, epoch);
   }
+  // Poll with a relaxed load; only a successful poll pays for the fence that
+  // orders the payload reads after the tag.
   __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
     if (ld_relaxed_u32(&q->tag) != epoch) return false;
     __threadfence();
-    o.r = __ldcg(&q->r); o.P = __ldcg(&q->P); o.tau = __ldcg(&q->tau);
-    o.src = __ldcg(&q->src); o.pix = __ldcg(&q->pix); o.level = __ldcg(&q->level);
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(&q->r));    // r, P
+    const double2 b = __ldcg(reinterpret_cast<const double2*>(&q->tau));  // tau, (src, pix)
+    const uint2 c = __ldcg(reinterpret_cast<const uint2*>(&q->level));    // level, tag
+    const unsigned long long sp = (unsigned long long)__double_as_longlong(b.y);
+    o.r = a.x; o.P = a.y; o.tau = b.x;
+    o.src = (uint32_t)(sp & 0xffffffffu);
+    o.pix = (uint32_t)(sp >> 32);
+    o.level = c.x;
     return true;
   }
-  __device__ __forceinline__ void set_root(uint32_t gsrc, uint32_t lvl0, uint32_t p) {
-    src = gsrc; level = lvl0; pix = p; r = 0.0; P = 1.0; tau = 0.0;
+  __device__ __forceinline__ static Rec root_rec(uint32_t gsrc, uint32_t lvl0, uint32_t p) {
+    Rec c;
+    c.r = 0.0; c.P = 1.0; c.tau = 0.0; c.src = gsrc; c.pix = p; c.level = lvl0; c.tag = 0;
+    return c;
   }
   __device__ __forceinline__ void become_child0() {
     level += 1; pix = 4u * pix; P = P * 0.25;
@@ -396,12 +418,15 @@ struct Walk32 {
   int c0, c1, c2;
   int nx, ny, nz, steps;
   unsigned nseg;
+  float nh;             // n_HI of the current cell, loaded one step ahead
   const float* nhi;
   float* K;
   float* G;
 
   __device__ __forceinline__ int lvl() const { return (int)(level & 15u); }
+  __device__ __forceinline__ int cell_index() const { return c0 + nx * (c1 + ny * c2); }
   __device__ __forceinline__ bool diag_exact() const { return (level & 256u) != 0; }
+  __device__ __forceinline__ bool is_root() const { return P == 1.0f && r.hi == 0.0f && tau == 0.0f; }
   __device__ __forceinline__ int inst(const TraceArgs& A) const { return A.src[src].inst; }
   __device__ __forceinline__ double unit(const TraceArgs& A) const { return A.src[src].unit; }
   __device__ __forceinline__ bool inside() const {
@@ -448,6 +473,7 @@ struct Walk32 {
     Pstart = P;
     steps = 0;
     if (!inside()) return false;
+    nh = __ldg(&nhi[cell_index()]);
     t0 = next_t(c0, sh.x, sl.x, iv0);
     t1 = next_t(c1, sh.y, sl.y, iv1);
     t2 = next_t(c2, sh.z, sl.z, iv2);
@@ -458,31 +484,38 @@ struct Walk32 {
     r = {q.r, q.r_lo}; P = q.P; tau = q.tau; tau_err = q.tau_err; src = q.src; pix = q.pix;
     level = q.tag & 15u;
   }
-  __device__ __forceinline__ void store_child(Rec* q, uint32_t cpix, uint32_t epoch) const {
-    __stcg(&q->r, r.hi);
-    __stcg(&q->P, P * 0.25f);
-    __stcg(&q->tau, tau);
-    __stcg(&q->tau_err, tau_err);
-    __stcg(&q->src, src);
-    __stcg(&q->pix, cpix);
-    __stcg(&q->r_lo, r.lo);
-    st_release_u32(&q->tag, (epoch << 4) | (uint32_t)(lvl() + 1));
+  // Record of child cpix (level + 1, P/4, same radius, optical depth and its
+  // error bound); the level sits in the tag's low bits until publication.
+  __device__ __forceinline__ Rec make_child(uint32_t cpix) const {
+    Rec c;
+    c.r = r.hi; c.P = P * 0.25f; c.tau = tau; c.tau_err = tau_err;
+    c.src = src; c.pix = cpix; c.r_lo = r.lo; c.tag = (uint32_t)(lvl() + 1);
+    return c;
+  }
+  // Publish a record in the global queue: payload first, then the tag
+  // ((epoch << 4) | level) with release semantics.
+  __device__ __forceinline__ static void publish(Rec* q, const Rec& c, uint32_t epoch) {
+    __stcg(reinterpret_cast<float4*>(&q->r), make_float4(c.r, c.P, c.tau, c.tau_err));
+    __stcg(reinterpret_cast<uint2*>(&q->src), make_uint2(c.src, c.pix));
+    __stcg(&q->r_lo, c.r_lo);
+    st_release_u32(&q->tag, (epoch << 4) | (c.tag & 15u));
   }
   // Poll with a relaxed load; only a successful poll pays for the fence that
-  // orders the payload reads after the tag (acquire loads in the polling loop
-  // were measurably slower).
+  // orders the payload reads after the tag.
   __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
     const uint32_t tg = ld_relaxed_u32(&q->tag);
     if ((tg >> 4) != (epoch & 0x0fffffffu)) return false;
     __threadfence();
-    o.r = __ldcg(&q->r); o.P = __ldcg(&q->P); o.tau = __ldcg(&q->tau);
-    o.tau_err = __ldcg(&q->tau_err); o.src = __ldcg(&q->src); o.pix = __ldcg(&q->pix);
-    o.r_lo = __ldcg(&q->r_lo);
-    o.tag = tg;
+    const float4 a = __ldcg(reinterpret_cast<const float4*>(&q->r));
+    const uint4 b = __ldcg(reinterpret_cast<const uint4*>(&q->src));
+    o.r = a.x; o.P = a.y; o.tau = a.z; o.tau_err = a.w;
+    o.src = b.x; o.pix = b.y; o.r_lo = __uint_as_float(b.z); o.tag = tg;
     return true;
   }
-  __device__ __forceinline__ void set_root(uint32_t gsrc, uint32_t l, uint32_t p) {
-    src = gsrc; level = l; pix = p; r = {0.0f, 0.0f}; P = 1.0f; tau = 0.0f; tau_err = 0.0f;
+  __device__ __forceinline__ static Rec root_rec(uint32_t gsrc, uint32_t l, uint32_t p) {
+    Rec c;
+    c.r = 0.0f; c.P = 1.0f; c.tau = 0.0f; c.tau_err = 0.0f; c.src = gsrc; c.pix = p; c.r_lo = 0.0f; c.tag = l;
+    return c;
   }
   __device__ __forceinline__ void become_child0() {
     level = (uint32_t)(lvl() + 1); pix = 4u * pix; P = P * 0.25f;
@@ -531,17 +564,17 @@ struct Walk32 {
     if (split) return EV_SPLIT;
     float dr = f2_diff(rn, r);
     if (dr < 0.0f) dr = 0.0f;
-    const int idx = c0 + nx * (c1 + ny * c2);
-    const float nh = __ldg(&nhi[idx]);
+    const int idx = cell_index();
     const float4 k32 = __ldg(&A.src[src].k32);  // sdx, w, rw, heat
     const float kap = k32.x * nh;
     const float dtau = kap * dr;
-    // absorbed fraction am = 1 - e^-tau and transmitted fraction tr = e^-tau,
-    // each from the form that does not cancel
-    float am, tr;
-    if (dtau < 0.5f) { am = -expm1f(-dtau); tr = 1.0f - am; }
-    else { tr = expf(-dtau); am = 1.0f - tr; }
-    const float phi = dtau > 0.0f ? __fdividef(am, dtau) : 1.0f;
+    // transmitted fraction tr = e^-tau; phi = (1 - e^-tau)/tau from its Taylor
+    // series below tau = 1/4 (7 terms: truncation < 2e-13), else from tr.
+    // Both are computed and one is selected, so lanes do not diverge.
+    const float tr = expf(-dtau);
+    const float ser = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(dtau, 1.0f / 5040.0f, -1.0f / 720.0f), dtau, 1.0f / 120.0f), dtau,
+                                          -1.0f / 24.0f), dtau, 1.0f / 6.0f), dtau, -0.5f), dtau, 1.0f);
+    const float phi = dtau < 0.25f ? ser : __fdividef(1.0f - tr, dtau);
     const float kadd = P * k32.y * dr * phi;
     atomicAdd(&K[idx], kadd);
     if (k32.w != 0.0f) atomicAdd(&G[idx], kadd * k32.w);
@@ -584,6 +617,8 @@ struct Walk32 {
       acc.escaped += (double)P * u;
       return EV_DONE;
     }
+    // the next cell is known before its density is needed: start the load now
+    nh = __ldg(&nhi[cell_index()]);
     if (++steps > A.max_steps) {
       set_status(A.ctl, RT_ERR_STATE);
       const double u = unit(A);
@@ -632,6 +667,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   long long ticket = -1;
   long long seen_out = -1;
   uint64_t seen_ns = global_ns();
+  unsigned backoff = 256;  // ns; idle warps back off exponentially up to 4 us
 
   for (;;) {
     // (1) idle lanes without a ticket take one (one atomic per warp)
@@ -652,12 +688,12 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
       if (tk < A.n_roots) {
         const uint32_t gsrc = (uint32_t)(tk / A.npix0);
         const uint32_t p = (uint32_t)(tk - (unsigned long long)gsrc * A.npix0);
-        w.set_root(gsrc, (uint32_t)A.level0, p);
+        w.load(W::root_rec(gsrc, (uint32_t)A.level0, p));
         got = true;
         const SourceDev& S = A.src[gsrc];
         acc_switch(acc, w.nseg, S.inst, A);
         acc.emitted += S.unit;
-        LC.add(A, S.inst, S.local, A.level0, p);
+        LC.add(A, S.inst, S.local, A.level0, p, 1);
       } else {
         const unsigned long long slot = tk - A.n_roots;
         if (slot < A.cap) {
@@ -693,9 +729,11 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         if (lane == 0) set_status(A.ctl, RT_ERR_TIMEOUT);
         break;
       }
-      __nanosleep(128);
+      __nanosleep(backoff);
+      backoff = backoff < 4096 ? 2 * backoff : 4096;
       continue;
     }
+    backoff = 256;
     // (4) trace a few segments
     if (active && ev == EV_NONE) {
       for (int it = 0; it < A.segs_per_iter; ++it) {
@@ -726,11 +764,11 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         const unsigned long long my = base + 3ULL * __popc(sm & lt_mask);
         const SourceDev& S = A.src[w.src];
         const int cl = w.lvl() + 1;
-        for (uint32_t k = 0; k < 4; ++k) LC.add(A, S.inst, S.local, cl, 4u * w.pix + k);
+        LC.add(A, S.inst, S.local, cl, 4u * w.pix, 4);
         unsigned dropped = 0;
         for (uint32_t k = 1; k < 4; ++k) {
           const unsigned long long slot = my + (k - 1);
-          if (slot < A.cap) w.store_child(&queue[slot], 4u * w.pix + k, epoch);
+          if (slot < A.cap) W::publish(&queue[slot], w.make_child(4u * w.pix + k), epoch);
           else ++dropped;
         }
         if (dropped) {

@@ -31,6 +31,7 @@ RT_MEM_DEVICE = 1
 RT_DTYPE_F64 = 0
 RT_DTYPE_F32 = 1
 RT_MAX_LEVEL = 14
+RT_TRACE_CHECKSUMS = 1
 NLEV = RT_MAX_LEVEL + 1
 
 PRECISIONS = {"fp64": RT_FP64, "fp32_mixed": RT_FP32_MIXED, "mixed": RT_FP32_MIXED}
@@ -53,7 +54,7 @@ class rt_trace_params(ctypes.Structure):
     _fields_ = [("level0", ctypes.c_int), ("phi_c", ctypes.c_double), ("f_term", ctypes.c_double),
                 ("max_level", ctypes.c_int), ("queue_capacity", ctypes.c_int64),
                 ("timeout_s", ctypes.c_double), ("blocks_per_sm", ctypes.c_int),
-                ("segs_per_iter", ctypes.c_int)]
+                ("segs_per_iter", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
 class rt_budget(ctypes.Structure):
@@ -100,6 +101,16 @@ def lib():
             "rt_selfcheck_directions": ([vp, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
             "rt_kernel_launches": ([], ctypes.c_uint64),
             "rt_get_last_error": ([], ctypes.c_char_p),
+            "rt_batch_create": ([vp, vp, ctypes.POINTER(vp)], i),
+            "rt_batch_destroy": ([vp], i),
+            "rt_batch_add": ([vp, vp, ctypes.POINTER(i)], i),
+            "rt_batch_remove": ([vp, i], i),
+            "rt_batch_size": ([vp], i),
+            "rt_batch_trace": ([vp, ctypes.POINTER(rt_trace_params), i], i),
+            "rt_batch_chem": ([vp, d, i, d], i),
+            "rt_batch_step": ([vp, ctypes.POINTER(rt_trace_params), d, i, d, i], i),
+            "rt_batch_get_budget": ([vp, i, ctypes.POINTER(rt_budget)], i),
+            "rt_batch_autotune": ([vp, ctypes.POINTER(rt_trace_params)], i),
             "rt_trace_noalloc": ([ctypes.POINTER(rt_noalloc_grid), i, vp, vp, vp, vp,
                                   ctypes.POINTER(rt_trace_params), vp, ctypes.POINTER(rt_budget)], i),
             "rt_noalloc_last_error": ([], ctypes.c_char_p),
@@ -183,10 +194,10 @@ def rt_clear_sources(grid):
 
 
 def trace_params(level0=1, phi_c=5.1, f_term=1e-10, max_level=RT_MAX_LEVEL, queue_capacity=0,
-                 timeout_s=2.0, blocks_per_sm=0, segs_per_iter=0) -> rt_trace_params:
+                 timeout_s=2.0, blocks_per_sm=0, segs_per_iter=0, checksums=False) -> rt_trace_params:
     return rt_trace_params(int(level0), float(phi_c), float(f_term), int(max_level),
                            int(queue_capacity), float(timeout_s), int(blocks_per_sm),
-                           int(segs_per_iter))
+                           int(segs_per_iter), RT_TRACE_CHECKSUMS if checksums else 0)
 
 
 def budget_dict(b: rt_budget) -> dict:
@@ -319,3 +330,90 @@ def rt_trace_noalloc(dims, box_len_cm, n_HI, n_H, x_HI, kph, gamma, pos_cm, ndot
     if code != RT_OK:
         raise RtError(code, lib().rt_noalloc_last_error().decode(errors="replace"))
     return budget_dict(b)
+
+
+def rt_batch_create(ctx, stream=None):
+    h = ctypes.c_void_p()
+    check(lib().rt_batch_create(ctx, ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+    return h
+
+
+def rt_batch_destroy(batch):
+    check(lib().rt_batch_destroy(batch))
+
+
+def rt_batch_add(batch, grid) -> int:
+    slot = ctypes.c_int()
+    check(lib().rt_batch_add(batch, grid, ctypes.byref(slot)))
+    return slot.value
+
+
+def rt_batch_remove(batch, slot):
+    check(lib().rt_batch_remove(batch, int(slot)))
+
+
+def rt_batch_size(batch) -> int:
+    return int(lib().rt_batch_size(batch))
+
+
+def rt_batch_trace(batch, params: rt_trace_params, sync: bool = True):
+    check(lib().rt_batch_trace(batch, ctypes.byref(params), 1 if sync else 0))
+
+
+def rt_batch_chem(batch, dt_s, nsub, alpha_B):
+    check(lib().rt_batch_chem(batch, float(dt_s), int(nsub), float(alpha_B)))
+
+
+def rt_batch_step(batch, params: rt_trace_params, dt_s, nsub, alpha_B, nsteps):
+    check(lib().rt_batch_step(batch, ctypes.byref(params), float(dt_s), int(nsub), float(alpha_B), int(nsteps)))
+
+
+def rt_batch_get_budget(batch, slot) -> dict:
+    b = rt_budget()
+    check(lib().rt_batch_get_budget(batch, int(slot), ctypes.byref(b)))
+    return budget_dict(b)
+
+
+def rt_batch_autotune(batch, params: rt_trace_params) -> rt_trace_params:
+    check(lib().rt_batch_autotune(batch, ctypes.byref(params)))
+    return params
+
+
+class Batch:
+    """Convenience owner of one batch handle (marshalling only)."""
+
+    def __init__(self, ctx, stream=None):
+        self.h = rt_batch_create(ctx, stream)
+        self.grids = {}
+
+    def add(self, grid: "Grid") -> int:
+        slot = rt_batch_add(self.h, grid.h)
+        self.grids[slot] = grid
+        return slot
+
+    def remove(self, slot: int):
+        rt_batch_remove(self.h, slot)
+        self.grids.pop(slot, None)
+
+    def trace(self, sync=True, **kw):
+        rt_batch_trace(self.h, trace_params(**kw), sync)
+
+    def chem(self, dt_s, nsub=10, alpha_B=2.59e-13):
+        rt_batch_chem(self.h, dt_s, nsub, alpha_B)
+
+    def step(self, nsteps, dt_s, nsub=10, alpha_B=2.59e-13, **kw):
+        rt_batch_step(self.h, trace_params(**kw), dt_s, nsub, alpha_B, nsteps)
+
+    def budget(self, slot) -> dict:
+        return rt_batch_get_budget(self.h, slot)
+
+    def close(self):
+        if self.h:
+            rt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -41,7 +41,7 @@ def run_oracle(g, **params):
 
 
 def run_gpu(g, precision="fp64", **params):
-    p = dict(synth.DEFAULT_PARAMS)
+    p = dict(synth.DEFAULT_PARAMS, checksums=True)
     p.update(params)
     grid = native.Grid(ctx(), g, precision)
     b = grid.trace(**p)

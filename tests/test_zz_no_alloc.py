@@ -44,10 +44,10 @@ def _small_clumpy():
 def test_noalloc_matches_regular_entry_point_twice(make):
     g = make()
     grid = native.Grid(parity.ctx(), g, "fp32_mixed")
-    ref = grid.trace()
+    ref = grid.trace(checksums=True, **synth.DEFAULT_PARAMS)
     ref_rates = grid.rates()
     grid.close()
-    params = native.trace_params(**synth.DEFAULT_PARAMS)
+    params = native.trace_params(checksums=True, **synth.DEFAULT_PARAMS)
     n_HI, n_H, x_HI, kph, gamma = _device_grid(g)
     mask = ref_rates["kph"] > 1e-8 * ref_rates["kph"].max()
     for call in range(2):
