@@ -84,6 +84,8 @@ typedef struct {
                             0 = as many as fit (lower it to share the GPU) */
   int segs_per_iter;     /* segments a lane traces between queue visits; 0 = tuned */
   int flags;             /* RT_TRACE_CHECKSUMS: also fill rt_budget.hashes */
+  int passes;            /* launches over equal ranges of the sources (>= 0);
+                            0 = 1, or as many as the automatic sizing needs */
 } rt_trace_params;
 #define RT_TRACE_CHECKSUMS 1
 
@@ -99,10 +101,12 @@ typedef struct {
   uint64_t segments;                   /* cell segments with length > 0 */
   uint64_t fallbacks;                  /* FP32 crossing/split decisions re-taken in FP64 */
   uint64_t fallbacks_tau;              /* FP32 termination decisions re-taken in FP64 */
-  uint64_t queue_pushed;               /* records written to the queue */
+  uint64_t queue_pushed;               /* records written to the queue, all passes */
   int status;                          /* RT_OK or the device-side error */
-  float kernel_ms;                     /* duration of the trace kernel itself
+  float kernel_ms;                     /* duration of the trace launches themselves
                                           (CUDA events on the grid's stream) */
+  uint64_t queue_peak;                 /* records of the largest pass */
+  int passes;                          /* launches the sources were split into */
 } rt_budget;
 /* hashes[l] is the sum modulo 2^64 over created packages of
  * mix(((uint64)src << 40) ^ ((uint64)l << 34) ^ pixel), where mix is the
@@ -134,7 +138,12 @@ int rt_clear_sources(rt_grid* grid);
  * deposits, Eqs. "kph", "gamma"; termination) and reduce the photon budget.
  * out == NULL: enqueue only (no host synchronisation; may be captured in a
  * CUDA graph when queue_capacity > 0); read the result with rt_get_budget.
- * out != NULL: wait, and retry with a larger queue if it overflowed. */
+ * out != NULL: wait; with queue_capacity 0, a trace that overflowed the
+ * queue is redone with a larger queue, up to 2^31 records or half the free
+ * device memory, and beyond that as several launches ("passes") over equal
+ * ranges of the sources, which add into the same k_ph, Gamma and budget.  The
+ * pass count is kept as the start for the grid's next trace.  A single source
+ * whose packages do not fit returns RT_ERR_QUEUE_OVERFLOW. */
 int rt_trace(rt_grid* grid, const rt_trace_params* params, rt_budget* out);
 /* Result of the last trace (synchronises the grid's stream). */
 int rt_get_budget(rt_grid* grid, rt_budget* out);
@@ -165,12 +174,13 @@ int rt_get_ionised(rt_grid* grid, void* x_HII, int dtype, int mem_kind);
  * ionisation update (Step 6) for every grid.  Each grid keeps its own fields,
  * photon budget and counters; results equal those of the grid traced alone
  * (up to the order of floating-point sums).  All grids of a batch have the
- * same precision and context; while a grid is in a batch, use it only
- * through the batch (its own stream is not used).
+ * same precision and context.  Batch launches start after the work already
+ * queued on each member grid's own stream (rt_set_state, say); per-grid calls
+ * on a member wait for the batch's stream first.  Queue sizing and
+ * source passes follow rt_trace.
  * ------------------------------------------------------------------------- */
 /* stream: cudaStream_t for the batch's work; NULL = the batch creates its own
- * (a blocking stream).  Per-grid calls on a grid in a batch wait for the
- * batch's stream first. */
+ * (a blocking stream). */
 int rt_batch_create(rt_ctx* ctx, void* stream, rt_batch** out);
 int rt_batch_destroy(rt_batch* batch);
 /* Add a grid; *slot receives its slot number (reused after removal). */
@@ -179,14 +189,18 @@ int rt_batch_remove(rt_batch* batch, int slot);
 /* Number of grids in the batch. */
 int rt_batch_size(rt_batch* batch);
 /* One trace of every grid (as rt_trace; sync != 0 waits and retries a queue
- * overflow with a larger queue). */
+ * overflow with a larger queue or more passes). */
 int rt_batch_trace(rt_batch* batch, const rt_trace_params* params, int sync);
 /* Ionisation update of every grid (as rt_chem_update).  Asynchronous. */
 int rt_batch_chem(rt_batch* batch, double dt_s, int nsub, double alpha_B);
 /* nsteps coupled steps (trace, then update) of every grid.  One step is
  * captured once as a CUDA graph (after a synchronous sizing trace) and
  * replayed; it is captured again when the grids or arguments change.
- * Asynchronous after the capture. */
+ * Asynchronous after the capture.  The graph keeps the sizing trace's pass
+ * count; with queue_capacity 0 its queue holds 4x the largest pass's records
+ * plus 2^20 (within the limit rt_trace states); a replay that needs more
+ * reports RT_ERR_QUEUE_OVERFLOW through rt_batch_get_budget (its results are
+ * then invalid). */
 int rt_batch_step(rt_batch* batch, const rt_trace_params* params, double dt_s, int nsub, double alpha_B,
                   int nsteps);
 /* Result of the last trace for the grid in `slot` (synchronises). */
@@ -215,7 +229,8 @@ int rt_selfcheck_directions(rt_ctx* ctx, int level, double* max_abs_err, double*
  * process exits.  It calls no cudaMalloc, cudaFree or other allocating
  * routine.  Limits: at most RT_NOALLOC_MAX_SOURCES sources and
  * RT_NOALLOC_MAX_RECORDS queue records per call (a larger trace returns
- * RT_ERR_QUEUE_OVERFLOW); queue_capacity, if set, must not exceed the latter.
+ * RT_ERR_QUEUE_OVERFLOW); queue_capacity, if set, must not exceed the latter;
+ * the trace runs as one pass (params->passes 0 or 1).
  *
  * Every call shares the static array, and each call clears what must start
  * at zero; calls whose work overlaps on the GPU (other streams or host

@@ -16,7 +16,7 @@
 #include "rt_internal.cuh"
 
 namespace rtg {
-cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, cudaStream_t st);
+cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass, cudaStream_t st);
 cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm);
 cudaError_t launch_trace(int precision, const TraceArgs& A, int grid, int block, cudaStream_t st);
 cudaError_t launch_chem(int precision, long long ncell, const double* nH, double* xHI, double* xHII,
@@ -103,6 +103,8 @@ struct TraceState {
   unsigned long long cap = 0;  // records
   size_t rec_bytes = 0;
   unsigned long long* ctl = nullptr;
+  int passes = 1;       // source ranges the last automatically sized trace used
+  int passes_run = 1;   // passes of the last trace launched
   ~TraceState() {
     if (queue) cudaFree(queue);
     if (ctl) cudaFree(ctl);
@@ -255,7 +257,7 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
   I.nx = g->nx; I.ny = g->ny; I.nz = g->nz; I.pad = 0;
   I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.xHII = g->xHII; I.K = g->K; I.G = g->G; I.acc = g->acc;
   I.cnt = g->cnt;
-  if (e == cudaSuccess) e = cudaMemcpy(g->inst_dev, &I, sizeof I, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->inst_dev, &I, sizeof I, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMallocHost(&g->host_rb, 4096);
   if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
@@ -382,6 +384,7 @@ static int check_params(const rt_trace_params* p) {
   if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32)
     return fail(RT_ERR_INVALID_ARG, "rt_trace: blocks_per_sm = %d", p->blocks_per_sm);
   if (p->segs_per_iter < 0 || p->segs_per_iter > 1024) return fail(RT_ERR_INVALID_ARG, "rt_trace: segs_per_iter = %d", p->segs_per_iter);
+  if (p->passes < 0) return fail(RT_ERR_INVALID_ARG, "rt_trace: passes = %d", p->passes);
   return RT_OK;
 }
 
@@ -394,13 +397,90 @@ static int ensure_queue(rt_grid* g, unsigned long long cap) {
   g->ts.cap = 0;
   CUDA_TRY(cudaMalloc(&g->ts.queue, cap * rec));
   // tags start at 0; epochs start at 1
-  CUDA_TRY(cudaMemset(g->ts.queue, 0, cap * rec));
+  CUDA_TRY(cudaMemsetAsync(g->ts.queue, 0, cap * rec, g->stream));
   g->ts.cap = cap;
   g->ts.rec_bytes = rec;
   return RT_OK;
 }
 
-static int enqueue_trace(rt_grid* g, const rt_trace_params* p) {
+static void fill_common_args(TraceArgs& A, const rt_trace_params* p) {
+  for (int l = 0; l < kLevels; ++l) {
+    // Eq. "split": Phi = N_pix dx^2 / (4 pi R^2) < Phi_c  <=>  R > R_split(l)
+    A.rsplit[l] = sqrt((12.0 * ldexp(1.0, 2 * l)) / (4.0 * M_PI * p->phi_c));
+    A.rsplit32[l] = (float)A.rsplit[l];
+    A.rsplit32lo[l] = (float)(A.rsplit[l] - (double)A.rsplit32[l]);
+  }
+  A.level0 = p->level0;
+  A.max_level = p->max_level;
+  A.tau_term = -log(p->f_term);
+  A.tau_term32 = (float)A.tau_term;
+  A.timeout_ns = (long long)((p->timeout_s > 0 ? p->timeout_s : 2.0) * 1e9);
+  A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 8;
+  A.checksums = (p->flags & RT_TRACE_CHECKSUMS) != 0;
+}
+
+// One trace as `passes` launches of the trace kernel over consecutive, equal
+// ranges of the sources, for traces whose packages do not fit the queue at
+// once; deposits, budget sums and counters accumulate across the passes.
+// A.npix0, A.queue, A.cap, A.ctl and the per-trace fields are set by the
+// caller; A.src, A.nsrc and A.n_roots are set here per pass.
+static int launch_passes(TraceArgs A, const SourceDev* src, int nsrc, int passes, int precision, int blocks,
+                         cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st) {
+  if (passes > nsrc) passes = nsrc;
+  if (passes < 1) passes = 1;
+  for (int i = 0; i < passes; ++i) {
+    const int s0 = (int)((long long)nsrc * i / passes);
+    const int s1 = (int)((long long)nsrc * (i + 1) / passes);
+    const unsigned long long n = (unsigned long long)A.npix0 * (unsigned long long)(s1 - s0);
+    LAUNCH_TRY(launch_trace_init(A.ctl, n, i == 0, st));
+    if (i == 0) CUDA_TRY(cudaEventRecord(ev0, st));
+    if (n == 0) continue;
+    A.src = src + s0;
+    A.nsrc = s1 - s0;
+    A.n_roots = n;
+    LAUNCH_TRY(launch_trace(precision, A, blocks, 256, st));
+  }
+  CUDA_TRY(cudaEventRecord(ev1, st));
+  return RT_OK;
+}
+
+// Largest automatically sized queue: 2^31 records, and at most half of the
+// device memory that is free (counting the queue it would replace).
+static unsigned long long queue_cap_limit(size_t rec, size_t held_bytes) {
+  unsigned long long lim = 1ULL << 31;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+    const unsigned long long m = ((unsigned long long)fr + held_bytes) / 2 / rec;
+    if (m < lim) lim = m;
+  } else {
+    cudaGetLastError();
+  }
+  if (lim < (1ULL << 20)) lim = 1ULL << 20;
+  return lim;
+}
+
+// Next attempt after a queue overflow of an automatically sized trace: grow
+// the queue up to `limit` records, then split the sources into more passes.
+// `peak` (records of the largest pass) undercounts the need, because dropped
+// children were never expanded.  False when neither is possible.
+static bool grow_after_overflow(unsigned long long peak, unsigned long long limit, int nsrc,
+                                unsigned long long* cap, int* passes) {
+  if (*cap < limit) {
+    const unsigned long long need = peak + peak / 4 + 1024;
+    *cap = need > 4 * *cap ? need : 4 * *cap;
+    if (*cap > limit) *cap = limit;
+    return true;
+  }
+  if (*passes >= nsrc) return false;
+  long long np = 2LL * *passes;
+  const long long want = (long long)*passes * (long long)(peak / (limit / 2 + 1) + 1);
+  if (want > np) np = want;
+  if (np > nsrc) np = nsrc;
+  *passes = (int)np;
+  return true;
+}
+
+static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes) {
   int rc = prepare_sources(g, p->level0);
   if (rc) return rc;
   cudaStream_t st = g->stream;
@@ -409,29 +489,19 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p) {
   CUDA_TRY(cudaMemsetAsync(g->G, 0, ne, st));
   CUDA_TRY(cudaMemsetAsync(g->acc, 0, 4 * sizeof(double), st));
   CUDA_TRY(cudaMemsetAsync(g->cnt, 0, kCntWords * sizeof(unsigned long long), st));
-  const unsigned long long npix0 = 12ULL << (2 * p->level0);
-  const unsigned long long n_roots = npix0 * (unsigned long long)g->src.size();
-  LAUNCH_TRY(launch_trace_init(g->ts.ctl, n_roots, st));
-  if (n_roots == 0) {
+  const int nsrc = (int)g->src.size();
+  if (nsrc == 0) {
+    LAUNCH_TRY(launch_trace_init(g->ts.ctl, 0, 1, st));
     g->traced = false;
+    g->ts.passes_run = 0;
     return RT_OK;
   }
   TraceArgs A;
   memset(&A, 0, sizeof A);
+  fill_common_args(A, p);
   A.inst = g->inst_dev;
   A.ninst = 1;
-  A.src = g->src_dev;
-  A.nsrc = (int)g->src.size();
-  A.level0 = p->level0;
-  A.max_level = p->max_level;
-  A.npix0 = (uint32_t)npix0;
-  A.n_roots = n_roots;
-  for (int l = 0; l < kLevels; ++l) {
-    // Eq. "split": Phi = N_pix dx^2 / (4 pi R^2) < Phi_c  <=>  R > R_split(l)
-    A.rsplit[l] = sqrt((12.0 * ldexp(1.0, 2 * l)) / (4.0 * M_PI * p->phi_c));
-    A.rsplit32[l] = (float)A.rsplit[l];
-    A.rsplit32lo[l] = (float)(A.rsplit[l] - (double)A.rsplit32[l]);
-  }
+  A.npix0 = (uint32_t)(12u << (2 * p->level0));
   A.dir_tab = nullptr;
   A.dir_levels = -1;
   if (g->precision == RT_FP32_MIXED) {
@@ -445,24 +515,19 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p) {
     A.dir_tab = g->ctx->dir_tab;
     A.dir_levels = g->ctx->dir_levels;
   }
-  A.tau_term = -log(p->f_term);
-  A.tau_term32 = (float)A.tau_term;
   A.queue = g->ts.queue;
   A.cap = g->ts.cap;
   A.ctl = g->ts.ctl;
-  A.timeout_ns = (long long)((p->timeout_s > 0 ? p->timeout_s : 2.0) * 1e9);
-  A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 8;
   A.max_steps = 2 * (g->nx + g->ny + g->nz) + 16;
-  A.checksums = (p->flags & RT_TRACE_CHECKSUMS) != 0;
   const int block = 256;  // the trace kernel is compiled for 256-thread blocks
   int per_sm = 0;
   CUDA_TRY(trace_occupancy(g->precision, block, &per_sm));
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
-  CUDA_TRY(cudaEventRecord(g->ev0, st));
-  LAUNCH_TRY(launch_trace(g->precision, A, per_sm * g->ctx->num_sms, block, st));
-  CUDA_TRY(cudaEventRecord(g->ev1, st));
+  if ((rc = launch_passes(A, g->src_dev, nsrc, passes, g->precision, per_sm * g->ctx->num_sms, g->ev0, g->ev1, st)))
+    return rc;
   g->traced = true;
+  g->ts.passes_run = passes < nsrc ? passes : nsrc;
   return RT_OK;
 }
 
@@ -486,7 +551,9 @@ static int read_budget(rt_grid* g, rt_budget* out) {
   out->segments = hcnt[kCntSegments];
   out->fallbacks = hcnt[kCntFallbacks];
   out->fallbacks_tau = hcnt[kCntFallbacksTau];
-  out->queue_pushed = hctl[CTL_TAIL];
+  out->queue_pushed = hctl[CTL_PUSHED] + hctl[CTL_TAIL];
+  out->queue_peak = hctl[CTL_PEAK] > hctl[CTL_TAIL] ? hctl[CTL_PEAK] : hctl[CTL_TAIL];
+  out->passes = g->ts.passes_run;
   out->status = (int)hctl[CTL_STATUS];
   float ms = 0.f;
   if (g->traced && cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) out->kernel_ms = ms;
@@ -510,20 +577,23 @@ int rt_trace(rt_grid* g, const rt_trace_params* p, rt_budget* out) {
       if (cap > (1ULL << 26)) cap = 1ULL << 26;
     }
   }
+  const size_t rec = g->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+  const int p_min = p->passes > 1 ? p->passes : 1;
+  int passes = automatic && g->ts.passes > p_min ? g->ts.passes : p_min;
+  const int nsrc = (int)g->src.size();
   for (int attempt = 0;; ++attempt) {
     if ((rc = ensure_queue(g, cap))) return rc;
-    if ((rc = enqueue_trace(g, p))) return rc;
+    if ((rc = enqueue_trace(g, p, passes))) return rc;
     if (!out) return RT_OK;
     if ((rc = read_budget(g, out))) return rc;
-    if (out->status == RT_ERR_QUEUE_OVERFLOW && automatic && attempt < 6) {
-      unsigned long long need = out->queue_pushed + out->queue_pushed / 4 + 1024;
-      cap = need > 4 * cap ? need : 4 * cap;
-      if (cap > (1ULL << 31)) cap = 1ULL << 31;
-      continue;
+    if (out->status == RT_ERR_QUEUE_OVERFLOW && automatic && attempt < 40) {
+      const unsigned long long limit = queue_cap_limit(rec, (size_t)g->ts.cap * g->ts.rec_bytes);
+      if (grow_after_overflow(out->queue_peak, limit, nsrc, &cap, &passes)) continue;
     }
     if (out->status != RT_OK)
-      return fail(out->status, "rt_trace: device status %d (queue capacity %llu, pushed %llu)", out->status,
-                  (unsigned long long)g->ts.cap, (unsigned long long)out->queue_pushed);
+      return fail(out->status, "rt_trace: device status %d (queue capacity %llu, largest pass %llu, passes %d)",
+                  out->status, (unsigned long long)g->ts.cap, (unsigned long long)out->queue_peak, out->passes);
+    if (automatic) g->ts.passes = passes > p_min && 4 * out->queue_peak < g->ts.cap ? passes / 2 : passes;
     return RT_OK;
   }
 }
@@ -683,6 +753,7 @@ struct rt_batch {
   // captured step graph and the arguments it was captured with
   cudaGraphExec_t graph = nullptr;
   bool graph_ok = false;
+  unsigned long long graph_launches = 0;  // kernels one replay runs
   rt_trace_params gp;
   double g_dt = 0, g_alpha = 0;
   int g_nsub = 0;
@@ -697,21 +768,6 @@ struct rt_batch {
   }
 };
 
-static void fill_common_args(TraceArgs& A, const rt_trace_params* p) {
-  for (int l = 0; l < kLevels; ++l) {
-    // Eq. "split": Phi = N_pix dx^2 / (4 pi R^2) < Phi_c  <=>  R > R_split(l)
-    A.rsplit[l] = sqrt((12.0 * ldexp(1.0, 2 * l)) / (4.0 * M_PI * p->phi_c));
-    A.rsplit32[l] = (float)A.rsplit[l];
-    A.rsplit32lo[l] = (float)(A.rsplit[l] - (double)A.rsplit32[l]);
-  }
-  A.level0 = p->level0;
-  A.max_level = p->max_level;
-  A.tau_term = -log(p->f_term);
-  A.tau_term32 = (float)A.tau_term;
-  A.timeout_ns = (long long)((p->timeout_s > 0 ? p->timeout_s : 2.0) * 1e9);
-  A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 8;
-  A.checksums = (p->flags & RT_TRACE_CHECKSUMS) != 0;
-}
 
 static int batch_rebuild(rt_batch* b, int level0) {
   if (!b->dirty && b->built_level0 == level0) return RT_OK;
@@ -753,8 +809,13 @@ static int batch_rebuild(rt_batch* b, int level0) {
     CUDA_TRY(cudaMalloc((void**)&b->src_dev, src.size() * sizeof(SourceDev)));
     b->src_cap = src.size();
   }
-  if (!inst.empty()) CUDA_TRY(cudaMemcpy(b->inst_dev, inst.data(), inst.size() * sizeof(InstDev), cudaMemcpyHostToDevice));
-  if (!src.empty()) CUDA_TRY(cudaMemcpy(b->src_dev, src.data(), src.size() * sizeof(SourceDev), cudaMemcpyHostToDevice));
+  // on the batch's stream (which may not be ordered with the legacy stream);
+  // the host vectors live until the copies end
+  if (!inst.empty())
+    CUDA_TRY(cudaMemcpyAsync(b->inst_dev, inst.data(), inst.size() * sizeof(InstDev), cudaMemcpyHostToDevice, b->stream));
+  if (!src.empty())
+    CUDA_TRY(cudaMemcpyAsync(b->src_dev, src.data(), src.size() * sizeof(SourceDev), cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
   b->nsrc = (int)src.size();
   b->n_roots = (12ULL << (2 * level0)) * (unsigned long long)src.size();
   b->max_diag = diag;
@@ -764,15 +825,16 @@ static int batch_rebuild(rt_batch* b, int level0) {
   return RT_OK;
 }
 
-static int batch_enqueue(rt_batch* b, const rt_trace_params* p) {
+static int batch_enqueue(rt_batch* b, const rt_trace_params* p, int passes) {
   int rc = batch_rebuild(b, p->level0);
   if (rc) return rc;
   const int ninst = (int)b->dev_slot.size();
   cudaStream_t st = b->stream;
   LAUNCH_TRY(launch_batch_zero(b->inst_dev, ninst, b->precision, b->max_cells, st));  // Step 2
-  LAUNCH_TRY(launch_trace_init(b->ts.ctl, b->n_roots, st));
-  if (b->n_roots == 0) {
+  if (b->nsrc == 0) {
+    LAUNCH_TRY(launch_trace_init(b->ts.ctl, 0, 1, st));
     b->traced = false;
+    b->ts.passes_run = 0;
     return RT_OK;
   }
   TraceArgs A;
@@ -780,10 +842,7 @@ static int batch_enqueue(rt_batch* b, const rt_trace_params* p) {
   fill_common_args(A, p);
   A.inst = b->inst_dev;
   A.ninst = ninst;
-  A.src = b->src_dev;
-  A.nsrc = b->nsrc;
   A.npix0 = (uint32_t)(12u << (2 * p->level0));
-  A.n_roots = b->n_roots;
   A.queue = b->ts.queue;
   A.cap = b->ts.cap;
   A.ctl = b->ts.ctl;
@@ -803,10 +862,11 @@ static int batch_enqueue(rt_batch* b, const rt_trace_params* p) {
   CUDA_TRY(trace_occupancy(b->precision, 256, &per_sm));
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
-  CUDA_TRY(cudaEventRecord(b->ev0, st));
-  LAUNCH_TRY(launch_trace(b->precision, A, per_sm * b->ctx->num_sms, 256, st));
-  CUDA_TRY(cudaEventRecord(b->ev1, st));
+  if ((rc = launch_passes(A, b->src_dev, b->nsrc, passes, b->precision, per_sm * b->ctx->num_sms, b->ev0, b->ev1,
+                          st)))
+    return rc;
   b->traced = true;
+  b->ts.passes_run = passes < b->nsrc ? passes : b->nsrc;
   return RT_OK;
 }
 
@@ -818,7 +878,7 @@ static int batch_ensure_queue(rt_batch* b, unsigned long long cap) {
   b->ts.queue = nullptr;
   b->ts.cap = 0;
   CUDA_TRY(cudaMalloc(&b->ts.queue, cap * rec));
-  CUDA_TRY(cudaMemset(b->ts.queue, 0, cap * rec));
+  CUDA_TRY(cudaMemsetAsync(b->ts.queue, 0, cap * rec, b->stream));
   b->ts.cap = cap;
   b->ts.rec_bytes = rec;
   b->graph_ok = false;
@@ -826,15 +886,23 @@ static int batch_ensure_queue(rt_batch* b, unsigned long long cap) {
 }
 
 // status and queue use of the batch's last trace (synchronises)
-static int batch_status(rt_batch* b, int* status, unsigned long long* pushed, float* ms) {
+struct BatchStatus {
+  int status;
+  unsigned long long pushed;  // records, all passes
+  unsigned long long peak;    // records of the largest pass
+  float ms;
+};
+
+static int batch_status(rt_batch* b, BatchStatus* bs) {
   unsigned long long* hctl = (unsigned long long*)b->host_rb;
   CUDA_TRY(cudaMemcpyAsync(hctl, b->ts.ctl, CTL_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream));
   CUDA_TRY(cudaStreamSynchronize(b->stream));
-  *status = (int)hctl[CTL_STATUS];
-  *pushed = hctl[CTL_TAIL];
-  *ms = 0.f;
-  if (b->traced && cudaEventElapsedTime(ms, b->ev0, b->ev1) != cudaSuccess) {
-    *ms = 0.f;
+  bs->status = (int)hctl[CTL_STATUS];
+  bs->pushed = hctl[CTL_PUSHED] + hctl[CTL_TAIL];
+  bs->peak = hctl[CTL_PEAK] > hctl[CTL_TAIL] ? hctl[CTL_PEAK] : hctl[CTL_TAIL];
+  bs->ms = 0.f;
+  if (b->traced && cudaEventElapsedTime(&bs->ms, b->ev0, b->ev1) != cudaSuccess) {
+    bs->ms = 0.f;
     cudaGetLastError();
   }
   return RT_OK;
@@ -855,7 +923,8 @@ int rt_batch_create(rt_ctx* ctx, void* stream, rt_batch** out) {
     b->own_stream = true;
   }
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->ts.ctl, CTL_N * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMemset(b->ts.ctl, 0, CTL_N * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ts.ctl, 0, CTL_N * sizeof(unsigned long long), b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
   if (e == cudaSuccess) e = cudaMallocHost(&b->host_rb, 4096);
@@ -919,12 +988,21 @@ int rt_batch_size(rt_batch* b) {
   return n;
 }
 
+// per-grid calls (rt_set_state, rt_trace, ...) run on each grid's own stream;
+// a batch launch reads every member, so it starts after them
+static int sync_members(rt_batch* b) {
+  for (rt_grid* g : b->slots)
+    if (g) CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return RT_OK;
+}
+
 int rt_batch_trace(rt_batch* b, const rt_trace_params* p, int sync) {
   if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_trace: batch is NULL");
   int rc = check_params(p);
   if (rc) return rc;
   CUDA_TRY(cudaSetDevice(b->ctx->device));
   if (rt_batch_size(b) == 0) return RT_OK;
+  if ((rc = sync_members(b))) return rc;
   unsigned long long cap = (unsigned long long)p->queue_capacity;
   const bool automatic = cap == 0;
   if (automatic) {
@@ -937,23 +1015,23 @@ int rt_batch_trace(rt_batch* b, const rt_trace_params* p, int sync) {
       if (cap > (1ULL << 26)) cap = 1ULL << 26;
     }
   }
+  const size_t rec = b->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+  const int p_min = p->passes > 1 ? p->passes : 1;
+  int passes = automatic && b->ts.passes > p_min ? b->ts.passes : p_min;
   for (int attempt = 0;; ++attempt) {
     if ((rc = batch_ensure_queue(b, cap))) return rc;
-    if ((rc = batch_enqueue(b, p))) return rc;
+    if ((rc = batch_enqueue(b, p, passes))) return rc;
     if (!sync) return RT_OK;
-    int status;
-    unsigned long long pushed;
-    float ms;
-    if ((rc = batch_status(b, &status, &pushed, &ms))) return rc;
-    if (status == RT_ERR_QUEUE_OVERFLOW && automatic && attempt < 6) {
-      unsigned long long need = pushed + pushed / 4 + 1024;
-      cap = need > 4 * cap ? need : 4 * cap;
-      if (cap > (1ULL << 31)) cap = 1ULL << 31;
-      continue;
+    BatchStatus bs;
+    if ((rc = batch_status(b, &bs))) return rc;
+    if (bs.status == RT_ERR_QUEUE_OVERFLOW && automatic && attempt < 40) {
+      const unsigned long long limit = queue_cap_limit(rec, (size_t)b->ts.cap * b->ts.rec_bytes);
+      if (grow_after_overflow(bs.peak, limit, b->nsrc, &cap, &passes)) continue;
     }
-    if (status != RT_OK)
-      return fail(status, "rt_batch_trace: device status %d (queue capacity %llu, pushed %llu)", status,
-                  (unsigned long long)b->ts.cap, pushed);
+    if (bs.status != RT_OK)
+      return fail(bs.status, "rt_batch_trace: device status %d (queue capacity %llu, largest pass %llu, passes %d)",
+                  bs.status, (unsigned long long)b->ts.cap, bs.peak, b->ts.passes_run);
+    if (automatic) b->ts.passes = passes > p_min && 4 * bs.peak < b->ts.cap ? passes / 2 : passes;
     return RT_OK;
   }
 }
@@ -964,6 +1042,7 @@ int rt_batch_chem(rt_batch* b, double dt_s, int nsub, double alpha_B) {
     return fail(RT_ERR_INVALID_ARG, "rt_batch_chem: bad dt_s / nsub / alpha_B");
   CUDA_TRY(cudaSetDevice(b->ctx->device));
   if (rt_batch_size(b) == 0) return RT_OK;
+  if (int rcs = sync_members(b)) return rcs;
   if (b->dirty) {
     int rc = batch_rebuild(b, b->built_level0 >= 0 ? b->built_level0 : 1);
     if (rc) return rc;
@@ -976,7 +1055,7 @@ int rt_batch_chem(rt_batch* b, double dt_s, int nsub, double alpha_B) {
 static bool same_params(const rt_trace_params& a, const rt_trace_params& b) {
   return a.level0 == b.level0 && a.phi_c == b.phi_c && a.f_term == b.f_term && a.max_level == b.max_level &&
          a.queue_capacity == b.queue_capacity && a.timeout_s == b.timeout_s && a.blocks_per_sm == b.blocks_per_sm &&
-         a.segs_per_iter == b.segs_per_iter && a.flags == b.flags;
+         a.segs_per_iter == b.segs_per_iter && a.flags == b.flags && a.passes == b.passes;
 }
 
 int rt_batch_step(rt_batch* b, const rt_trace_params* p, double dt_s, int nsub, double alpha_B, int nsteps) {
@@ -987,6 +1066,7 @@ int rt_batch_step(rt_batch* b, const rt_trace_params* p, double dt_s, int nsub, 
     return fail(RT_ERR_INVALID_ARG, "rt_batch_step: bad nsteps / dt_s / nsub / alpha_B");
   CUDA_TRY(cudaSetDevice(b->ctx->device));
   if (rt_batch_size(b) == 0 || nsteps == 0) return RT_OK;
+  if ((rc = sync_members(b))) return rc;
   const bool reuse = b->graph_ok && !b->dirty && b->built_level0 == p->level0 && same_params(b->gp, *p) &&
                      b->g_dt == dt_s && b->g_nsub == nsub && b->g_alpha == alpha_B;
   if (!reuse) {
@@ -994,12 +1074,15 @@ int rt_batch_step(rt_batch* b, const rt_trace_params* p, double dt_s, int nsub, 
     // capture one step -- zero, emit, trace, update -- as a graph
     rt_trace_params q = *p;
     if ((rc = rt_batch_trace(b, &q, 1))) return rc;
+    const int passes = b->ts.passes_run > 0 ? b->ts.passes_run : 1;
     if (q.queue_capacity == 0) {
-      int status;
-      unsigned long long pushed;
-      float ms;
-      if ((rc = batch_status(b, &status, &pushed, &ms))) return rc;
-      unsigned long long need = pushed + pushed / 2 + (1ULL << 16);
+      BatchStatus bs;
+      if ((rc = batch_status(b, &bs))) return rc;
+      // headroom: the media evolve between replays, and traces grow as they ionise
+      const size_t rec = b->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+      const unsigned long long limit = queue_cap_limit(rec, (size_t)b->ts.cap * b->ts.rec_bytes);
+      unsigned long long need = 4 * bs.peak + (1ULL << 20);
+      if (need > limit) need = limit;
       if (need > b->ts.cap && (rc = batch_ensure_queue(b, need))) return rc;
       q.queue_capacity = (int64_t)b->ts.cap;
     }
@@ -1010,10 +1093,11 @@ int rt_batch_step(rt_batch* b, const rt_trace_params* p, double dt_s, int nsub, 
     cudaGraph_t graph = nullptr;
     const unsigned long long launches_before = g_launches.load();
     CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    int rc1 = batch_enqueue(b, &q);
+    int rc1 = batch_enqueue(b, &q, passes);
     cudaError_t e1 = launch_batch_chem(b->inst_dev, (int)b->dev_slot.size(), b->precision, b->max_cells,
                                        dt_s / nsub, nsub, alpha_B, b->stream);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    b->graph_launches = g_launches.load() - launches_before + 1;  // + the update
     g_launches.store(launches_before);  // captured kernels count when the graph runs
     if (rc1) { if (graph) cudaGraphDestroy(graph); return rc1; }
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
@@ -1031,7 +1115,7 @@ int rt_batch_step(rt_batch* b, const rt_trace_params* p, double dt_s, int nsub, 
   }
   for (int i = 0; i < nsteps; ++i) {
     CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
-    g_launches.fetch_add(4);  // zero, init, trace, chemistry
+    g_launches.fetch_add(b->graph_launches);
   }
   return RT_OK;
 }
@@ -1039,11 +1123,10 @@ int rt_batch_step(rt_batch* b, const rt_trace_params* p, double dt_s, int nsub, 
 int rt_batch_get_budget(rt_batch* b, int slot, rt_budget* out) {
   if (!b || !out || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot])
     return fail(RT_ERR_INVALID_ARG, "rt_batch_get_budget: no grid in slot %d", slot);
-  int status;
-  unsigned long long pushed;
-  float ms;
-  int rc = batch_status(b, &status, &pushed, &ms);
+  BatchStatus bs;
+  int rc = batch_status(b, &bs);
   if (rc) return rc;
+  const int status = bs.status;
   rt_grid* g = b->slots[slot];
   double* hacc = (double*)g->host_rb;
   unsigned long long* hcnt = (unsigned long long*)((char*)g->host_rb + 64);
@@ -1061,9 +1144,11 @@ int rt_batch_get_budget(rt_batch* b, int slot, rt_budget* out) {
   out->segments = hcnt[kCntSegments];
   out->fallbacks = hcnt[kCntFallbacks];
   out->fallbacks_tau = hcnt[kCntFallbacksTau];
-  out->queue_pushed = pushed;
+  out->queue_pushed = bs.pushed;
+  out->queue_peak = bs.peak;
+  out->passes = b->ts.passes_run;
   out->status = status;
-  out->kernel_ms = ms;
+  out->kernel_ms = bs.ms;
   if (status != RT_OK) return fail(status, "rt_batch_get_budget: device status %d", status);
   return RT_OK;
 }
@@ -1089,11 +1174,9 @@ int rt_batch_autotune(rt_batch* b, rt_trace_params* p) {
       float tmin = 1e30f;
       for (int rep = 0; rep < 2; ++rep) {
         if ((rc = rt_batch_trace(b, &q, 1))) return rc;
-        int status;
-        unsigned long long pushed;
-        float ms;
-        if ((rc = batch_status(b, &status, &pushed, &ms))) return rc;
-        if (ms < tmin) tmin = ms;
+        BatchStatus bs;
+        if ((rc = batch_status(b, &bs))) return rc;
+        if (bs.ms < tmin) tmin = bs.ms;
       }
       if (tmin < best) {
         best = tmin;

@@ -30,7 +30,7 @@
 #include "rt_internal.cuh"
 
 namespace rtg {
-cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, cudaStream_t st);
+cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass, cudaStream_t st);
 cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm);
 cudaError_t launch_trace(int precision, const TraceArgs& A, int grid, int block, cudaStream_t st);
 cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st);
@@ -119,7 +119,7 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
   if (nsrc > 0 && (!pos_cm || !ndot || !e_ph_eV || !sigma_cm2)) return na_fail(RT_ERR_INVALID_ARG, "source arrays");
   if (p->level0 < 0 || p->max_level < p->level0 || p->max_level > RT_MAX_LEVEL || !(p->phi_c > 0) ||
       !(p->f_term > 0 && p->f_term < 1) || p->segs_per_iter < 0 || p->segs_per_iter > 1024 ||
-      p->blocks_per_sm < 0 || p->blocks_per_sm > 32)
+      p->blocks_per_sm < 0 || p->blocks_per_sm > 32 || p->passes < 0 || p->passes > 1)
     return na_fail(RT_ERR_INVALID_ARG, "trace parameters");
   if (p->queue_capacity > RT_NOALLOC_MAX_RECORDS)
     return na_fail(RT_ERR_INVALID_ARG, "queue_capacity above RT_NOALLOC_MAX_RECORDS (262144)");
@@ -200,7 +200,7 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
   }
 
   const unsigned long long n_roots = (unsigned long long)npix0 * (unsigned long long)nsrc;
-  if ((e = launch_trace_init(ctl, n_roots, st)) != cudaSuccess) return na_fail(RT_ERR_CUDA, "trace init", e);
+  if ((e = launch_trace_init(ctl, n_roots, 1, st)) != cudaSuccess) return na_fail(RT_ERR_CUDA, "trace init", e);
   if (n_roots > 0) {
     TraceArgs A;
     memset(&A, 0, sizeof A);

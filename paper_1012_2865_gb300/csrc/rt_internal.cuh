@@ -19,6 +19,8 @@ enum CtlWord {
   CTL_OUTSTANDING = 2,  // live packages (signed)
   CTL_STATUS = 3,       // RT_OK or first device error (atomicCAS)
   CTL_EPOCH = 4,        // tag of this trace's queue records
+  CTL_PEAK = 5,         // largest TAIL of the earlier passes of this trace
+  CTL_PUSHED = 6,       // sum of TAIL over the earlier passes of this trace
   CTL_N = 8
 };
 

@@ -804,19 +804,31 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   }
 }
 
-__global__ void trace_init_kernel(unsigned long long* ctl, unsigned long long n_roots) {
+// Resets the queue for one pass.  A trace may run as several passes over
+// ranges of its sources; the status of earlier passes stays (the first error
+// wins) and their queue use is folded into CTL_PEAK / CTL_PUSHED.
+__global__ void trace_init_kernel(unsigned long long* ctl, unsigned long long n_roots, int first_pass) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (first_pass) {
+      ctl[CTL_STATUS] = 0;
+      ctl[CTL_PEAK] = 0;
+      ctl[CTL_PUSHED] = 0;
+    } else {
+      const unsigned long long t = ctl[CTL_TAIL];
+      if (t > ctl[CTL_PEAK]) ctl[CTL_PEAK] = t;
+      ctl[CTL_PUSHED] += t;
+    }
     ctl[CTL_HEAD] = 0;
     ctl[CTL_TAIL] = 0;
     ctl[CTL_OUTSTANDING] = n_roots;
-    ctl[CTL_STATUS] = 0;
     ctl[CTL_EPOCH] = ctl[CTL_EPOCH] + 1;
   }
 }
 
 // Host-side launch helpers (called from api.cu).
-cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, cudaStream_t st) {
-  trace_init_kernel<<<1, 32, 0, st>>>(ctl, n_roots);
+cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass,
+                              cudaStream_t st) {
+  trace_init_kernel<<<1, 32, 0, st>>>(ctl, n_roots, first_pass);
   return cudaGetLastError();
 }
 

@@ -54,7 +54,7 @@ class rt_trace_params(ctypes.Structure):
     _fields_ = [("level0", ctypes.c_int), ("phi_c", ctypes.c_double), ("f_term", ctypes.c_double),
                 ("max_level", ctypes.c_int), ("queue_capacity", ctypes.c_int64),
                 ("timeout_s", ctypes.c_double), ("blocks_per_sm", ctypes.c_int),
-                ("segs_per_iter", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("segs_per_iter", ctypes.c_int), ("flags", ctypes.c_int), ("passes", ctypes.c_int)]
 
 
 class rt_budget(ctypes.Structure):
@@ -63,7 +63,8 @@ class rt_budget(ctypes.Structure):
                 ("hashes", ctypes.c_uint64 * NLEV), ("segments", ctypes.c_uint64),
                 ("fallbacks", ctypes.c_uint64), ("fallbacks_tau", ctypes.c_uint64),
                 ("queue_pushed", ctypes.c_uint64),
-                ("status", ctypes.c_int), ("kernel_ms", ctypes.c_float)]
+                ("status", ctypes.c_int), ("kernel_ms", ctypes.c_float),
+                ("queue_peak", ctypes.c_uint64), ("passes", ctypes.c_int)]
 
 
 class rt_noalloc_grid(ctypes.Structure):
@@ -194,10 +195,11 @@ def rt_clear_sources(grid):
 
 
 def trace_params(level0=1, phi_c=5.1, f_term=1e-10, max_level=RT_MAX_LEVEL, queue_capacity=0,
-                 timeout_s=2.0, blocks_per_sm=0, segs_per_iter=0, checksums=False) -> rt_trace_params:
+                 timeout_s=2.0, blocks_per_sm=0, segs_per_iter=0, checksums=False,
+                 passes=0) -> rt_trace_params:
     return rt_trace_params(int(level0), float(phi_c), float(f_term), int(max_level),
                            int(queue_capacity), float(timeout_s), int(blocks_per_sm),
-                           int(segs_per_iter), RT_TRACE_CHECKSUMS if checksums else 0)
+                           int(segs_per_iter), RT_TRACE_CHECKSUMS if checksums else 0, int(passes))
 
 
 def budget_dict(b: rt_budget) -> dict:
@@ -205,7 +207,8 @@ def budget_dict(b: rt_budget) -> dict:
                 counts=np.array(b.counts[:], dtype=np.uint64),
                 hashes=np.array(b.hashes[:], dtype=np.uint64), segments=int(b.segments),
                 fallbacks=int(b.fallbacks), fallbacks_tau=int(b.fallbacks_tau),
-                queue_pushed=int(b.queue_pushed), status=int(b.status),
+                queue_pushed=int(b.queue_pushed), queue_peak=int(b.queue_peak), passes=int(b.passes),
+                status=int(b.status),
                 kernel_ms=float(b.kernel_ms))
 
 

@@ -1,0 +1,190 @@
+"""Continuous-batching request loop for radiative-transfer solves.
+
+A request is one grid (medium + sources) advanced by `nsteps` coupled steps
+(rt_trace + rt_chem_update).  The server keeps the grids of all admitted
+requests resident on the device in one rt_batch; every step advances all of
+them with one persistent trace launch and one update launch.  Requests that
+arrive while others run are admitted between steps when a slot is free and
+the device has room for their grid (free HBM minus a reserve); finished
+requests are read back to the host and leave the batch.  All computation
+runs in librt_gb300.so; this module only schedules.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import native, synth
+
+
+def grid_bytes(ncell: int, precision: str) -> int:
+    """Device bytes of one grid: n_H, x_HI, x_HII (FP64) + n_HI, k_ph, Gamma."""
+    e = 8 if precision == "fp64" else 4
+    return ncell * (24 + 3 * e)
+
+
+@dataclass
+class Request:
+    rid: int
+    grid: dict
+    nsteps: int
+    arrival: float = 0.0      # seconds on the server clock
+    admitted: float = -1.0
+    finished: float = -1.0
+    steps_done: int = 0
+    slot: int = -1
+    handle: object = None
+    x_HI: np.ndarray = None
+    kph: np.ndarray = None
+    segments: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class Server:
+    def __init__(self, ctx, precision: str = "fp32_mixed", max_slots: int = 64,
+                 reserve_bytes: int = 4 << 30, dt_s: float = 0.5 * synth.MYR_S, nsub: int = 10,
+                 alpha_B: float = synth.ALPHA_B, params: dict = None, mem_info=None):
+        self.ctx = ctx
+        self.precision = precision
+        self.max_slots = max_slots
+        self.reserve = reserve_bytes
+        self.dt_s, self.nsub, self.alpha_B = dt_s, nsub, alpha_B
+        self.params = dict(synth.DEFAULT_PARAMS)
+        if params:
+            self.params.update(params)
+        self.batch = native.Batch(ctx)
+        self.pending = collections.deque()
+        self.active = {}
+        self.done = []
+        self.steps = 0
+        self.segments = 0
+        self._mem_info = mem_info
+
+    def free_bytes(self) -> int:
+        if self._mem_info is not None:
+            return self._mem_info()
+        import torch
+        return torch.cuda.mem_get_info()[0]
+
+    def submit(self, req: Request):
+        self.pending.append(req)
+
+    def admit(self, now: float) -> int:
+        """Admit pending requests while a slot and device memory are free."""
+        n = 0
+        while self.pending and len(self.active) < self.max_slots:
+            req = self.pending[0]
+            need = grid_bytes(int(np.prod(req.grid["dims"])), self.precision)
+            if self.free_bytes() - need < self.reserve:
+                break
+            self.pending.popleft()
+            req.handle = native.Grid(self.ctx, req.grid, self.precision)
+            req.slot = self.batch.add(req.handle)
+            req.admitted = now
+            self.active[req.slot] = req
+            n += 1
+        return n
+
+    def step(self, now_fn) -> int:
+        """One coupled step of every active request; returns requests finished."""
+        if not self.active:
+            return 0
+        self.batch.trace(sync=True, **self.params)
+        self.batch.chem(self.dt_s, self.nsub, self.alpha_B)
+        self.steps += 1
+        finished = []
+        for slot, req in self.active.items():
+            b = self.batch.budget(slot)
+            req.segments += b["segments"]
+            self.segments += b["segments"]
+            req.steps_done += 1
+            if req.steps_done >= req.nsteps:
+                finished.append(slot)
+        for slot in finished:
+            req = self.active.pop(slot)
+            r = req.handle.rates()  # waits for the batch's update
+            req.x_HI, req.kph = r["x_HI"], r["kph"]
+            req.finished = now_fn()
+            self.batch.remove(slot)
+            req.handle.close()
+            req.handle = None
+            self.done.append(req)
+        return len(finished)
+
+    def run(self, requests: list, time_limit_s: float = None) -> dict:
+        """Serve a stream: request.arrival is in seconds from the start."""
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0  # noqa: E731
+        todo = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        while todo or self.pending or self.active:
+            t = now()
+            while todo and todo[0].arrival <= t:
+                self.submit(todo.popleft())
+            self.admit(t)
+            if self.active:
+                self.step(now)
+            elif todo:
+                time.sleep(max(0.0, min(todo[0].arrival - now(), 0.01)))
+            if time_limit_s is not None and now() > time_limit_s:
+                break
+        return self.report(now())
+
+    def report(self, wall_s: float) -> dict:
+        lat = np.array([r.latency for r in self.done]) if self.done else np.array([np.nan])
+        return dict(completed=len(self.done), wall_s=wall_s, steps=self.steps, segments=self.segments,
+                    segments_per_s=self.segments / wall_s if wall_s > 0 else 0.0,
+                    p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+                    requests_per_s=len(self.done) / wall_s if wall_s > 0 else 0.0)
+
+    def close(self):
+        for req in self.active.values():
+            if req.handle is not None:
+                req.handle.close()
+        self.active.clear()
+        self.batch.close()
+
+
+class MediumPool:
+    """Request media cut from one pre-generated log-normal field.
+
+    Each request takes an N^3 sub-cube at a seeded random offset of a 256^3
+    field (P(k) ~ k^-3, sigma_ln = 1, mean 1e-2 cm^-3), so media of any size
+    up to 256 are available at request rate without per-request FFTs.
+    """
+
+    def __init__(self, side: int = 256, seed: int = synth.BASE_SEED + 5):
+        self.side = side
+        self.field = synth.lognormal_density(side, seed=seed).reshape(side, side, side)
+
+    def request(self, spec: dict, rid: int) -> Request:
+        rng = np.random.default_rng(spec["seed"])
+        N = min(int(spec["N"]), self.side)
+        o = rng.integers(0, self.side - N + 1, 3)
+        n = np.ascontiguousarray(self.field[o[2]:o[2] + N, o[1]:o[1] + N, o[0]:o[0] + N]).reshape(-1)
+        box = synth.box_cm(N)
+        pos, ndot, e, sg = synth.random_sources((N, N, N), box / N, int(spec["nsrc"]), 1e47, 1e50, rng)
+        g = synth._grid(N, box, n, 1.0, pos, ndot, e, sg)
+        return Request(rid=rid, grid=g, nsteps=int(spec["nsteps"]), arrival=float(spec["arrival_s"]))
+
+
+def run_alone(ctx, req: Request, precision: str, dt_s: float = 0.5 * synth.MYR_S, nsub: int = 10,
+              alpha_B: float = synth.ALPHA_B, params: dict = None) -> tuple:
+    """The same request on its own grid, one step after another (reference path)."""
+    p = dict(synth.DEFAULT_PARAMS)
+    if params:
+        p.update(params)
+    grid = native.Grid(ctx, req.grid, precision)
+    segs = 0
+    for _ in range(req.nsteps):
+        segs += grid.trace(**p)["segments"]
+        grid.chem(dt_s, nsub, alpha_B)
+    r = grid.rates()
+    grid.close()
+    return r["x_HI"], r["kph"], segs

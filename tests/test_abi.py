@@ -31,8 +31,8 @@ int main(void) {
          offsetof(rt_grid_desc, n_H), offsetof(rt_grid_desc, x_HII));
   printf("%zu %zu %zu %zu\n", sizeof(rt_trace_params), offsetof(rt_trace_params, phi_c),
          offsetof(rt_trace_params, queue_capacity), offsetof(rt_trace_params, segs_per_iter));
-  printf("%zu %zu %zu %zu\n", sizeof(rt_budget), offsetof(rt_budget, counts),
-         offsetof(rt_budget, segments), offsetof(rt_budget, status));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(rt_budget), offsetof(rt_budget, counts),
+         offsetof(rt_budget, segments), offsetof(rt_budget, status), offsetof(rt_budget, passes));
   return 0;
 }
 """)
@@ -43,7 +43,7 @@ int main(void) {
     D, T, B = native.rt_grid_desc, native.rt_trace_params, native.rt_budget
     assert got[0] == [ctypes.sizeof(D), D.box_len_cm.offset, D.n_H.offset, D.x_HII.offset]
     assert got[1] == [ctypes.sizeof(T), T.phi_c.offset, T.queue_capacity.offset, T.segs_per_iter.offset]
-    assert got[2] == [ctypes.sizeof(B), B.counts.offset, B.segments.offset, B.status.offset]
+    assert got[2] == [ctypes.sizeof(B), B.counts.offset, B.segments.offset, B.status.offset, B.passes.offset]
 
 
 def test_error_message_without_gpu_is_reported_not_raised_from_c():

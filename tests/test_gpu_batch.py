@@ -110,3 +110,33 @@ def test_batch_remove_add_and_autotune():
         _compare(batch.budget(slot), gr.rates(), b_ref, alone.rates(), SUM_ORDER_TOL["fp32_mixed"])
         alone.close()
     batch.close()
+
+
+def test_batch_on_a_non_blocking_stream_orders_member_work():
+    """A batch on a caller's non-blocking stream sees state set on its grids' streams."""
+    import torch
+    ctx = parity.ctx()
+    gs = _grids(seed=13, n=3)
+    dt = 0.5 * synth.MYR_S
+    x_new = [np.random.default_rng(i).uniform(0.0, 1.0, len(g["x_HI"])) for i, g in enumerate(gs)]
+    ref = []
+    for g, x in zip(gs, x_new):
+        grid = native.Grid(ctx, g, "fp32_mixed")
+        native.rt_set_state(grid.h, x)
+        for _ in range(2):
+            grid.trace(**synth.DEFAULT_PARAMS)
+            grid.chem(dt, 10, synth.ALPHA_B)
+        ref.append(grid.rates()["x_HI"])
+        grid.close()
+    stream = torch.cuda.Stream()  # non-blocking: not ordered with the legacy stream
+    batch = native.Batch(ctx, stream.cuda_stream)
+    grids = [native.Grid(ctx, g, "fp32_mixed") for g in gs]
+    for gr in grids:
+        batch.add(gr)
+    batch.step(1, dt, 10, synth.ALPHA_B, **synth.DEFAULT_PARAMS)  # captures the graph
+    for gr, x in zip(grids, x_new):
+        native.rt_set_state(gr.h, torch.tensor(x, dtype=torch.float64, device="cuda"))
+    batch.step(2, dt, 10, synth.ALPHA_B, **synth.DEFAULT_PARAMS)
+    for gr, x_ref in zip(grids, ref):
+        np.testing.assert_allclose(gr.rates()["x_HI"], x_ref, rtol=1e-4, atol=1e-12)
+    batch.close()
