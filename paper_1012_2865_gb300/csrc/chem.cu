@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "f2.cuh"
 #include "rt_internal.cuh"
 
 namespace rtg {
@@ -24,35 +25,43 @@ __device__ __forceinline__ void chem_cell_fp64(double& x, double& z, double n, d
   }
 }
 
-// One cell, FP32-mixed path: FP32 solution + one FP64 Newton correction per
-// substep (see chem_mixed_kernel).
-__device__ __forceinline__ void chem_cell_mixed(double& x, double& z, double n, float kc, double h, int nsub,
-                                                double alpha) {
-  const double a = h * alpha * n;
-  const double hk = h * (double)kc;
-  const double b = 1.0 + hk;
-  const double two_a_b = 2.0 * a + b;
-  const float af = (float)a, bf = (float)b, hkf = (float)hk;
+// One cell, FP32-mixed path: FP32 solution + one double-float Newton
+// correction per substep (see chem_mixed_kernel).  x, z and n arrive and
+// leave in FP64; in between they are carried as double-float pairs.  ha and
+// h2 are h alpha_B and h as pairs.  Returns n_H x_HI as FP32.
+__device__ __forceinline__ float chem_cell_mixed(double& x, double& z, double n, float kc, F2 ha, F2 h2,
+                                                 int nsub) {
+  const F2 n2 = f2_from_double(n);
+  const F2 a = f2_mul(ha, n2);
+  const F2 hk = f2_mul_f(h2, kc);
+  const F2 one = {1.0f, 0.0f};
+  const F2 b = f2_add(one, hk);
+  const F2 two_a_b = f2_add(F2{2.0f * a.hi, 2.0f * a.lo}, b);
+  const float af = a.hi, bf = b.hi, hkf = hk.hi;
+  F2 xp = f2_from_double(x), zp = f2_from_double(z);
   for (int i = 0; i < nsub; ++i) {
-    const float xf = (float)x, zf = (float)z;
+    const float xf = xp.hi, zf = zp.hi;
     const float wf = zf + hkf;
     const float sq = sqrtf(fmaf(4.0f * af, wf, bf * bf));
     if (xf < 0.5f) {
       const float xg = 2.0f * (af + xf) / (2.0f * af + bf + sq);
-      const double xd = (double)xg;
-      const double g = fma(fma(a, xd, -two_a_b), xd, a + x);
+      const F2 t = f2_mul_f(f2_sub(f2_mul_f(a, xg), two_a_b), xg);
+      const float g = f2_to_float(f2_add(t, f2_add(a, xp)));
       const float gp = fmaf(2.0f * af, xg, -(2.0f * af + bf));
-      x = xd - (double)((float)g / gp);
-      z = 1.0 - x;
+      xp = two_sum(xg, -__fdiv_rn(g, gp));
+      zp = f2_sub(one, xp);
     } else {
       const float zg = 2.0f * wf / (bf + sq);
-      const double zd = (double)zg;
-      const double f = fma(fma(a, zd, b), zd, -(z + hk));
+      const F2 t = f2_mul_f(f2_add(f2_mul_f(a, zg), b), zg);
+      const float f = f2_to_float(f2_sub(t, f2_add(zp, hk)));
       const float fp = fmaf(2.0f * af, zg, bf);
-      z = zd - (double)((float)f / fp);
-      x = 1.0 - z;
+      zp = two_sum(zg, -__fdiv_rn(f, fp));
+      xp = f2_sub(one, zp);
     }
   }
+  x = f2_to_double(xp);
+  z = f2_to_double(zp);
+  return f2_to_float(f2_mul(n2, xp));
 }
 
 // Backward Euler on dx/dt = alpha_B n_H (1 - x)^2 - k x, x = x_HI,
@@ -82,28 +91,29 @@ __global__ void chem_kernel(long long ncell, const double* __restrict__ nH, doub
   }
 }
 
-// Same backward-Euler step for the FP32-mixed path, solved by FP32 +
-// one FP64 Newton correction: the smaller fraction is first obtained in FP32
-// from its cancellation-free formula, then corrected once with the residual
-// of the implicit equation evaluated in FP64,
+// Same backward-Euler step for the FP32-mixed path, solved by FP32 + one
+// Newton correction: the smaller fraction is first obtained in FP32 from its
+// cancellation-free formula, then corrected once with the residual of the
+// implicit equation evaluated in double-float arithmetic,
 //   x-form: g(x') = a x'^2 - (2a + b) x' + (a + x),  g' = 2a x' - (2a + b),
 //   z-form: f(z') = a z'^2 + b z' - (z + hk),         f' = 2a z' + b.
-// From a ~1e-7 relative guess one Newton step leaves ~1e-15, so the state
-// stays FP64-accurate while the step costs a few FP64 operations instead of
-// two FP64 divisions and a square root.
+// From a ~1e-7 relative guess one Newton step leaves ~1e-14 (the residual's
+// double-float rounding, ~2^-48 of its largest term), so the carried state
+// stays within ~1e-14 of the FP64 recursion while the substeps run on the
+// FP32 pipe; FP64 is used only to load and store the state.
 __global__ void chem_mixed_kernel(long long ncell, const double* __restrict__ nH, double* __restrict__ xHI,
                                   double* __restrict__ xHII, const float* __restrict__ K,
                                   float* __restrict__ nhi, double h, int nsub, double alpha) {
+  const F2 ha = f2_from_double(h * alpha), h2 = f2_from_double(h);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
     double x = xHI[c], z = xHII[c];
     const float kc = K[c];
     if (kc == 0.0f && z == 0.0 && x == 1.0) continue;
-    const double n = nH[c];
-    chem_cell_mixed(x, z, n, kc, h, nsub, alpha);
+    const float nx = chem_cell_mixed(x, z, nH[c], kc, ha, h2, nsub);
     xHI[c] = x;
     xHII[c] = z;
-    nhi[c] = (float)(n * x);
+    nhi[c] = nx;
   }
 }
 
@@ -190,6 +200,7 @@ __global__ void batch_zero_kernel(const InstDev* __restrict__ inst, int esz) {
 template <bool MIXED>
 __global__ void batch_chem_kernel(const InstDev* __restrict__ inst, double h, int nsub, double alpha) {
   const InstDev I = inst[blockIdx.y];
+  const F2 ha = f2_from_double(h * alpha), h2 = f2_from_double(h);
   const long long n = (long long)I.nx * I.ny * I.nz;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
@@ -197,11 +208,10 @@ __global__ void batch_chem_kernel(const InstDev* __restrict__ inst, double h, in
     if (MIXED) {
       const float kc = ((const float*)I.K)[c];
       if (kc == 0.0f && z == 0.0 && x == 1.0) continue;
-      const double nh = I.nH[c];
-      chem_cell_mixed(x, z, nh, kc, h, nsub, alpha);
+      const float nx = chem_cell_mixed(x, z, I.nH[c], kc, ha, h2, nsub);
       ((double*)I.xHI)[c] = x;
       I.xHII[c] = z;
-      ((float*)I.nhi)[c] = (float)(nh * x);
+      ((float*)I.nhi)[c] = nx;
     } else {
       const double kc = ((const double*)I.K)[c];
       if (kc == 0.0 && z == 0.0 && x == 1.0) continue;

@@ -25,6 +25,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "f2.cuh"
 #include "healpix.cuh"
 #include "rt_internal.cuh"
 
@@ -320,49 +321,6 @@ __device__ __noinline__ double retrace_tau64(const TraceArgs& A, uint32_t src, i
 constexpr float kEps32 = 5.9604645e-8f;   // 2^-24
 constexpr float kBandT = 9.094947e-13f;   // 2^-40
 constexpr float kClose = 4.76837158e-7f;  // 2^-21: high parts farther apart are ordered
-
-struct F2 {
-  float hi, lo;
-};
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, err};
-}
-__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
-  F2 s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-// a - b as FP32 (both pairs), accurate to ~2^-44 |a|
-__device__ __forceinline__ float f2_diff(F2 a, F2 b) {
-  const F2 d = two_sum(a.hi, -b.hi);
-  return __fadd_rn(d.hi, __fadd_rn(d.lo, __fsub_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ bool f2_less(F2 a, F2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
-__device__ __forceinline__ bool f2_eq(F2 a, F2 b) { return a.hi == b.hi && a.lo == b.lo; }
-// 1 / (n.hi + n.lo) as a pair (one Newton correction)
-__device__ __forceinline__ F2 f2_recip(F2 n) {
-  const float q = __frcp_rn(n.hi);
-  float e = fmaf(-n.hi, q, 1.0f);
-  e = fmaf(-n.lo, q, e);
-  return fast_two_sum(q, __fmul_rn(e, q));
-}
-__device__ __forceinline__ int f2_floor(F2 u) {
-  const float f = floorf(u.hi);
-  if (u.hi == f && u.lo < 0.0f) return (int)f - 1;
-  return (int)f;
-}
 
 // Direction of (level, pix) as FP32 pairs: from the device table when the
 // level is tabulated, else from the FP64 evaluation.  Returns the
