@@ -229,7 +229,7 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
   ALLOC(g->nH, n8);
   ALLOC(g->xHI, n8);
   ALLOC(g->xHII, n8);
-  ALLOC(g->nhi, ne);
+  ALLOC(g->nhi, d->precision == RT_FP32_MIXED ? 2 * ne : ne);  // mixed: (hi, lo) pairs
   ALLOC(g->K, ne);
   ALLOC(g->G, ne);
   ALLOC(g->acc, 4 * sizeof(double));
@@ -254,7 +254,8 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
   if (e == cudaSuccess) e = cudaMemsetAsync(g->K, 0, ne, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->G, 0, ne, st);
   InstDev I;
-  I.nx = g->nx; I.ny = g->ny; I.nz = g->nz; I.pad = 0;
+  I.nx = g->nx; I.ny = g->ny; I.nz = g->nz;
+  I.flags = g->precision == RT_FP32_MIXED ? kInstNhiPair : 0;
   I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.xHII = g->xHII; I.K = g->K; I.G = g->G; I.acc = g->acc;
   I.cnt = g->cnt;
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->inst_dev, &I, sizeof I, cudaMemcpyHostToDevice, st);
@@ -347,7 +348,7 @@ static void build_sources(const rt_grid* g, int level0, int inst, std::vector<So
     S.exact32 = exact && g->nx <= 4096 && g->ny <= 4096 && g->nz <= 4096;
     S.k32 = make_float4((float)S.sdx, (float)S.w, (float)S.rw, (float)S.heat);
     S.s32 = make_float4(s32[0], s32[1], s32[2], S.exact32 ? 1.0f : 0.0f);
-    S.slo32 = make_float4(slo[0], slo[1], slo[2], 0.0f);
+    S.slo32 = make_float4(slo[0], slo[1], slo[2], (float)(S.sdx - (double)(float)S.sdx));
     S.sabs32 = make_float4(sab[0], sab[1], sab[2], 0.0f);
     v.push_back(S);
   }
@@ -414,6 +415,7 @@ static void fill_common_args(TraceArgs& A, const rt_trace_params* p) {
   A.max_level = p->max_level;
   A.tau_term = -log(p->f_term);
   A.tau_term32 = (float)A.tau_term;
+  A.tau_term32lo = (float)(A.tau_term - (double)A.tau_term32);
   A.timeout_ns = (long long)((p->timeout_s > 0 ? p->timeout_s : 2.0) * 1e9);
   A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 8;
   A.checksums = (p->flags & RT_TRACE_CHECKSUMS) != 0;
@@ -784,6 +786,7 @@ static int batch_rebuild(rt_batch* b, int level0) {
     InstDev I;
     memset(&I, 0, sizeof I);
     I.nx = g->nx; I.ny = g->ny; I.nz = g->nz;
+    I.flags = g->precision == RT_FP32_MIXED ? kInstNhiPair : 0;
     I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.xHII = g->xHII; I.K = g->K; I.G = g->G;
     I.acc = g->acc; I.cnt = g->cnt;
     build_sources(g, level0, (int)inst.size(), src);

@@ -28,9 +28,8 @@ __device__ __forceinline__ void chem_cell_fp64(double& x, double& z, double n, d
 // One cell, FP32-mixed path: FP32 solution + one double-float Newton
 // correction per substep (see chem_mixed_kernel).  x, z and n arrive and
 // leave in FP64; in between they are carried as double-float pairs.  ha and
-// h2 are h alpha_B and h as pairs.  Returns n_H x_HI as FP32.
-__device__ __forceinline__ float chem_cell_mixed(double& x, double& z, double n, float kc, F2 ha, F2 h2,
-                                                 int nsub) {
+// h2 are h alpha_B and h as pairs.  Returns n_HI = n_H x_HI as a pair.
+__device__ __forceinline__ F2 chem_cell_mixed(double& x, double& z, double n, float kc, F2 ha, F2 h2, int nsub) {
   const F2 n2 = f2_from_double(n);
   const F2 a = f2_mul(ha, n2);
   const F2 hk = f2_mul_f(h2, kc);
@@ -61,7 +60,7 @@ __device__ __forceinline__ float chem_cell_mixed(double& x, double& z, double n,
   }
   x = f2_to_double(xp);
   z = f2_to_double(zp);
-  return f2_to_float(f2_mul(n2, xp));
+  return f2_mul(n2, xp);
 }
 
 // Backward Euler on dx/dt = alpha_B n_H (1 - x)^2 - k x, x = x_HI,
@@ -103,17 +102,17 @@ __global__ void chem_kernel(long long ncell, const double* __restrict__ nH, doub
 // FP32 pipe; FP64 is used only to load and store the state.
 __global__ void chem_mixed_kernel(long long ncell, const double* __restrict__ nH, double* __restrict__ xHI,
                                   double* __restrict__ xHII, const float* __restrict__ K,
-                                  float* __restrict__ nhi, double h, int nsub, double alpha) {
+                                  float2* __restrict__ nhi, double h, int nsub, double alpha) {
   const F2 ha = f2_from_double(h * alpha), h2 = f2_from_double(h);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
     double x = xHI[c], z = xHII[c];
     const float kc = K[c];
     if (kc == 0.0f && z == 0.0 && x == 1.0) continue;
-    const float nx = chem_cell_mixed(x, z, nH[c], kc, ha, h2, nsub);
+    const F2 nx = chem_cell_mixed(x, z, nH[c], kc, ha, h2, nsub);
     xHI[c] = x;
     xHII[c] = z;
-    nhi[c] = nx;
+    nhi[c] = make_float2(nx.hi, nx.lo);
   }
 }
 
@@ -123,6 +122,17 @@ __global__ void refresh_nhi_kernel(long long ncell, const double* __restrict__ n
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x)
     nhi[c] = (NT)__dmul_rn(nH[c], xHI[c]);
+}
+
+// FP32-mixed grids keep n_HI as a pair: FP32 rounding and remainder of the
+// FP64 product.
+__global__ void refresh_nhi_pair_kernel(long long ncell, const double* __restrict__ nH,
+                                        const double* __restrict__ xHI, float2* __restrict__ nhi) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const F2 v = f2_from_double(__dmul_rn(nH[c], xHI[c]));
+    nhi[c] = make_float2(v.hi, v.lo);
+  }
 }
 
 template <typename ST, typename DT>
@@ -152,7 +162,7 @@ cudaError_t launch_chem(int precision, long long ncell, const double* nH, double
     chem_kernel<double, double><<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const double*)K,
                                                          (double*)nhi, h, nsub, alpha);
   else
-    chem_mixed_kernel<<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const float*)K, (float*)nhi, h, nsub,
+    chem_mixed_kernel<<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const float*)K, (float2*)nhi, h, nsub,
                                               alpha);
   return cudaGetLastError();
 }
@@ -163,7 +173,7 @@ cudaError_t launch_refresh(int precision, long long ncell, const double* nH, con
   if (precision == RT_FP64)
     refresh_nhi_kernel<double><<<grid, block, 0, st>>>(ncell, nH, xHI, (double*)nhi);
   else
-    refresh_nhi_kernel<float><<<grid, block, 0, st>>>(ncell, nH, xHI, (float*)nhi);
+    refresh_nhi_pair_kernel<<<grid, block, 0, st>>>(ncell, nH, xHI, (float2*)nhi);
   return cudaGetLastError();
 }
 
@@ -208,10 +218,10 @@ __global__ void batch_chem_kernel(const InstDev* __restrict__ inst, double h, in
     if (MIXED) {
       const float kc = ((const float*)I.K)[c];
       if (kc == 0.0f && z == 0.0 && x == 1.0) continue;
-      const float nx = chem_cell_mixed(x, z, I.nH[c], kc, ha, h2, nsub);
+      const F2 nx = chem_cell_mixed(x, z, I.nH[c], kc, ha, h2, nsub);
       ((double*)I.xHI)[c] = x;
       I.xHII[c] = z;
-      ((float*)I.nhi)[c] = nx;
+      ((float2*)I.nhi)[c] = make_float2(nx.hi, nx.lo);
     } else {
       const double kc = ((const double*)I.K)[c];
       if (kc == 0.0 && z == 0.0 && x == 1.0) continue;

@@ -191,7 +191,7 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
       S.exact32 = exact && g->nx <= 4096 && g->ny <= 4096 && g->nz <= 4096;
       S.k32 = make_float4((float)S.sdx, (float)S.w, (float)S.rw, (float)S.heat);
       S.s32 = make_float4(s32[0], s32[1], s32[2], S.exact32 ? 1.0f : 0.0f);
-      S.slo32 = make_float4(slo[0], slo[1], slo[2], 0.0f);
+      S.slo32 = make_float4(slo[0], slo[1], slo[2], (float)(S.sdx - (double)(float)S.sdx));
       S.sabs32 = make_float4(sab[0], sab[1], sab[2], 0.0f);
     }
     if ((e = cudaMemcpyAsync(src + i0, chunk, m * sizeof(SourceDev), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
@@ -221,6 +221,8 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
     A.dir_levels = kNaTableLevels;
     A.tau_term = -log(p->f_term);
     A.tau_term32 = (float)A.tau_term;
+    A.tau_term32lo = (float)(A.tau_term - (double)A.tau_term32);
+  A.tau_term32lo = (float)(A.tau_term - (double)A.tau_term32);
     A.queue = base + kNaQueueOff;
     A.cap = p->queue_capacity > 0 ? (unsigned long long)p->queue_capacity : (unsigned long long)RT_NOALLOC_MAX_RECORDS;
     A.ctl = ctl;

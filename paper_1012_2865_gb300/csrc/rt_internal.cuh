@@ -31,7 +31,7 @@ struct __align__(16) SourceDev {
   // FP32 view (mixed path), one 16-byte load each
   float4 k32;     // sdx, w, rw, heat (see the FP64 fields)
   float4 s32;     // position as FP32 pair, high part; .w = 1 if exact32
-  float4 slo32;   // low part (s - s32)
+  float4 slo32;   // low part (s - s32); .w = sdx - k32.x
   float4 sabs32;  // 2^-46 |s| where the pair does not hold s exactly, else 0
   // FP64 view
   double s[3];    // position in cell units (pos_cm / dx)
@@ -46,10 +46,16 @@ struct __align__(16) SourceDev {
   int pad;
 };
 
+// InstDev.flags: the FP32-mixed grid stores n_HI as float2 pairs (n_HI
+// rounded to FP32, and the remainder), so the walker sums optical depth to
+// ~2^-44 of the FP64 evaluation.
+constexpr int kInstNhiPair = 1;
+
 // One grid (instance) as the trace kernel sees it.
 struct InstDev {
-  int nx, ny, nz, pad;
-  const void* nhi;          // absorber density n_HI (double or float), x fastest
+  int nx, ny, nz;
+  int flags;                // kInstNhiPair: nhi holds (hi, lo) FP32 pairs
+  const void* nhi;          // absorber density n_HI (double, float or float2), x fastest
   const double* nH;         // hydrogen density, FP64 (decisions re-taken in FP64)
   const double* xHI;        // neutral fraction, FP64
   double* xHII;             // ionised fraction, FP64 (chemistry)
@@ -70,14 +76,16 @@ struct __align__(16) Rec64 {
   uint32_t src, pix, level, tag;
 };
 struct __align__(16) Rec32 {
-  float r, P, tau;
-  float tau_err;  // bound on |tau (FP32) - tau (FP64 evaluation)|
+  float r, r_lo;  // radius as an FP32 pair
+  float P, tau;   // photon rate; optical depth as an FP32 pair (tau, tau_lo)
+  float tau_lo;
+  float tau_err;  // bound on |tau (pair) - tau (FP64 evaluation)|
   uint32_t src, pix;
-  float r_lo;     // radius as the FP32 pair (r, r_lo)
   uint32_t tag;   // (epoch << 4) | level
+  uint32_t pad[3];
 };
 static_assert(sizeof(Rec64) == 48, "record layout");
-static_assert(sizeof(Rec32) == 32, "record layout");
+static_assert(sizeof(Rec32) == 48, "record layout");
 
 struct TraceArgs {
   const InstDev* inst;
@@ -93,7 +101,7 @@ struct TraceArgs {
   const float4* dir_tab;      // pixel directions as FP32 pairs, levels 0..dir_levels
   int dir_levels;             // -1: no table
   double tau_term;
-  float tau_term32;
+  float tau_term32, tau_term32lo;  // tau_term as an FP32 pair
   void* queue;
   unsigned long long cap;
   unsigned long long* ctl;

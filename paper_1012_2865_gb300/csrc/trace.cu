@@ -368,15 +368,16 @@ __device__ __noinline__ int decide64(const TraceArgs& A, uint32_t src, int level
 struct Walk32 {
   using Rec = Rec32;
   uint32_t src, pix;
-  uint32_t level;       // bits 0-3 level, bit 8: 45-degree ray of an exact source
+  uint32_t level;       // bits 0-3 level, bit 8: 45-degree ray of an exact source,
+                        // bit 9: n_HI stored as FP32 pairs
   F2 r;
-  float P, tau, Pstart, tau_err;
+  float P, tau, tau_lo, Pstart, tau_err;
   F2 iv0, iv1, iv2;     // 1 / n_i (0 for a vanishing component)
   F2 t0, t1, t2;        // distance to the next plane on each axis
   int c0, c1, c2;
   int nx, ny, nz, steps;
   unsigned nseg;
-  float nh;             // n_HI of the current cell, loaded one step ahead
+  float nh, nh_lo;      // n_HI of the current cell (pair), loaded one step ahead
   const float* nhi;
   float* K;
   float* G;
@@ -384,6 +385,16 @@ struct Walk32 {
   __device__ __forceinline__ int lvl() const { return (int)(level & 15u); }
   __device__ __forceinline__ int cell_index() const { return c0 + nx * (c1 + ny * c2); }
   __device__ __forceinline__ bool diag_exact() const { return (level & 256u) != 0; }
+  __device__ __forceinline__ void load_nh(int idx) {
+    if (level & 512u) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(nhi) + idx);
+      nh = v.x;
+      nh_lo = v.y;
+    } else {
+      nh = __ldg(&nhi[idx]);
+      nh_lo = 0.0f;
+    }
+  }
   __device__ __forceinline__ bool is_root() const { return P == 1.0f && r.hi == 0.0f && tau == 0.0f; }
   __device__ __forceinline__ int inst(const TraceArgs& A) const { return A.src[src].inst; }
   __device__ __forceinline__ double unit(const TraceArgs& A) const { return A.src[src].unit; }
@@ -410,52 +421,60 @@ struct Walk32 {
     return fmaf(t.hi, kBandT, ab);
   }
 
-  __device__ __forceinline__ bool start(const TraceArgs& A) {
+  // Geometry of a package at radius r: direction pairs, first cell, next
+  // crossings.  False when that cell is outside the box.
+  __device__ __forceinline__ bool start_geom(const TraceArgs& A) {
     const SourceDev& S = A.src[src];
     const float4 sh = __ldg(&S.s32);
     const float4 sl = __ldg(&S.slo32);
     const InstDev& I = A.inst[S.inst];
     nx = I.nx; ny = I.ny; nz = I.nz;
-    nhi = (const float*)I.nhi;
-    K = (float*)I.K;
-    G = (float*)I.G;
     F2 n[3];
     const int diag = dir_pair(A, lvl(), pix, n);
-    level = (level & 15u) | ((diag && sh.w != 0.0f) ? 256u : 0u);
+    level = (level & (15u | 512u)) | ((diag && sh.w != 0.0f) ? 256u : 0u);
     iv0 = n[0].hi != 0.0f ? f2_recip(n[0]) : F2{0.0f, 0.0f};
     iv1 = n[1].hi != 0.0f ? f2_recip(n[1]) : F2{0.0f, 0.0f};
     iv2 = n[2].hi != 0.0f ? f2_recip(n[2]) : F2{0.0f, 0.0f};
     c0 = cell_of(f2_add(F2{sh.x, sl.x}, f2_mul(r, n[0])), n[0].hi);
     c1 = cell_of(f2_add(F2{sh.y, sl.y}, f2_mul(r, n[1])), n[1].hi);
     c2 = cell_of(f2_add(F2{sh.z, sl.z}, f2_mul(r, n[2])), n[2].hi);
-    Pstart = P;
-    steps = 0;
     if (!inside()) return false;
-    nh = __ldg(&nhi[cell_index()]);
     t0 = next_t(c0, sh.x, sl.x, iv0);
     t1 = next_t(c1, sh.y, sl.y, iv1);
     t2 = next_t(c2, sh.z, sl.z, iv2);
     return true;
   }
+  __device__ __forceinline__ bool start(const TraceArgs& A) {
+    const InstDev& I = A.inst[A.src[src].inst];
+    nhi = (const float*)I.nhi;
+    K = (float*)I.K;
+    G = (float*)I.G;
+    level = (level & ~512u) | ((I.flags & kInstNhiPair) ? 512u : 0u);
+    Pstart = P;
+    steps = 0;
+    if (!start_geom(A)) return false;
+    load_nh(cell_index());
+    return true;
+  }
 
   __device__ __forceinline__ void load(const Rec& q) {
-    r = {q.r, q.r_lo}; P = q.P; tau = q.tau; tau_err = q.tau_err; src = q.src; pix = q.pix;
+    r = {q.r, q.r_lo}; P = q.P; tau = q.tau; tau_lo = q.tau_lo; tau_err = q.tau_err; src = q.src; pix = q.pix;
     level = q.tag & 15u;
   }
   // Record of child cpix (level + 1, P/4, same radius, optical depth and its
   // error bound); the level sits in the tag's low bits until publication.
   __device__ __forceinline__ Rec make_child(uint32_t cpix) const {
     Rec c;
-    c.r = r.hi; c.P = P * 0.25f; c.tau = tau; c.tau_err = tau_err;
-    c.src = src; c.pix = cpix; c.r_lo = r.lo; c.tag = (uint32_t)(lvl() + 1);
+    c.r = r.hi; c.r_lo = r.lo; c.P = P * 0.25f; c.tau = tau; c.tau_lo = tau_lo; c.tau_err = tau_err;
+    c.src = src; c.pix = cpix; c.tag = (uint32_t)(lvl() + 1);
     return c;
   }
   // Publish a record in the global queue: payload first, then the tag
   // ((epoch << 4) | level) with release semantics.
   __device__ __forceinline__ static void publish(Rec* q, const Rec& c, uint32_t epoch) {
-    __stcg(reinterpret_cast<float4*>(&q->r), make_float4(c.r, c.P, c.tau, c.tau_err));
-    __stcg(reinterpret_cast<uint2*>(&q->src), make_uint2(c.src, c.pix));
-    __stcg(&q->r_lo, c.r_lo);
+    __stcg(reinterpret_cast<float4*>(&q->r), make_float4(c.r, c.r_lo, c.P, c.tau));
+    __stcg(reinterpret_cast<uint4*>(&q->tau_lo),
+           make_uint4(__float_as_uint(c.tau_lo), __float_as_uint(c.tau_err), c.src, c.pix));
     st_release_u32(&q->tag, (epoch << 4) | (c.tag & 15u));
   }
   // Poll with a relaxed load; only a successful poll pays for the fence that
@@ -465,21 +484,26 @@ struct Walk32 {
     if ((tg >> 4) != (epoch & 0x0fffffffu)) return false;
     __threadfence();
     const float4 a = __ldcg(reinterpret_cast<const float4*>(&q->r));
-    const uint4 b = __ldcg(reinterpret_cast<const uint4*>(&q->src));
-    o.r = a.x; o.P = a.y; o.tau = a.z; o.tau_err = a.w;
-    o.src = b.x; o.pix = b.y; o.r_lo = __uint_as_float(b.z); o.tag = tg;
+    const uint4 b = __ldcg(reinterpret_cast<const uint4*>(&q->tau_lo));
+    o.r = a.x; o.r_lo = a.y; o.P = a.z; o.tau = a.w;
+    o.tau_lo = __uint_as_float(b.x); o.tau_err = __uint_as_float(b.y); o.src = b.z; o.pix = b.w; o.tag = tg;
     return true;
   }
   __device__ __forceinline__ static Rec root_rec(uint32_t gsrc, uint32_t l, uint32_t p) {
     Rec c;
-    c.r = 0.0f; c.P = 1.0f; c.tau = 0.0f; c.tau_err = 0.0f; c.src = gsrc; c.pix = p; c.r_lo = 0.0f; c.tag = l;
+    c.r = 0.0f; c.r_lo = 0.0f; c.P = 1.0f; c.tau = 0.0f; c.tau_lo = 0.0f; c.tau_err = 0.0f; c.src = gsrc; c.pix = p;
+    c.tag = l;
     return c;
   }
   __device__ __forceinline__ void become_child0() {
     level = (uint32_t)(lvl() + 1); pix = 4u * pix; P = P * 0.25f;
   }
 
-  __device__ __forceinline__ int step(const TraceArgs& A, LaneAcc& acc) {
+  // The next crossing as the FP64 evaluation takes it: bits 0-2 the planes
+  // crossed, bit 3 a split first, bits 4-5 the axis of the smallest pair;
+  // rn_out receives the crossing distance.  Orders the pairs cannot prove are
+  // re-taken in FP64 (decide64) and counted in fb.
+  __device__ __forceinline__ int decide(const TraceArgs& A, F2& rn_out, unsigned& fb) const {
     // next crossing: the smallest pair, and whether the order is provable
     int imin = 0;
     F2 rn = t0;
@@ -516,16 +540,42 @@ struct Walk32 {
         m0 = (d64 & 1) != 0;
         m1 = (d64 & 2) != 0;
         m2 = (d64 & 4) != 0;
-        acc.fallbacks++;
+        ++fb;
       }
     }
-    if (split) return EV_SPLIT;
-    float dr = f2_diff(rn, r);
-    if (dr < 0.0f) dr = 0.0f;
+    rn_out = rn;
+    return (m0 ? 1 : 0) | (m1 ? 2 : 0) | (m2 ? 4 : 0) | (split ? 8 : 0) | (imin << 4);
+  }
+  // Cross the planes of `m` (bits 0-2) at distance rn.
+  __device__ __forceinline__ void advance(const TraceArgs& A, int m, F2 rn) {
+    if (m & 7) {
+      const float4 sh = __ldg(&A.src[src].s32);
+      const float4 sl = __ldg(&A.src[src].slo32);
+      if (m & 1) { c0 += iv0.hi > 0.0f ? 1 : -1; t0 = next_t(c0, sh.x, sl.x, iv0); }
+      if (m & 2) { c1 += iv1.hi > 0.0f ? 1 : -1; t1 = next_t(c1, sh.y, sl.y, iv1); }
+      if (m & 4) { c2 += iv2.hi > 0.0f ? 1 : -1; t2 = next_t(c2, sh.z, sl.z, iv2); }
+    }
+    r = rn;
+  }
+
+  __device__ __forceinline__ int step(const TraceArgs& A, LaneAcc& acc) {
+    F2 rn;
+    unsigned fb = 0;
+    const int m = decide(A, rn, fb);
+    acc.fallbacks += fb;
+    const int l = lvl();
+    if (m & 8) return EV_SPLIT;
+    // segment length, kappa = sigma dx n_HI and dtau as FP32 pairs: the
+    // optical depth (pair) follows the FP64 sum to ~2^-44 where n_HI is a pair
+    F2 dr2 = f2_sub(rn, r);
+    if (dr2.hi < 0.0f) dr2 = F2{0.0f, 0.0f};
+    const float dr = dr2.hi;
     const int idx = cell_index();
     const float4 k32 = __ldg(&A.src[src].k32);  // sdx, w, rw, heat
-    const float kap = k32.x * nh;
-    const float dtau = kap * dr;
+    const F2 kap2 = f2_mul(F2{k32.x, __ldg(&A.src[src].slo32.w)}, F2{nh, nh_lo});
+    const F2 dtau2 = f2_mul(kap2, dr2);
+    const float kap = kap2.hi;
+    const float dtau = dtau2.hi;
     // transmitted fraction tr = e^-tau; phi = (1 - e^-tau)/tau from its Taylor
     // series below tau = 1/4 (7 terms: truncation < 2e-13), else from tr.
     // Both are computed and one is selected, so lanes do not diverge.
@@ -538,15 +588,28 @@ struct Walk32 {
     if (k32.w != 0.0f) atomicAdd(&G[idx], kadd * k32.w);
     if (dr > 0.0f) nseg++;
     P = P * tr;
-    tau = tau + dtau;
-    // tau_FP32 - tau_FP64: roundings of kappa, dr and the sum, plus the pair
-    // error of dr (2 x 2^-40 rn, with margin)
-    tau_err = tau_err + dtau * (8.0f * kEps32) + kap * fmaf(rn.hi, 4.0f * kBandT, 1e-30f) + tau * (2.0f * kEps32);
     {
-      const float d = tau - A.tau_term32;
-      const float bnd = tau_err + A.tau_term32 * (4.0f * kEps32) + 1e-12f;
+      const F2 t2 = f2_add(F2{tau, tau_lo}, dtau2);
+      tau = t2.hi;
+      tau_lo = t2.lo;
+    }
+    // |tau - tau_FP64| grows by kappa times the pair errors of rn and r (each
+    // within 2^-40 rn + 2^-46 |s|/|n| on its axis; twice that, with margin),
+    // the rounding of the pair products (2^-37 dtau; 2^-22 dtau where n_HI is
+    // plain FP32) and of the pair sum (2^-44 tau)
+    {
+      const float4 sa = __ldg(&A.src[src].sabs32);
+      const float ab = fmaxf(sa.x * fabsf(iv0.hi), fmaxf(sa.y * fabsf(iv1.hi), sa.z * fabsf(iv2.hi)));
+      const float e_dtau = (level & 512u) ? 8.0f * kBandT : 4.0f * kEps32;
+      tau_err = tau_err + dtau * e_dtau + kap * (fmaf(rn.hi, 4.0f * kBandT, 1e-30f) + 4.0f * ab) +
+                tau * (kBandT / 16.0f);
+    }
+    {
+      const float d = f2_diff(F2{tau, tau_lo}, F2{A.tau_term32, A.tau_term32lo});
+      const float bnd = tau_err + tau * (4.0f * kBandT) + 1e-30f;
       bool term = d > bnd;
       if (!term && !(-d > bnd)) {
+        // too close to call: the lineage's optical depth in FP64
         const double t64 = retrace_tau64(A, src, l, pix, c0, c1, c2);
         acc.fallbacks_tau++;
         term = isnan(t64) ? (d > 0.0f) : (t64 > A.tau_term);
@@ -561,14 +624,7 @@ struct Walk32 {
         return EV_DONE;
       }
     }
-    if (m0 || m1 || m2) {
-      const float4 sh = __ldg(&A.src[src].s32);
-      const float4 sl = __ldg(&A.src[src].slo32);
-      if (m0) { c0 += iv0.hi > 0.0f ? 1 : -1; t0 = next_t(c0, sh.x, sl.x, iv0); }
-      if (m1) { c1 += iv1.hi > 0.0f ? 1 : -1; t1 = next_t(c1, sh.y, sl.y, iv1); }
-      if (m2) { c2 += iv2.hi > 0.0f ? 1 : -1; t2 = next_t(c2, sh.z, sl.z, iv2); }
-    }
-    r = rn;
+    advance(A, m, rn);
     if (!inside()) {
       const double u = unit(A);
       acc.absorbed += ((double)Pstart - (double)P) * u;
@@ -576,7 +632,7 @@ struct Walk32 {
       return EV_DONE;
     }
     // the next cell is known before its density is needed: start the load now
-    nh = __ldg(&nhi[cell_index()]);
+    load_nh(cell_index());
     if (++steps > A.max_steps) {
       set_status(A.ctl, RT_ERR_STATE);
       const double u = unit(A);

@@ -21,9 +21,9 @@ from . import native, synth
 
 
 def grid_bytes(ncell: int, precision: str) -> int:
-    """Device bytes of one grid: n_H, x_HI, x_HII (FP64) + n_HI, k_ph, Gamma."""
-    e = 8 if precision == "fp64" else 4
-    return ncell * (24 + 3 * e)
+    """Device bytes of one grid: n_H, x_HI, x_HII (FP64) + n_HI, k_ph, Gamma
+    (FP64, or FP32 with n_HI as an FP32 pair)."""
+    return ncell * (24 + (24 if precision == "fp64" else 16))
 
 
 @dataclass
