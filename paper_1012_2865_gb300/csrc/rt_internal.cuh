@@ -12,16 +12,18 @@ constexpr int kLevels = RT_MAX_LEVEL + 1;
 constexpr double kEvErg = 1.602176634e-12;  // erg per eV
 constexpr double kEHI = 13.6;               // hydrogen threshold, eV (Sec. 2.2)
 
-// Control words of one trace (64-bit each), in device memory.
+// Control words of one trace (64-bit each), in device memory.  The three
+// that every warp updates or polls sit in cache lines of their own, so their
+// atomics and loads do not queue behind one another in L2.
 enum CtlWord {
-  CTL_HEAD = 0,         // next ticket to hand out
-  CTL_TAIL = 1,         // queue slots reserved by producers
-  CTL_OUTSTANDING = 2,  // live packages (signed)
-  CTL_STATUS = 3,       // RT_OK or first device error (atomicCAS)
-  CTL_EPOCH = 4,        // tag of this trace's queue records
-  CTL_PEAK = 5,         // largest TAIL of the earlier passes of this trace
-  CTL_PUSHED = 6,       // sum of TAIL over the earlier passes of this trace
-  CTL_N = 8
+  CTL_HEAD = 0,          // next ticket to hand out
+  CTL_TAIL = 16,         // queue slots reserved by producers
+  CTL_OUTSTANDING = 32,  // live packages (signed)
+  CTL_STATUS = 48,       // RT_OK or first device error (atomicCAS)
+  CTL_EPOCH = 49,        // tag of this trace's queue records
+  CTL_PEAK = 50,         // largest TAIL of the earlier passes of this trace
+  CTL_PUSHED = 51,       // sum of TAIL over the earlier passes of this trace
+  CTL_N = 64             // words (512 bytes)
 };
 
 // One point source, prepared on the host for the kernels.  P of a package is
@@ -109,6 +111,7 @@ struct TraceArgs {
   int segs_per_iter;
   int max_steps;  // bound on segments of one package (guards the DDA loop)
   int checksums;  // accumulate the created-set checksum
+  int pf_radius;  // prefetch n_HI within this many cells of each source into L2 first (0: none)
 };
 
 // 64-bit finaliser used for the created-package checksum (documented in rt.h).

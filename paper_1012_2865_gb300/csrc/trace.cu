@@ -45,7 +45,8 @@ enum Event { EV_NONE = 0, EV_SPLIT = 1, EV_DONE = 2 };
 // memory (one slot per thread) and is touched only at package events.
 struct LaneAcc {
   double emitted, absorbed, escaped;
-  unsigned int segments, fallbacks, fallbacks_tau;
+  unsigned long long segments;
+  unsigned int fallbacks, fallbacks_tau;
   int inst;
 };
 
@@ -55,7 +56,7 @@ __device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A) {
     if (a.emitted != 0.0) atomicAdd(&I.acc[0], a.emitted);
     if (a.absorbed != 0.0) atomicAdd(&I.acc[1], a.absorbed);
     if (a.escaped != 0.0) atomicAdd(&I.acc[2], a.escaped);
-    if (a.segments) atomicAdd(&I.cnt[kCntSegments], (unsigned long long)a.segments);
+    if (a.segments) atomicAdd(&I.cnt[kCntSegments], a.segments);
     if (a.fallbacks) atomicAdd(&I.cnt[kCntFallbacks], (unsigned long long)a.fallbacks);
     if (a.fallbacks_tau) atomicAdd(&I.cnt[kCntFallbacksTau], (unsigned long long)a.fallbacks_tau);
   }
@@ -114,6 +115,7 @@ __device__ __forceinline__ double next_t64(int c, double s, double n) {
 
 struct Walk64 {
   using Rec = Rec64;
+  static constexpr int kNhiBytes = 8;
   uint32_t src, level, pix;
   double r, P, tau, Pstart;
   double s0, s1, s2, n0, n1, n2, t0, t1, t2;
@@ -367,6 +369,7 @@ __device__ __noinline__ int decide64(const TraceArgs& A, uint32_t src, int level
 
 struct Walk32 {
   using Rec = Rec32;
+  static constexpr int kNhiBytes = 4;  // per cell; twice that where n_HI is a pair
   uint32_t src, pix;
   uint32_t level;       // bits 0-3 level, bit 8: 45-degree ray of an exact source,
                         // bit 9: n_HI stored as FP32 pairs
@@ -653,9 +656,40 @@ struct Walk32 {
 // ---------------------------------------------------------------------------
 // The persistent kernel, generic over the walker.
 // ---------------------------------------------------------------------------
+// Before the queue loop: every thread prefetches into L2 a share of the n_HI
+// rows within A.pf_radius cells of each source (clipped to its grid).  The
+// first levels of the ray tree have few packages, each waiting on the
+// memory latency of every cell it enters; with the rows already in L2 that
+// wait is an L2 hit.  elem: bytes per cell of the walker's n_HI.
+__device__ __forceinline__ void prefetch_sources(const TraceArgs& A, int elem_base) {
+  const int R = A.pf_radius, w = 2 * R + 1;
+  const long long rows = (long long)A.nsrc * w * w;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows; i += stride) {
+    const int si = (int)(i / (w * w));
+    const int rr = (int)(i - (long long)si * w * w);
+    const SourceDev& S = A.src[si];
+    const InstDev& I = A.inst[S.inst];
+    const float4 s32 = __ldg(&S.s32);
+    const int sx = min(max((int)floorf(s32.x), 0), I.nx - 1);
+    const int sy = min(max((int)floorf(s32.y), 0), I.ny - 1);
+    const int sz = min(max((int)floorf(s32.z), 0), I.nz - 1);
+    const int y = sy - R + rr % w, z = sz - R + rr / w;
+    if (y < 0 || y >= I.ny || z < 0 || z >= I.nz) continue;
+    const int x0 = max(sx - R, 0), x1 = min(sx + R, I.nx - 1);
+    const int elem = (I.flags & kInstNhiPair) ? 2 * elem_base : elem_base;
+    const size_t row = ((size_t)z * I.ny + y) * I.nx;
+    const char* p = (const char*)I.nhi + (row + x0) * elem;
+    const char* last = (const char*)I.nhi + (row + x1) * elem;  // every address stays inside the row
+    for (; p < last; p += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(last));
+  }
+}
+
 template <class W, int MinBlocks>
 __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   using Rec = typename W::Rec;
+  if (A.pf_radius > 0) prefetch_sources(A, W::kNhiBytes);
   __shared__ unsigned int sh_cnt[kShInst * kLevels];
   __shared__ unsigned long long sh_hsh[kShInst * kLevels];
   __shared__ LaneAcc sh_acc[kBlock];
@@ -755,24 +789,33 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         if (ev != EV_NONE) break;
       }
     }
-    // (5) splits: reserve 3 slots per splitting lane, publish children 1-3,
-    //     keep child 0
+    // (5) splits reserve 3 slots per splitting lane, publish children 1-3 and
+    //     keep child 0; finished packages leave the outstanding count.  One
+    //     atomic per warp carries both: +3 per split, -1 per finished package.
     const bool split = (ev == EV_SPLIT);
     const unsigned sm = __ballot_sync(kFull, split);
-    if (sm) {
-      const int leader = __ffs(sm) - 1;
+    const unsigned dm = __ballot_sync(kFull, ev == EV_DONE);
+    if (sm | dm) {
+      const int leader = __ffs(sm | dm) - 1;
       const unsigned nsp = __popc(sm);
       unsigned long long base = 0;
       if (lane == leader) {
-        // The increment must be performed before any child is published, or
-        // a consumer could finish a child and see the count reach zero: wait
-        // for the atomic's return value, then fence.
-        const unsigned long long o = atomicAdd(&A.ctl[CTL_OUTSTANDING], 3ULL * nsp);
+        // The count must include the children before any child is published,
+        // or a consumer could finish a child and see it reach zero: wait for
+        // the atomic's return value, then fence.
+        const long long delta = 3LL * nsp - (long long)__popc(dm);
+        const unsigned long long o = atomicAdd(&A.ctl[CTL_OUTSTANDING], (unsigned long long)delta);
         asm volatile("" ::"l"(o) : "memory");
-        base = atomicAdd(&A.ctl[CTL_TAIL], 3ULL * nsp);
-        __threadfence();
+        if (nsp) {
+          base = atomicAdd(&A.ctl[CTL_TAIL], 3ULL * nsp);
+          __threadfence();
+        }
       }
       base = __shfl_sync(kFull, base, leader);
+      if (ev == EV_DONE) {
+        active = false;
+        ev = EV_NONE;
+      }
       if (split) {
         w.on_split(A, acc);
         const unsigned long long my = base + 3ULL * __popc(sm & lt_mask);
@@ -797,17 +840,44 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         }
       }
     }
-    // (6) finished packages leave the outstanding count
+    // (6) a child 0 that starts outside the box is finished too
     const bool done = (ev == EV_DONE);
-    const unsigned dm = __ballot_sync(kFull, done);
-    if (dm) {
-      if (lane == __ffs(dm) - 1)
-        atomicAdd(&A.ctl[CTL_OUTSTANDING], (unsigned long long)(-(long long)__popc(dm)));
+    const unsigned dm2 = __ballot_sync(kFull, done);
+    if (dm2) {
+      if (lane == __ffs(dm2) - 1)
+        atomicAdd(&A.ctl[CTL_OUTSTANDING], (unsigned long long)(-(long long)__popc(dm2)));
       if (done) active = false;
     }
   }
   acc.segments += w.nseg;
-  acc_flush(acc, A);
+  // The lanes' budget sums: where every lane of the block last worked on the
+  // same grid (or on none), reduce them in shared memory and flush once per
+  // block, instead of 256 atomics per word onto the same few addresses.
+  __shared__ int sh_inst;
+  if (threadIdx.x == 0) sh_inst = -1;
+  __syncthreads();
+  if (acc.inst >= 0) atomicMax(&sh_inst, acc.inst);
+  __syncthreads();
+  if (__syncthreads_and(acc.inst < 0 || acc.inst == sh_inst)) {
+    for (int h = kBlock / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) {
+        LaneAcc& o = sh_acc[threadIdx.x + h];
+        acc.emitted += o.emitted;
+        acc.absorbed += o.absorbed;
+        acc.escaped += o.escaped;
+        acc.segments += o.segments;
+        acc.fallbacks += o.fallbacks;
+        acc.fallbacks_tau += o.fallbacks_tau;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      acc.inst = sh_inst;
+      acc_flush(acc, A);
+    }
+  } else {
+    acc_flush(acc, A);
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < kShInst * kLevels; i += blockDim.x) {
     const int inst = i / kLevels, l = i - inst * kLevels;
