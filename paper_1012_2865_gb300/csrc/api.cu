@@ -6,7 +6,6 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -112,24 +111,6 @@ struct TraceState {
   }
 };
 
-// Host view of a source for the L2 prefetch: its cell and its grid's shape.
-struct PfSrc {
-  int x, y, z, nx, ny, nz;
-  int elem;  // bytes of n_HI per cell
-};
-
-static PfSrc pf_src(const SourceDev& S, int nx, int ny, int nz, int elem) {
-  PfSrc p;
-  const int c[3] = {(int)floor(S.s[0]), (int)floor(S.s[1]), (int)floor(S.s[2])};
-  const int n[3] = {nx, ny, nz};
-  int v[3];
-  for (int a = 0; a < 3; ++a) v[a] = c[a] < 0 ? 0 : (c[a] >= n[a] ? n[a] - 1 : c[a]);
-  p.x = v[0]; p.y = v[1]; p.z = v[2];
-  p.nx = nx; p.ny = ny; p.nz = nz;
-  p.elem = elem;
-  return p;
-}
-
 struct rt_grid {
   rt_ctx* ctx;
   int nx, ny, nz;
@@ -148,7 +129,6 @@ struct rt_grid {
   InstDev* inst_dev = nullptr;
   struct SrcIn { double pos[3], ndot, e_ph, sigma; };
   std::vector<SrcIn> src;              // sources as given by the caller
-  std::vector<PfSrc> pf;        // their cells, for the L2 prefetch
   SourceDev* src_dev = nullptr;
   size_t src_dev_cap = 0;
   bool src_dirty = true;
@@ -379,8 +359,6 @@ static int prepare_sources(rt_grid* g, int level0) {
   if (!g->src_dirty && g->last_level0 == level0) return RT_OK;
   std::vector<SourceDev> v;
   build_sources(g, level0, 0, v);
-  g->pf.clear();  // n_HI takes 8 bytes a cell: FP64, or an FP32 pair
-  for (const SourceDev& S : v) g->pf.push_back(pf_src(S, g->nx, g->ny, g->nz, 8));
   if (v.size() > g->src_dev_cap) {
     if (g->src_dev) cudaFree(g->src_dev);
     g->src_dev = nullptr;
@@ -448,36 +426,8 @@ static void fill_common_args(TraceArgs& A, const rt_trace_params* p) {
 // once; deposits, budget sums and counters accumulate across the passes.
 // A.npix0, A.queue, A.cap, A.ctl and the per-trace fields are set by the
 // caller; A.src, A.nsrc and A.n_roots are set here per pass.
-// Largest radius (cells) whose clipped boxes around sources [s0, s1) hold at
-// most kPrefetchBytes of n_HI; 0 below 2 cells.  A box of radius R around
-// each source is what the first levels of its ray tree read.
-constexpr double kPrefetchBytes = 48.0 * (1 << 20);
-static int prefetch_radius(const std::vector<PfSrc>& pf, int s0, int s1) {
-  if (s1 <= s0) return 0;
-  auto bytes = [&](int R) {
-    double b = 0;
-    for (int i = s0; i < s1; ++i) {
-      const PfSrc& p = pf[i];
-      const double lx = (double)(std::min(p.nx - 1, p.x + R) - std::max(0, p.x - R) + 1);
-      const double ly = (double)(std::min(p.ny - 1, p.y + R) - std::max(0, p.y - R) + 1);
-      const double lz = (double)(std::min(p.nz - 1, p.z + R) - std::max(0, p.z - R) + 1);
-      b += lx * ly * lz * p.elem;
-    }
-    return b;
-  };
-  int hi = 0;
-  for (int i = s0; i < s1; ++i) hi = std::max(hi, std::max(pf[i].nx, std::max(pf[i].ny, pf[i].nz)));
-  int lo = 0;
-  while (lo < hi) {  // largest R in [0, hi] with bytes(R) <= budget
-    const int mid = (lo + hi + 1) / 2;
-    if (bytes(mid) <= kPrefetchBytes) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo >= 2 ? lo : 0;
-}
-
 static int launch_passes(TraceArgs A, const SourceDev* src, int nsrc, int passes, int precision, int blocks,
-                         cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st, const std::vector<PfSrc>& pf) {
+                         cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st) {
   if (passes > nsrc) passes = nsrc;
   if (passes < 1) passes = 1;
   for (int i = 0; i < passes; ++i) {
@@ -490,7 +440,6 @@ static int launch_passes(TraceArgs A, const SourceDev* src, int nsrc, int passes
     A.src = src + s0;
     A.nsrc = s1 - s0;
     A.n_roots = n;
-    A.pf_radius = (int)pf.size() == nsrc ? prefetch_radius(pf, s0, s1) : 0;
     LAUNCH_TRY(launch_trace(precision, A, blocks, 256, st));
   }
   CUDA_TRY(cudaEventRecord(ev1, st));
@@ -577,8 +526,7 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes) {
   CUDA_TRY(trace_occupancy(g->precision, block, &per_sm));
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
-  if ((rc = launch_passes(A, g->src_dev, nsrc, passes, g->precision, per_sm * g->ctx->num_sms, g->ev0, g->ev1, st,
-                          g->pf)))
+  if ((rc = launch_passes(A, g->src_dev, nsrc, passes, g->precision, per_sm * g->ctx->num_sms, g->ev0, g->ev1, st)))
     return rc;
   g->traced = true;
   g->ts.passes_run = passes < nsrc ? passes : nsrc;
@@ -794,7 +742,6 @@ struct rt_batch {
   SourceDev* src_dev = nullptr;
   size_t src_cap = 0;
   int nsrc = 0;
-  std::vector<PfSrc> pf;  // source cells, for the L2 prefetch
   unsigned long long n_roots = 0;
   long long max_cells = 0;
   int max_dims = 0;
@@ -830,7 +777,6 @@ static int batch_rebuild(rt_batch* b, int level0) {
   std::vector<InstDev> inst;
   std::vector<SourceDev> src;
   b->dev_slot.clear();
-  b->pf.clear();
   b->max_cells = 0;
   b->max_dims = 0;
   double diag = 0;
@@ -843,9 +789,7 @@ static int batch_rebuild(rt_batch* b, int level0) {
     I.flags = g->precision == RT_FP32_MIXED ? kInstNhiPair : 0;
     I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.xHII = g->xHII; I.K = g->K; I.G = g->G;
     I.acc = g->acc; I.cnt = g->cnt;
-    const size_t first = src.size();
     build_sources(g, level0, (int)inst.size(), src);
-    for (size_t k = first; k < src.size(); ++k) b->pf.push_back(pf_src(src[k], g->nx, g->ny, g->nz, 8));
     inst.push_back(I);
     b->dev_slot.push_back((int)s);
     if (g->ncell > b->max_cells) b->max_cells = g->ncell;
@@ -922,7 +866,7 @@ static int batch_enqueue(rt_batch* b, const rt_trace_params* p, int passes) {
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
   if ((rc = launch_passes(A, b->src_dev, b->nsrc, passes, b->precision, per_sm * b->ctx->num_sms, b->ev0, b->ev1,
-                          st, b->pf)))
+                          st)))
     return rc;
   b->traced = true;
   b->ts.passes_run = passes < b->nsrc ? passes : b->nsrc;

@@ -111,7 +111,6 @@ struct TraceArgs {
   int segs_per_iter;
   int max_steps;  // bound on segments of one package (guards the DDA loop)
   int checksums;  // accumulate the created-set checksum
-  int pf_radius;  // prefetch n_HI within this many cells of each source into L2 first (0: none)
 };
 
 // 64-bit finaliser used for the created-package checksum (documented in rt.h).

@@ -115,7 +115,6 @@ __device__ __forceinline__ double next_t64(int c, double s, double n) {
 
 struct Walk64 {
   using Rec = Rec64;
-  static constexpr int kNhiBytes = 8;
   uint32_t src, level, pix;
   double r, P, tau, Pstart;
   double s0, s1, s2, n0, n1, n2, t0, t1, t2;
@@ -369,7 +368,6 @@ __device__ __noinline__ int decide64(const TraceArgs& A, uint32_t src, int level
 
 struct Walk32 {
   using Rec = Rec32;
-  static constexpr int kNhiBytes = 4;  // per cell; twice that where n_HI is a pair
   uint32_t src, pix;
   uint32_t level;       // bits 0-3 level, bit 8: 45-degree ray of an exact source,
                         // bit 9: n_HI stored as FP32 pairs
@@ -656,40 +654,9 @@ struct Walk32 {
 // ---------------------------------------------------------------------------
 // The persistent kernel, generic over the walker.
 // ---------------------------------------------------------------------------
-// Before the queue loop: every thread prefetches into L2 a share of the n_HI
-// rows within A.pf_radius cells of each source (clipped to its grid).  The
-// first levels of the ray tree have few packages, each waiting on the
-// memory latency of every cell it enters; with the rows already in L2 that
-// wait is an L2 hit.  elem: bytes per cell of the walker's n_HI.
-__device__ __forceinline__ void prefetch_sources(const TraceArgs& A, int elem_base) {
-  const int R = A.pf_radius, w = 2 * R + 1;
-  const long long rows = (long long)A.nsrc * w * w;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows; i += stride) {
-    const int si = (int)(i / (w * w));
-    const int rr = (int)(i - (long long)si * w * w);
-    const SourceDev& S = A.src[si];
-    const InstDev& I = A.inst[S.inst];
-    const float4 s32 = __ldg(&S.s32);
-    const int sx = min(max((int)floorf(s32.x), 0), I.nx - 1);
-    const int sy = min(max((int)floorf(s32.y), 0), I.ny - 1);
-    const int sz = min(max((int)floorf(s32.z), 0), I.nz - 1);
-    const int y = sy - R + rr % w, z = sz - R + rr / w;
-    if (y < 0 || y >= I.ny || z < 0 || z >= I.nz) continue;
-    const int x0 = max(sx - R, 0), x1 = min(sx + R, I.nx - 1);
-    const int elem = (I.flags & kInstNhiPair) ? 2 * elem_base : elem_base;
-    const size_t row = ((size_t)z * I.ny + y) * I.nx;
-    const char* p = (const char*)I.nhi + (row + x0) * elem;
-    const char* last = (const char*)I.nhi + (row + x1) * elem;  // every address stays inside the row
-    for (; p < last; p += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(last));
-  }
-}
-
 template <class W, int MinBlocks>
 __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   using Rec = typename W::Rec;
-  if (A.pf_radius > 0) prefetch_sources(A, W::kNhiBytes);
   __shared__ unsigned int sh_cnt[kShInst * kLevels];
   __shared__ unsigned long long sh_hsh[kShInst * kLevels];
   __shared__ LaneAcc sh_acc[kBlock];
