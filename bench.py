@@ -35,7 +35,12 @@ UNIT = "ray-segments/s"
 WORKLOAD = ("stromgren-128^3: Test-1 medium (6.6 kpc, n_H=1e-3, corner source 5e48 ph/s, 13.6 eV), "
             "I-front at the 500 Myr radius; step = rt_trace (level 1, Phi_c 5.1, f_term 1e-10) + "
             "rt_chem_update (0.5 Myr, 10 substeps)")
+WORKLOAD_CLUMPY = ("clumpy-256^3: log-normal medium (P(k) ~ k^-3, sigma_ln 1, mean n_H 1e-2), 1000 sources "
+                   "of 1e48-1e50 ph/s at random cell centres, x_HI = 1; step = rt_trace (level 1, Phi_c 5.1, "
+                   "f_term 1e-10) + rt_chem_update (0.5 Myr, 10 substeps)")
 DT_S = 0.5 * 3.15576e13
+# the trace kernel's sources: a profile summary's DRAM traffic holds only for these exact files
+TRACE_SOURCES = ("trace.cu", "rt_internal.cuh", "f2.cuh", "healpix.cuh")
 
 
 def _dist():
@@ -103,6 +108,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRACE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1012_2865_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _profiled_traffic(precision: str, workload: str):
+    """DRAM bytes per trace launch from the committed ncu summary of this
+    workload, or None when there is none or the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", f"trace_kernel_{precision}_{workload}.md")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        if fields.get("kernel_source_sha256") != _kernel_source_hash():
+            return None
+        return float(fields["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -120,7 +152,7 @@ def run_native(args, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = native.rt_ctx_create(local)
-    g = synth.stromgren_snapshot(args.grid)
+    g = synth.clumpy() if args.workload == "clumpy" else synth.stromgren_snapshot(args.grid)
     params = dict(synth.DEFAULT_PARAMS)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
@@ -206,24 +238,30 @@ def run_native(args, rank, world, local):
     value = r["segments"] * world / total_s
     ee = e2e(head) if not args.no_e2e else dict(value=None, h2d=0, d2h=0)
     peaks, peak_kind = _peaks()
-    ebytes = 8 if head == "fp64" else 4
-    rec = 48 if head == "fp64" else 32
-    # algorithmic bytes per launch: n_HI read + k_ph RED per segment (Gamma is
-    # identically 0 for 13.6 eV photons) + one write and one read per queue record
-    alg = r["seg_per_step"] * 2 * ebytes + r["pushed"] * 2 * rec
+    # algorithmic bytes per launch: per segment the n_HI read (FP64, or the FP32
+    # pair: 8 bytes) and the k_ph reduction (8 / 4 bytes; Gamma is identically 0
+    # for 13.6 eV photons); per queue record one write and one read of 48 bytes
+    red = 8 if head == "fp64" else 4
+    alg = r["seg_per_step"] * (8 + red) + r["pushed"] * 2 * 48
     achieved = alg / (kern_s / args.steps) / 1e9
+    wtag = "clumpy256" if args.workload == "clumpy" else f"stromgren{args.grid}"
+    traffic = _profiled_traffic(head, wtag)
+    if args.workload == "clumpy":
+        wl = WORKLOAD_CLUMPY
+    else:
+        wl = WORKLOAD if args.grid == 128 else WORKLOAD.replace("128^3", f"{args.grid}^3")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if head == "fp64" else "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.grid == 128 else WORKLOAD.replace("128^3", f"{args.grid}^3"),
+        "config": {"workload": wl,
                    "precision": head, "segments_per_step": r["seg_per_step"],
                    "queue_records_per_step": r["pushed"], "l2": "flushed (512 MB write) between steps",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0),
                      "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs", 6800.0),
-                     "traffic": None, "peak_kind": peak_kind,
+                     "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes": alg,
                      "kernel": "trace_kernel", "kernel_ms": 1e3 * kern_s / args.steps},
         "e2e": {"value": ee["value"], "unit": UNIT, "h2d_bytes_per_step": ee["h2d"],
                 "d2h_bytes_per_step": ee["d2h"]},
@@ -404,6 +442,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-fp64-budget-s", type=float, default=90.0)
     ap.add_argument("--grid", type=int, default=128, help="cells per side (128 = the benchmark workload)")
+    ap.add_argument("--workload", default="stromgren", choices=["stromgren", "clumpy"],
+                    help="stromgren: the benchmark workload; clumpy: the 256^3 multi-source case (profiling)")
     args = ap.parse_args()
     args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
     rank, world, local = _dist()

@@ -25,6 +25,11 @@ __device__ __forceinline__ void chem_cell_fp64(double& x, double& z, double n, d
   }
 }
 
+// x == 1 and z == 0 (either sign), compared as bit patterns
+__device__ __forceinline__ bool is_neutral(double x, double z) {
+  return __double_as_longlong(x) == 0x3FF0000000000000LL && (__double_as_longlong(z) << 1) == 0;
+}
+
 // One cell, FP32-mixed path: FP32 solution + one double-float Newton
 // correction per substep (see chem_mixed_kernel).  x, z and n arrive and
 // leave in FP64; in between they are carried as double-float pairs.  ha and
@@ -102,13 +107,13 @@ __global__ void chem_kernel(long long ncell, const double* __restrict__ nH, doub
 // FP32 pipe; FP64 is used only to load and store the state.
 __global__ void chem_mixed_kernel(long long ncell, const double* __restrict__ nH, double* __restrict__ xHI,
                                   double* __restrict__ xHII, const float* __restrict__ K,
-                                  float2* __restrict__ nhi, double h, int nsub, double alpha) {
-  const F2 ha = f2_from_double(h * alpha), h2 = f2_from_double(h);
+                                  float2* __restrict__ nhi, float4 hh, int nsub) {
+  const F2 ha = {hh.x, hh.y}, h2 = {hh.z, hh.w};
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
     double x = xHI[c], z = xHII[c];
     const float kc = K[c];
-    if (kc == 0.0f && z == 0.0 && x == 1.0) continue;
+    if (kc == 0.0f && is_neutral(x, z)) continue;
     const F2 nx = chem_cell_mixed(x, z, nH[c], kc, ha, h2, nsub);
     xHI[c] = x;
     xHII[c] = z;
@@ -148,6 +153,13 @@ __global__ void complement_kernel(long long n, const double* __restrict__ x, dou
     out[c] = __dsub_rn(1.0, x[c]);
 }
 
+// h alpha_B and h as FP32 pairs (host side), for the mixed update kernels
+static float4 step_pairs(double h, double alpha) {
+  const double ha = h * alpha;
+  const float a_hi = (float)ha, h_hi = (float)h;
+  return make_float4(a_hi, (float)(ha - (double)a_hi), h_hi, (float)(h - (double)h_hi));
+}
+
 static int grid_for(long long n, int block) {
   long long g = (n + block - 1) / block;
   if (g > 152 * 32) g = 152 * 32;
@@ -162,8 +174,8 @@ cudaError_t launch_chem(int precision, long long ncell, const double* nH, double
     chem_kernel<double, double><<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const double*)K,
                                                          (double*)nhi, h, nsub, alpha);
   else
-    chem_mixed_kernel<<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const float*)K, (float2*)nhi, h, nsub,
-                                              alpha);
+    chem_mixed_kernel<<<grid, block, 0, st>>>(ncell, nH, xHI, xHII, (const float*)K, (float2*)nhi,
+                                              step_pairs(h, alpha), nsub);
   return cudaGetLastError();
 }
 
@@ -208,16 +220,16 @@ __global__ void batch_zero_kernel(const InstDev* __restrict__ inst, int esz) {
 }
 
 template <bool MIXED>
-__global__ void batch_chem_kernel(const InstDev* __restrict__ inst, double h, int nsub, double alpha) {
+__global__ void batch_chem_kernel(const InstDev* __restrict__ inst, double h, int nsub, double alpha, float4 hh) {
   const InstDev I = inst[blockIdx.y];
-  const F2 ha = f2_from_double(h * alpha), h2 = f2_from_double(h);
+  const F2 ha = {hh.x, hh.y}, h2 = {hh.z, hh.w};
   const long long n = (long long)I.nx * I.ny * I.nz;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
     double x = I.xHI[c], z = I.xHII[c];
     if (MIXED) {
       const float kc = ((const float*)I.K)[c];
-      if (kc == 0.0f && z == 0.0 && x == 1.0) continue;
+      if (kc == 0.0f && is_neutral(x, z)) continue;
       const F2 nx = chem_cell_mixed(x, z, I.nH[c], kc, ha, h2, nsub);
       ((double*)I.xHI)[c] = x;
       I.xHII[c] = z;
@@ -251,9 +263,11 @@ cudaError_t launch_batch_chem(const InstDev* inst, int ninst, int precision, lon
   if (bx > 64) bx = 64;
   if (bx < 1) bx = 1;
   if (precision == RT_FP64)
-    batch_chem_kernel<false><<<dim3((unsigned)bx, (unsigned)ninst), 256, 0, st>>>(inst, h, nsub, alpha);
+    batch_chem_kernel<false><<<dim3((unsigned)bx, (unsigned)ninst), 256, 0, st>>>(inst, h, nsub, alpha,
+                                                                                   step_pairs(h, alpha));
   else
-    batch_chem_kernel<true><<<dim3((unsigned)bx, (unsigned)ninst), 256, 0, st>>>(inst, h, nsub, alpha);
+    batch_chem_kernel<true><<<dim3((unsigned)bx, (unsigned)ninst), 256, 0, st>>>(inst, h, nsub, alpha,
+                                                                                  step_pairs(h, alpha));
   return cudaGetLastError();
 }
 

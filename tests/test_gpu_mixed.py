@@ -21,6 +21,26 @@ def test_fp32_direction_bound_holds(level):
     assert err <= 0.5 * bound, (level, err, bound)
 
 
+@pytest.mark.parametrize("precision", ["fp32_mixed", "fp64"])
+def test_update_matches_oracle_on_the_same_rates(precision):
+    """The ionisation update alone: given the rates this grid's own trace
+    deposited, the GPU update equals the oracle's to rounding (FP64: the same
+    operations; FP32-mixed: double-float Newton corrections, ~1e-13)."""
+    g = synth.clumpy(N=32, nsrc=20, seed=5)
+    rng = np.random.default_rng(3)
+    g["x_HI"] = np.where(rng.random(32 ** 3) < 0.5, 1.0, 10.0 ** rng.uniform(-9, 0, 32 ** 3))
+    g["x_HII"] = 1.0 - g["x_HI"]
+    grid, b, r = parity.run_gpu(g, precision)
+    grid.chem(synth.MYR_S, 10, synth.ALPHA_B)
+    x_gpu = grid.rates()["x_HI"]
+    x_o, z_o = oracle.chem(g["n_H"], g["x_HI"], g["x_HII"], np.asarray(r["kph"], dtype=np.float64), synth.MYR_S, 10,
+                           synth.ALPHA_B)
+    rtol = 1e-14 if precision == "fp64" else 1e-11
+    np.testing.assert_allclose(x_gpu, x_o, rtol=rtol, atol=1e-300)
+    np.testing.assert_allclose(1.0 - x_gpu[x_gpu < 0.5], z_o[x_gpu < 0.5], rtol=1e-9)
+    grid.close()
+
+
 def test_config0_mixed():
     g = synth.stromgren(32)
     grid, b, r = parity.run_gpu(g, "fp32_mixed")
