@@ -108,6 +108,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def barrier():
+    """Barrier across ranks (no-op without an initialised process group)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def reduce_over_ranks(total_s: float, segments: int):
+    """Replicas: the slowest rank's timed seconds and the work of all ranks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_s, segments
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    n = torch.tensor([segments], dtype=torch.int64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 def _kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -174,6 +195,8 @@ def run_native(args, rank, world, local):
         step_ms, kern_ms = [], []
         segs = 0
         launches = 0
+        torch.cuda.synchronize()
+        barrier()
         with ClockSampler(local) as clk:
             for _ in range(args.steps):
                 native.rt_set_state(grid.h, x0, z0)  # restore the snapshot (untimed)
@@ -192,6 +215,8 @@ def run_native(args, rank, world, local):
                 kern_ms.append(bb["kernel_ms"])
                 segs += bb["segments"]
                 assert bb["segments"] == seg_per_step
+        torch.cuda.synchronize()
+        barrier()
         grid.close()
         return dict(step_ms=step_ms, kern_ms=kern_ms, segments=segs, seg_per_step=seg_per_step,
                     pushed=pushed, launches=launches, clocks=clk.summary())
@@ -229,19 +254,16 @@ def run_native(args, rank, world, local):
     r = res[head]
     total_s = sum(r["step_ms"]) / 1e3
     kern_s = sum(r["kern_ms"]) / 1e3
-    # max over ranks, sum of work
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = r["segments"] * world / total_s
+    # the slowest rank's time, the work of all ranks
+    total_s, all_segments = reduce_over_ranks(total_s, r["segments"])
+    value = all_segments / total_s
     ee = e2e(head) if not args.no_e2e else dict(value=None, h2d=0, d2h=0)
     peaks, peak_kind = _peaks()
     # algorithmic bytes per launch: per segment the n_HI read (FP64, or the FP32
-    # pair: 8 bytes) and the k_ph reduction (8 / 4 bytes; Gamma is identically 0
-    # for 13.6 eV photons); per queue record one write and one read of 48 bytes
-    red = 8 if head == "fp64" else 4
+    # pair: 8 bytes) and the k_ph reduction (8 / 4 bytes), plus the Gamma
+    # reduction where photons carry energy above 13.6 eV; per queue record one
+    # write and one read of 48 bytes
+    red = (8 if head == "fp64" else 4) * (2 if np.any(np.asarray(g["e_ph_eV"]) > 13.6) else 1)
     alg = r["seg_per_step"] * (8 + red) + r["pushed"] * 2 * 48
     achieved = alg / (kern_s / args.steps) / 1e9
     wtag = "clumpy256" if args.workload == "clumpy" else f"stromgren{args.grid}"
@@ -273,9 +295,10 @@ def run_native(args, rank, world, local):
         out[f"{prec}_path"] = {"value": q["segments"] * world / (sum(q["step_ms"]) / 1e3),
                                "ms_per_step": sum(q["step_ms"]) / args.steps,
                                "kernel_ms": sum(q["kern_ms"]) / args.steps}
-    if not args.no_batched:
+    # the batched and serving configurations are measured on one GPU
+    if not args.no_batched and world == 1:
         out["batched"] = batched(args, ctx, stream, dev, world)
-    if not args.no_serving:
+    if not args.no_serving and world == 1:
         out["serving"] = serving(args, ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
