@@ -548,13 +548,26 @@ struct Walk32 {
     return (m0 ? 1 : 0) | (m1 ? 2 : 0) | (m2 ? 4 : 0) | (split ? 8 : 0) | (imin << 4);
   }
   // Cross the planes of `m` (bits 0-2) at distance rn.
+  // The first crossed axis is selected rather than branched on, so the lanes
+  // of a warp (crossing different axes) evaluate one next_t together; a
+  // second or third axis crossed at the same point (edges, corners) is rare.
   __device__ __forceinline__ void advance(const TraceArgs& A, int m, F2 rn) {
-    if (m & 7) {
+    const int mm = m & 7;
+    if (mm) {
       const float4 sh = __ldg(&A.src[src].s32);
       const float4 sl = __ldg(&A.src[src].slo32);
-      if (m & 1) { c0 += iv0.hi > 0.0f ? 1 : -1; t0 = next_t(c0, sh.x, sl.x, iv0); }
-      if (m & 2) { c1 += iv1.hi > 0.0f ? 1 : -1; t1 = next_t(c1, sh.y, sl.y, iv1); }
-      if (m & 4) { c2 += iv2.hi > 0.0f ? 1 : -1; t2 = next_t(c2, sh.z, sl.z, iv2); }
+      const int a = (mm & 1) ? 0 : ((mm & 2) ? 1 : 2);
+      const F2 iv = a == 0 ? iv0 : (a == 1 ? iv1 : iv2);
+      const int c = (a == 0 ? c0 : (a == 1 ? c1 : c2)) + (iv.hi > 0.0f ? 1 : -1);
+      const F2 t = next_t(c, a == 0 ? sh.x : (a == 1 ? sh.y : sh.z), a == 0 ? sl.x : (a == 1 ? sl.y : sl.z), iv);
+      if (a == 0) { c0 = c; t0 = t; }
+      else if (a == 1) { c1 = c; t1 = t; }
+      else { c2 = c; t2 = t; }
+      const int rest = mm & ~(1 << a);
+      if (rest) {
+        if (rest & 2) { c1 += iv1.hi > 0.0f ? 1 : -1; t1 = next_t(c1, sh.y, sl.y, iv1); }
+        if (rest & 4) { c2 += iv2.hi > 0.0f ? 1 : -1; t2 = next_t(c2, sh.z, sl.z, iv2); }
+      }
     }
     r = rn;
   }
