@@ -120,6 +120,8 @@ int rt_ctx_destroy(rt_ctx* ctx);
 
 /* Create a grid (Sec. 2.2 state: n_H, x_HI, x_HII) in library-owned device
  * memory.  The caller's arrays are copied; they may be freed on return.
+ * n_H must be finite and >= 0 and x_HI in [0, 1] in every cell (checked on
+ * the device; RT_ERR_INVALID_ARG names the first failing cell).
  * stream: cudaStream_t for all later work on this grid. */
 int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* desc, void* stream, rt_grid** out);
 int rt_grid_destroy(rt_grid* grid);
@@ -157,8 +159,10 @@ int rt_chem_update(rt_grid* grid, double dt_s, int nsub, double alpha_B);
 
 /* Replace the gas state of every cell (Sec. 2.2): n_H (may be NULL to keep
  * it), x_HI, and x_HII (NULL for 1 - x_HI), in memory mem_kind, same checks
- * as rt_create_grid; refreshes the absorber density.  Asynchronous for
- * device pointers; host arrays are copied before the call returns. */
+ * as rt_create_grid; refreshes the absorber density.  The new state is
+ * staged and checked on the device: the call returns once the check is done
+ * (the caller's arrays may then be reused) and leaves the state unchanged
+ * when it fails. */
 int rt_set_state(rt_grid* grid, const double* n_H, const double* x_HI, const double* x_HII,
                  int mem_kind);
 

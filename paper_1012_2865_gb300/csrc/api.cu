@@ -26,6 +26,8 @@ cudaError_t launch_refresh(int precision, long long ncell, const double* nH, con
 cudaError_t launch_convert(long long n, const void* src, int src_dtype, void* dst, int dst_dtype,
                            cudaStream_t st);
 cudaError_t launch_complement(long long n, const double* x, double* out, cudaStream_t st);
+cudaError_t launch_check_state(long long n, const double* nH, const double* x, unsigned long long* bad,
+                               cudaStream_t st);
 cudaError_t launch_direction_check(int level, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st);
 cudaError_t launch_batch_zero(const InstDev* inst, int ninst, int precision, long long max_cells, cudaStream_t st);
@@ -182,6 +184,29 @@ int rt_ctx_destroy(rt_ctx* ctx) {
   return RT_OK;
 }
 
+// Range check of a state already on the device (nH may be NULL), on stream
+// st: RT_OK, or RT_ERR_INVALID_ARG naming the first bad cell and its value.
+// Synchronises st.
+static int check_state(const char* who, long long ncell, const double* nH, const double* x, cudaStream_t st) {
+  unsigned long long* bad = nullptr;
+  CUDA_TRY(cudaMallocAsync((void**)&bad, 2 * sizeof(unsigned long long), st));
+  unsigned long long h[2] = {0, 0};
+  cudaError_t e = cudaMemsetAsync(bad, 0xff, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = launch_check_state(ncell, nH, x, bad, st);
+  if (e == cudaSuccess) g_launches.fetch_add(1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, bad, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(bad, st);
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, "%s: state check: %s", who, cudaGetErrorString(e));
+  for (int k = 0; k < 2; ++k) {
+    if (h[k] == ~0ULL) continue;
+    double v = 0.0;
+    cudaMemcpy(&v, (k == 0 ? nH : x) + h[k], sizeof v, cudaMemcpyDeviceToHost);
+    return fail(RT_ERR_INVALID_ARG, "%s: %s[%llu] = %g", who, k == 0 ? "n_H" : "x_HI", h[k], v);
+  }
+  return RT_OK;
+}
+
 static int upload(void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_t st) {
   CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, mem_kind == RT_MEM_DEVICE ? cudaMemcpyDeviceToDevice
                                                                         : cudaMemcpyHostToDevice, st));
@@ -200,13 +225,6 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
   if (d->mem_kind != RT_MEM_HOST && d->mem_kind != RT_MEM_DEVICE)
     return fail(RT_ERR_INVALID_ARG, "rt_create_grid: unknown mem_kind %d", d->mem_kind);
   if (!d->n_H || !d->x_HI) return fail(RT_ERR_INVALID_ARG, "rt_create_grid: n_H and x_HI are required");
-  if (d->mem_kind == RT_MEM_HOST) {
-    for (long long c = 0; c < ncell; ++c) {
-      const double n = d->n_H[c], x = d->x_HI[c];
-      if (!(n >= 0) || !isfinite(n)) return fail(RT_ERR_INVALID_ARG, "rt_create_grid: n_H[%lld] = %g", c, n);
-      if (!(x >= 0 && x <= 1)) return fail(RT_ERR_INVALID_ARG, "rt_create_grid: x_HI[%lld] = %g", c, x);
-    }
-  }
   CUDA_TRY(cudaSetDevice(ctx->device));
   rt_grid* g = new rt_grid;
   g->ctx = ctx;
@@ -240,6 +258,8 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
   cudaStream_t st = g->stream;
   if ((rc = upload(g->nH, d->n_H, n8, d->mem_kind, st)) != RT_OK) { delete g; return rc; }
   if ((rc = upload(g->xHI, d->x_HI, n8, d->mem_kind, st)) != RT_OK) { delete g; return rc; }
+  // the values are checked on the device once they are there
+  if ((rc = check_state("rt_create_grid", ncell, g->nH, g->xHI, st)) != RT_OK) { delete g; return rc; }
   if (d->x_HII) {
     if ((rc = upload(g->xHII, d->x_HII, n8, d->mem_kind, st)) != RT_OK) { delete g; return rc; }
   } else {
@@ -625,26 +645,36 @@ int rt_set_state(rt_grid* g, const double* n_H, const double* x_HI, const double
   if (!g || !x_HI) return fail(RT_ERR_INVALID_ARG, "rt_set_state: grid and x_HI are required");
   if (int rcw = wait_batch(g)) return rcw;
   if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE) return fail(RT_ERR_INVALID_ARG, "rt_set_state: mem_kind %d", mem_kind);
-  const long long ncell = g->ncell;
-  if (mem_kind == RT_MEM_HOST) {
-    for (long long c = 0; c < ncell; ++c) {
-      if (n_H && (!(n_H[c] >= 0) || !isfinite(n_H[c]))) return fail(RT_ERR_INVALID_ARG, "rt_set_state: n_H[%lld] = %g", c, n_H[c]);
-      if (!(x_HI[c] >= 0 && x_HI[c] <= 1)) return fail(RT_ERR_INVALID_ARG, "rt_set_state: x_HI[%lld] = %g", c, x_HI[c]);
-    }
-  }
   CUDA_TRY(cudaSetDevice(g->ctx->device));
+  const long long ncell = g->ncell;
   const size_t n8 = (size_t)ncell * 8;
-  int rc;
   cudaStream_t st = g->stream;
-  if (n_H && (rc = upload(g->nH, n_H, n8, mem_kind, st))) return rc;
-  if ((rc = upload(g->xHI, x_HI, n8, mem_kind, st))) return rc;
+  // stage the new state on the device, check it there, and only then replace
+  // the grid's state (which an invalid call leaves unchanged)
+  const int nf = (n_H ? 1 : 0) + 1 + (x_HII ? 1 : 0);
+  double* stage = nullptr;
+  CUDA_TRY(cudaMallocAsync((void**)&stage, nf * n8, st));
+  double* sn = n_H ? stage : nullptr;
+  double* sx = stage + (n_H ? ncell : 0);
+  double* sz = x_HII ? sx + ncell : nullptr;
+  int rc = RT_OK;
+  if (n_H) rc = upload(sn, n_H, n8, mem_kind, st);
+  if (!rc) rc = upload(sx, x_HI, n8, mem_kind, st);
+  if (!rc && x_HII) rc = upload(sz, x_HII, n8, mem_kind, st);
+  if (!rc) rc = check_state("rt_set_state", ncell, sn, sx, st);
+  if (rc) {
+    cudaFreeAsync(stage, st);
+    return rc;
+  }
+  if (n_H) CUDA_TRY(cudaMemcpyAsync(g->nH, sn, n8, cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(g->xHI, sx, n8, cudaMemcpyDeviceToDevice, st));
   if (x_HII) {
-    if ((rc = upload(g->xHII, x_HII, n8, mem_kind, st))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(g->xHII, sz, n8, cudaMemcpyDeviceToDevice, st));
   } else {
     LAUNCH_TRY(launch_complement(ncell, g->xHI, g->xHII, st));
   }
   LAUNCH_TRY(launch_refresh(g->precision, ncell, g->nH, g->xHI, g->nhi, st));
-  if (mem_kind == RT_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+  CUDA_TRY(cudaFreeAsync(stage, st));
   return RT_OK;
 }
 

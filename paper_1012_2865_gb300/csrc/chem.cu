@@ -153,6 +153,21 @@ __global__ void complement_kernel(long long n, const double* __restrict__ x, dou
     out[c] = __dsub_rn(1.0, x[c]);
 }
 
+// Range check of a gas state: bad[0] = first cell whose n_H is negative, NaN
+// or infinite (nH may be NULL), bad[1] = first cell whose x_HI lies outside
+// [0, 1] or is NaN; entries stay at ~0 when every cell passes.
+__global__ void check_state_kernel(long long n, const double* __restrict__ nH, const double* __restrict__ x,
+                                   unsigned long long* __restrict__ bad) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    if (nH) {
+      const double v = nH[c];
+      if (!(v >= 0.0) || isinf(v)) atomicMin(&bad[0], (unsigned long long)c);
+    }
+    const double xv = x[c];
+    if (!(xv >= 0.0 && xv <= 1.0)) atomicMin(&bad[1], (unsigned long long)c);
+  }
+}
+
 // h alpha_B and h as FP32 pairs (host side), for the mixed update kernels
 static float4 step_pairs(double h, double alpha) {
   const double ha = h * alpha;
@@ -186,6 +201,13 @@ cudaError_t launch_refresh(int precision, long long ncell, const double* nH, con
     refresh_nhi_kernel<double><<<grid, block, 0, st>>>(ncell, nH, xHI, (double*)nhi);
   else
     refresh_nhi_pair_kernel<<<grid, block, 0, st>>>(ncell, nH, xHI, (float2*)nhi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_state(long long n, const double* nH, const double* x, unsigned long long* bad,
+                               cudaStream_t st) {
+  const int block = 256, grid = grid_for(n, block);
+  check_state_kernel<<<grid, block, 0, st>>>(n, nH, x, bad);
   return cudaGetLastError();
 }
 

@@ -107,6 +107,18 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(native.RtError):
         native.rt_create_grid(ctx, (4, 4, 4), g["box_len_cm"], g["n_H"], bad)
     grid = native.Grid(ctx, g)
+    before = grid.rates()["x_HI"]
+    for arr, name in ((np.where(np.arange(64) == 17, -0.25, g["x_HI"]), "x_HI[17]"),
+                      (np.where(np.arange(64) == 5, np.nan, g["x_HI"]), "x_HI[5]")):
+        with pytest.raises(native.RtError) as e:
+            native.rt_set_state(grid.h, arr)
+        assert e.value.code == native.RT_ERR_INVALID_ARG and name in str(e.value)
+    n_bad = g["n_H"].copy()
+    n_bad[40] = np.inf
+    with pytest.raises(native.RtError) as e:
+        native.rt_set_state(grid.h, g["x_HI"], n_H=n_bad)
+    assert "n_H[40]" in str(e.value)
+    np.testing.assert_array_equal(grid.rates()["x_HI"], before)  # a rejected state changes nothing
     with pytest.raises(native.RtError):
         native.rt_add_sources(grid.h, [[-1.0, 0, 0]], [1e48], [13.6], [6.3e-18])
     with pytest.raises(native.RtError):
