@@ -687,6 +687,10 @@ static int copy_field(rt_grid* g, const void* src, int src_dtype, void* dst, int
     LAUNCH_TRY(launch_convert(n, src, src_dtype, dst, dtype, st));
     return RT_OK;
   }
+  if (src_dtype == dtype) {  // same type: straight to the host
+    CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)n * eb, cudaMemcpyDeviceToHost, st));
+    return RT_OK;
+  }
   void* tmp = nullptr;
   CUDA_TRY(cudaMallocAsync(&tmp, (size_t)n * eb, st));
   cudaError_t e = launch_convert(n, src, src_dtype, tmp, dtype, st);
