@@ -45,6 +45,11 @@
  *   R8 Pixel directions use an exact quadrant reduction of the azimuth so that
  *      components that vanish are exactly 0 and mirror-symmetric pixels give
  *      mirror-symmetric vectors.
+ *  R13 Covering factor (Sec. 2.3, optional): R_0 in L_pix = R_0 theta_pix is
+ *      the radius where the segment starts; theta_pix = sqrt(Omega_pix) of a
+ *      square pixel; f_c is capped at 1 ("pixel fully contained") and is 1 at
+ *      r = 0; it scales every k_ph / Gamma contribution of the segment,
+ *      including the residual absorbed at termination (R3), never dP.
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC (no FMA
  * contraction, so the rounding of every expression is the one written here).
@@ -347,6 +352,27 @@ static int orc_push(orc_stack *st, orc_pkg p) {
   return 0;
 }
 
+/* Eq. "fc" (Sec. 2.3): the covering factor of a segment, reading R13.  The
+ * pixel is taken as a square of width L_pix = r theta_pix (theta_pix =
+ * sqrt(4 pi / N_pix), r the radius where the segment starts) centred on the
+ * segment's midpoint; D_edge is the distance from the midpoint to the
+ * nearest face of the cell along the three axes, dx/2 - max_i D_c,i (Eq.
+ * "midpoint"); f_c = (1/2 + D_edge / L_pix)^2, and 1 where the pixel fits in
+ * the cell (f_c > 1) or has no width (r = 0).  Cell units throughout. */
+static double orc_fc(const double s[3], const double n[3], double r, double dr, const int64_t c[3],
+                     double theta_pix) {
+  const double L = r * theta_pix;
+  if (!(L > 0)) return 1.0;
+  double dmax = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const double mid = s[i] + n[i] * (r + 0.5 * dr);
+    const double d = fabs(mid - ((double)c[i] + 0.5));
+    if (d > dmax) dmax = d;
+  }
+  const double f = 0.5 + (0.5 - dmax) / L;
+  return f * f < 1.0 ? f * f : 1.0;
+}
+
 /*
  * orc_trace: one radiative-transfer pass over a uniform grid.
  *   dims        nx, ny, nz (cells); cell index = i + nx*(j + ny*k)
@@ -362,13 +388,15 @@ static int orc_push(orc_stack *st, orc_pkg p) {
  *   counts[ORC_MAX_LEVEL+1]   packages created per level
  *   hashes[ORC_MAX_LEVEL+1]   checksum of the created (src, level, pixel) set
  *   segments     number of segments with dr > 0
+ *   fc           nonzero: scale the k_ph and Gamma contributions by the
+ *                covering factor of Eq. "fc" (photon budget unchanged)
  * returns 0, or -1 on a bad argument or allocation failure.
  */
 int orc_trace(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, int nsrc,
               const double *pos_cm, const double *ndot, const double *e_ph_eV,
               const double *sigma_cm2, int level0, double phi_c, double f_term, int max_level,
               double *kph, double *gamma, double *budget, uint64_t *counts, uint64_t *hashes,
-              uint64_t *segments) {
+              uint64_t *segments, int fc) {
   if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0 || level0 < 0 || max_level > ORC_MAX_LEVEL ||
       level0 > max_level || !(phi_c > 0) || !(f_term > 0 && f_term < 1))
     return -1;
@@ -437,7 +465,9 @@ int orc_trace(const int dims[3], double box_len_cm, const double *n_H, const dou
         const double absorbed_frac = -expm1(-dtau);         /* 1 - e^-tau */
         const double dP = pk.P * absorbed_frac;
         const double phi = (dtau > 0) ? absorbed_frac / dtau : 1.0;
-        const double k_add = pk.P * sigma_cm2[pk.src] * (dr * dx) * phi / vol;
+        const double f_c = fc ? orc_fc(s, n, pk.r, dr, c, sqrt(4.0 * M_PI / (12.0 * ldexp(1.0, 2 * (int)pk.level))))
+                              : 1.0;
+        const double k_add = pk.P * sigma_cm2[pk.src] * (dr * dx) * phi / vol * f_c;
         kph[idx] += k_add;
         gamma[idx] += k_add * heat;
         if (dr > 0) ++nseg;
@@ -447,7 +477,7 @@ int orc_trace(const int dims[3], double box_len_cm, const double *n_H, const dou
         orc_kadd(&absorbed, dP);
         /* Step 3i (reading R3): absorb the residual in this cell */
         if (pk.tau > tau_term) {
-          const double k_res = pk.P / (n_abs[idx] * vol);
+          const double k_res = pk.P / (n_abs[idx] * vol) * f_c;
           kph[idx] += k_res;
           gamma[idx] += k_res * heat;
           orc_kadd(&absorbed, pk.P);
