@@ -180,11 +180,11 @@ def run_native(args, rank, world, local):
     x0 = torch.tensor(g["x_HI"], dtype=torch.float64, device=dev)
     z0 = torch.tensor(g["x_HII"], dtype=torch.float64, device=dev)
 
-    def measure(precision):
+    def measure(precision, **extra):
         grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
-        b = grid.trace(**params)  # sizes the queue
+        b = grid.trace(**params, **extra)  # sizes the queue
         cap = max(1 << 20, int(b["queue_pushed"] * 1.5))
-        qp = dict(params, queue_capacity=cap)
+        qp = dict(params, queue_capacity=cap, **extra)
         seg_per_step = b["segments"]
         pushed = b["queue_pushed"]
         for _ in range(max(3, args.warmup)):
@@ -295,6 +295,12 @@ def run_native(args, rank, world, local):
         out[f"{prec}_path"] = {"value": q["segments"] * world / (sum(q["step_ms"]) / 1e3),
                                "ms_per_step": sum(q["step_ms"]) / args.steps,
                                "kernel_ms": sum(q["kern_ms"]) / args.steps}
+    # the same step with the covering-factor correction of Sec. 2.3 (optional)
+    if not args.no_fc:
+        q = measure(head, fc=True)
+        out["fc_path"] = {"value": q["segments"] / (sum(q["step_ms"]) / 1e3),
+                          "ms_per_step": sum(q["step_ms"]) / args.steps,
+                          "kernel_ms": sum(q["kern_ms"]) / args.steps, "precision": head}
     # the batched and serving configurations are measured on one GPU
     if not args.no_batched and world == 1:
         out["batched"] = batched(args, ctx, stream, dev, world)
@@ -462,6 +468,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-fc", action="store_true", help="skip the covering-factor (Sec. 2.3) leg")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-fp64-budget-s", type=float, default=90.0)
     ap.add_argument("--grid", type=int, default=128, help="cells per side (128 = the benchmark workload)")

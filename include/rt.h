@@ -83,11 +83,21 @@ typedef struct {
   int blocks_per_sm;     /* resident 256-thread blocks of the trace kernel per SM;
                             0 = as many as fit (lower it to share the GPU) */
   int segs_per_iter;     /* segments a lane traces between queue visits; 0 = tuned */
-  int flags;             /* RT_TRACE_CHECKSUMS: also fill rt_budget.hashes */
+  int flags;             /* RT_TRACE_CHECKSUMS: also fill rt_budget.hashes;
+                            RT_TRACE_FC: covering-factor correction */
   int passes;            /* launches over equal ranges of the sources (>= 0);
                             0 = 1, or as many as the automatic sizing needs */
 } rt_trace_params;
 #define RT_TRACE_CHECKSUMS 1
+/* Geometric correction (Sec. 2.3, Eqs. "midpoint", "fc"): each segment's
+ * k_ph and Gamma contribution is scaled by f_c = (1/2 + D_edge / L_pix)^2,
+ * capped at 1, with L_pix = r theta_pix the width of the package's pixel
+ * (taken as a square, theta_pix = sqrt(4 pi / N_pix), r the radius where the
+ * segment starts; f_c = 1 at r = 0) and D_edge the distance from the
+ * segment's midpoint to the nearest face of the cell along the axes.  dP,
+ * the photon budget and every decision are unchanged; k_ph is no longer
+ * photon conserving (as the paper notes). */
+#define RT_TRACE_FC 2
 
 /* Result of a trace, per grid. */
 typedef struct {

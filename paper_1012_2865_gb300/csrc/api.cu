@@ -439,6 +439,11 @@ static void fill_common_args(TraceArgs& A, const rt_trace_params* p) {
   A.timeout_ns = (long long)((p->timeout_s > 0 ? p->timeout_s : 2.0) * 1e9);
   A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 8;
   A.checksums = (p->flags & RT_TRACE_CHECKSUMS) != 0;
+  A.fc = (p->flags & RT_TRACE_FC) != 0;
+  for (int l = 0; l < kLevels; ++l) {
+    A.theta[l] = sqrt(4.0 * M_PI / (12.0 * ldexp(1.0, 2 * l)));
+    A.theta32[l] = (float)A.theta[l];
+  }
 }
 
 // One trace as `passes` launches of the trace kernel over consecutive, equal

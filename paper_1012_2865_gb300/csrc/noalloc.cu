@@ -231,6 +231,11 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
     A.segs_per_iter = p->segs_per_iter > 0 ? p->segs_per_iter : 8;
     A.max_steps = 2 * (g->nx + g->ny + g->nz) + 16;
     A.checksums = (p->flags & RT_TRACE_CHECKSUMS) != 0;
+    A.fc = (p->flags & RT_TRACE_FC) != 0;
+    for (int l = 0; l < kLevels; ++l) {
+      A.theta[l] = sqrt(4.0 * M_PI / (12.0 * ldexp(1.0, 2 * l)));
+      A.theta32[l] = (float)A.theta[l];
+    }
     int per_sm = 0;
     if ((e = trace_occupancy(RT_FP32_MIXED, 256, &per_sm)) != cudaSuccess) return na_fail(RT_ERR_CUDA, "occupancy", e);
     if (per_sm < 1) per_sm = 1;

@@ -111,6 +111,9 @@ struct TraceArgs {
   int segs_per_iter;
   int max_steps;  // bound on segments of one package (guards the DDA loop)
   int checksums;  // accumulate the created-set checksum
+  int fc;         // scale k_ph and Gamma deposits by the covering factor (Eq. "fc")
+  double theta[kLevels];    // pixel width sqrt(4 pi / N_pix(l)) in radians
+  float theta32[kLevels];
 };
 
 // 64-bit finaliser used for the created-package checksum (documented in rt.h).
