@@ -143,6 +143,11 @@ int rt_grid_destroy(rt_grid* grid);
 int rt_add_sources(rt_grid* grid, int n, const double* pos_cm, const double* ndot,
                    const double* e_ph_eV, const double* sigma_cm2);
 int rt_clear_sources(rt_grid* grid);
+/* Index of the grid's first source in the created-set checksum (default 0):
+ * a grid that holds sources [first, first + n) of a larger set (one shard of
+ * a source-partitioned trace) then contributes the same checksum terms as
+ * the whole set traced in one grid.  first + number of sources <= 2^23. */
+int rt_set_source_offset(rt_grid* grid, int first);
 
 /* One radiative-transfer pass, Steps 1-5: zero k_ph and Gamma, emit
  * 12*4^level0 packages per source, trace every package through the grid
@@ -181,6 +186,12 @@ int rt_set_state(rt_grid* grid, const double* n_H, const double* x_HI, const dou
 int rt_get_rates(rt_grid* grid, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind);
 /* Copy x_HII likewise. */
 int rt_get_ionised(rt_grid* grid, void* x_HII, int dtype, int mem_kind);
+/* Overwrite k_ph and Gamma (the quantities rt_get_rates returns) with the
+ * caller's arrays of element type dtype in memory mem_kind, converted to the
+ * grid's precision: for a trace partitioned by sources over several grids or
+ * devices, the sum of the partial rates is installed before rt_chem_update.
+ * Synchronous for host arrays, stream-ordered for device arrays. */
+int rt_set_rates(rt_grid* grid, const void* kph, const void* gamma, int dtype, int mem_kind);
 
 /* ---------------------------------------------------------------------------
  * Batches: many grids traced by one persistent launch that shares one

@@ -60,7 +60,7 @@ def _load():
             lib.orc_ang2pix_nest.restype = u64
             lib.orc_ray_path.argtypes = [p, p, p, d, i, p, p, p]
             lib.orc_ray_path.restype = i
-            lib.orc_trace.argtypes = [p, d, p, p, i, p, p, p, p, i, d, d, i, p, p, p, p, p, p, i]
+            lib.orc_trace.argtypes = [p, d, p, p, i, p, p, p, p, i, d, d, i, p, p, p, p, p, p, i, i]
             lib.orc_trace.restype = i
             lib.orc_chem.argtypes = [ctypes.c_size_t, p, p, p, p, d, i, d]
             lib.orc_chem.restype = None
@@ -129,7 +129,7 @@ def ray_path(dims, s, n, r0: float = 0.0, max_out: int = 100000):
 
 def trace(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, *,
           level0: int = 1, phi_c: float = 5.1, f_term: float = 1e-10,
-          max_level: int = MAX_LEVEL, fc: bool = False) -> dict:
+          max_level: int = MAX_LEVEL, fc: bool = False, src_offset: int = 0) -> dict:
     """One radiative-transfer pass (Steps 1-5).  Cell index = i + nx*(j + ny*k).
 
     Returns dict(kph, gamma (per cell, s^-1 and erg/s), budget=[emitted,
@@ -156,7 +156,7 @@ def trace(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, 
     rc = lib.orc_trace(_ptr(dims), float(box_len_cm), _ptr(n_H), _ptr(x_HI), int(nsrc), _ptr(pos),
                        _ptr(ndot), _ptr(e), _ptr(sg), int(level0), float(phi_c), float(f_term),
                        int(max_level), _ptr(kph), _ptr(gamma), _ptr(budget), _ptr(counts),
-                       _ptr(hashes), _ptr(seg), 1 if fc else 0)
+                       _ptr(hashes), _ptr(seg), 1 if fc else 0, int(src_offset))
     if rc != 0:
         raise ValueError("oracle trace rejected its arguments")
     return dict(kph=kph, gamma=gamma, budget=budget, counts=counts, hashes=hashes,

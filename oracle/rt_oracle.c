@@ -390,13 +390,15 @@ static double orc_fc(const double s[3], const double n[3], double r, double dr, 
  *   segments     number of segments with dr > 0
  *   fc           nonzero: scale the k_ph and Gamma contributions by the
  *                covering factor of Eq. "fc" (photon budget unchanged)
+ *   src_offset   index of the first source in the checksum (a shard of a
+ *                larger source list hashes its sources as the whole list does)
  * returns 0, or -1 on a bad argument or allocation failure.
  */
 int orc_trace(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, int nsrc,
               const double *pos_cm, const double *ndot, const double *e_ph_eV,
               const double *sigma_cm2, int level0, double phi_c, double f_term, int max_level,
               double *kph, double *gamma, double *budget, uint64_t *counts, uint64_t *hashes,
-              uint64_t *segments, int fc) {
+              uint64_t *segments, int fc, int src_offset) {
   if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0 || level0 < 0 || max_level > ORC_MAX_LEVEL ||
       level0 > max_level || !(phi_c > 0) || !(f_term > 0 && f_term < 1))
     return -1;
@@ -432,7 +434,7 @@ int orc_trace(const int dims[3], double box_len_cm, const double *n_H, const dou
       if (orc_push(&st, pk)) { free(st.v); free(n_abs); return -1; }
       orc_kadd(&emitted, P0);
       counts[level0] += 1;
-      hashes[level0] += orc_pkg_hash((uint32_t)src, (uint32_t)level0, npix0 - 1 - p);
+      hashes[level0] += orc_pkg_hash((uint32_t)(src + src_offset), (uint32_t)level0, npix0 - 1 - p);
     }
     /* Steps 3-5: trace until every package is split, absorbed or gone */
     while (st.n > 0) {
@@ -453,7 +455,7 @@ int orc_trace(const int dims[3], double box_len_cm, const double *n_H, const dou
             orc_pkg ch = {pk.src, pk.level + 1, 4 * pk.pix + (uint64_t)kk, pk.r, pk.P / 4.0, pk.tau};
             if (orc_push(&st, ch)) { free(st.v); free(n_abs); return -1; }
             counts[pk.level + 1] += 1;
-            hashes[pk.level + 1] += orc_pkg_hash(pk.src, pk.level + 1, 4 * pk.pix + (uint64_t)kk);
+            hashes[pk.level + 1] += orc_pkg_hash(pk.src + (uint32_t)src_offset, pk.level + 1, 4 * pk.pix + (uint64_t)kk);
           }
           break;
         }

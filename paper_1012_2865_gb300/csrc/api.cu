@@ -135,6 +135,7 @@ struct rt_grid {
   size_t src_dev_cap = 0;
   bool src_dirty = true;
   int last_level0 = -1;
+  int src_offset = 0;                  // index of the first source in checksums
   TraceState ts;
   // pinned readback buffer
   void* host_rb = nullptr;
@@ -313,7 +314,8 @@ int rt_add_sources(rt_grid* g, int n, const double* pos, const double* ndot, con
     if (!(e_ph[i] >= kEHI) || !isfinite(e_ph[i])) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: e_ph_eV[%d] = %g < 13.6", i, e_ph[i]);
     if (!(sigma[i] >= 0) || !isfinite(sigma[i])) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: sigma[%d] = %g", i, sigma[i]);
   }
-  if (g->src.size() + (size_t)n > (1u << 23)) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: too many sources");
+  if ((size_t)g->src_offset + g->src.size() + (size_t)n > (1u << 23))
+    return fail(RT_ERR_INVALID_ARG, "rt_add_sources: too many sources");
   for (int i = 0; i < n; ++i) {
     rt_grid::SrcIn S;
     for (int a = 0; a < 3; ++a) S.pos[a] = pos[3 * i + a];
@@ -322,6 +324,15 @@ int rt_add_sources(rt_grid* g, int n, const double* pos, const double* ndot, con
     S.sigma = sigma[i];
     g->src.push_back(S);
   }
+  g->src_dirty = true;
+  return RT_OK;
+}
+
+int rt_set_source_offset(rt_grid* g, int first) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_set_source_offset: grid is NULL");
+  if (first < 0 || (size_t)first + g->src.size() > (1u << 23))
+    return fail(RT_ERR_INVALID_ARG, "rt_set_source_offset: first = %d", first);
+  g->src_offset = first;
   g->src_dirty = true;
   return RT_OK;
 }
@@ -355,7 +366,7 @@ static void build_sources(const rt_grid* g, int level0, int inst, std::vector<So
     S.w = S.unit * H.sigma / (dx * dx);
     S.rw = S.unit / vol;
     S.inst = inst;
-    S.local = (int)i;
+    S.local = g->src_offset + (int)i;
     int exact = 1;
     float s32[3], slo[3], sab[3];
     for (int a = 0; a < 3; ++a) {
@@ -720,6 +731,35 @@ int rt_get_rates(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype, int 
   if ((rc = copy_field(g, g->G, kd, gamma, dtype, mem_kind))) return rc;
   if ((rc = copy_field(g, g->xHI, RT_DTYPE_F64, x_HI, dtype, mem_kind))) return rc;
   CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return RT_OK;
+}
+
+int rt_set_rates(rt_grid* g, const void* kph, const void* gamma, int dtype, int mem_kind) {
+  if (!g || !kph || !gamma) return fail(RT_ERR_INVALID_ARG, "rt_set_rates: grid, kph and gamma are required");
+  if (int rcw = wait_batch(g)) return rcw;
+  if (dtype != RT_DTYPE_F64 && dtype != RT_DTYPE_F32) return fail(RT_ERR_INVALID_ARG, "rt_set_rates: dtype %d", dtype);
+  if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE) return fail(RT_ERR_INVALID_ARG, "rt_set_rates: mem_kind %d", mem_kind);
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  const long long n = g->ncell;
+  const size_t eb = dtype == RT_DTYPE_F64 ? 8 : 4;
+  const int kd = g->precision == RT_FP64 ? RT_DTYPE_F64 : RT_DTYPE_F32;
+  cudaStream_t st = g->stream;
+  const void* src[2] = {kph, gamma};
+  void* dst[2] = {g->K, g->G};
+  for (int f = 0; f < 2; ++f) {
+    if (mem_kind == RT_MEM_DEVICE) {
+      LAUNCH_TRY(launch_convert(n, src[f], dtype, dst[f], kd, st));
+      continue;
+    }
+    void* tmp = nullptr;
+    CUDA_TRY(cudaMallocAsync(&tmp, (size_t)n * eb, st));
+    cudaError_t e = cudaMemcpyAsync(tmp, src[f], (size_t)n * eb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_convert(n, tmp, dtype, dst[f], kd, st);
+    if (e == cudaSuccess) g_launches.fetch_add(1);
+    cudaFreeAsync(tmp, st);
+    if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_set_rates: %s", cudaGetErrorString(e));
+  }
+  if (mem_kind == RT_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
   return RT_OK;
 }
 

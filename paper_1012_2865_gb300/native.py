@@ -99,6 +99,8 @@ def lib():
             "rt_get_rates": ([vp, vp, vp, vp, i, i], i),
             "rt_set_state": ([vp, vp, vp, vp, i], i),
             "rt_get_ionised": ([vp, vp, i, i], i),
+            "rt_set_rates": ([vp, vp, vp, i, i], i),
+            "rt_set_source_offset": ([vp, i], i),
             "rt_synchronize": ([vp], i),
             "rt_selfcheck_directions": ([vp, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
             "rt_kernel_launches": ([], ctypes.c_uint64),
@@ -234,6 +236,24 @@ def rt_set_state(grid, x_HI, x_HII=None, n_H=None):
     pz, kz, kz_ = _buf(x_HII)
     pn, kn, kn_ = _buf(n_H)
     check(lib().rt_set_state(grid, pn, px, pz, kx))
+
+
+def rt_set_source_offset(grid, first: int):
+    check(lib().rt_set_source_offset(grid, int(first)))
+
+
+def rt_set_rates(grid, kph, gamma):
+    """Install k_ph and Gamma: host arrays (sent as FP64) or CUDA tensors of
+    one dtype (float32 or float64)."""
+    dev = type(kph).__module__.startswith("torch") and kph.is_cuda
+    if dev:
+        assert kph.dtype == gamma.dtype and gamma.is_cuda
+        dt = RT_DTYPE_F64 if str(kph.dtype) == "torch.float64" else RT_DTYPE_F32
+    else:
+        dt = RT_DTYPE_F64
+    pk, kk, keep_k = _buf(kph)
+    pg, kg, keep_g = _buf(gamma)
+    check(lib().rt_set_rates(grid, pk, pg, dt, kk))
 
 
 def rt_chem_update(grid, dt_s, nsub, alpha_B):

@@ -1,0 +1,77 @@
+"""One grid traced by several ranks, each holding a share of its sources.
+
+The trace is linear in the sources: k_ph, Gamma, the photon budget, the
+packages created per level (and their checksum) and the segment count of the
+whole source list are the sums over any partition of it.  So each rank keeps
+the full medium, traces its contiguous range of the sources (with that
+range's global source numbering, for the checksum), and the ranks sum the
+rates and the budget (one all-reduce each); every rank then holds the rates
+of the whole trace and runs the same ionisation update, so the ranks' states
+stay identical.  The exchange is the only communication per step.
+
+`shard_trace` runs one rank's share and returns its partial results;
+`install` writes the summed rates back into the grid.  The all-reduce itself
+is the caller's (`torch.distributed.all_reduce` between ranks).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import native
+
+BUDGET_KEYS = ("emitted", "absorbed", "escaped")
+
+
+def source_range(nsrc: int, rank: int, world: int) -> tuple:
+    """Contiguous share [s0, s1) of nsrc sources for `rank` of `world`."""
+    if not (0 <= rank < world):
+        raise ValueError("rank outside [0, world)")
+    return nsrc * rank // world, nsrc * (rank + 1) // world
+
+
+def shard_of(g: dict, rank: int, world: int) -> tuple:
+    """The grid description restricted to this rank's sources, and s0."""
+    s0, s1 = source_range(len(g["ndot"]), rank, world)
+    sub = dict(g)
+    for k in ("pos_cm", "ndot", "e_ph_eV", "sigma_cm2"):
+        sub[k] = np.asarray(g[k])[s0:s1]
+    return sub, s0
+
+
+def budget_vector(b: dict) -> tuple:
+    """(FP64 sums, int64 counters) of a budget, in a fixed order for an
+    all-reduce; the checksums wrap modulo 2^64 as int64 sums do."""
+    f = np.array([b[k] for k in BUDGET_KEYS], dtype=np.float64)
+    i = np.concatenate([np.asarray(b["counts"], dtype=np.uint64), np.asarray(b["hashes"], dtype=np.uint64),
+                        np.array([b["segments"]], dtype=np.uint64)]).view(np.int64)
+    return f, i
+
+
+def budget_from_vector(f, i) -> dict:
+    u = np.asarray(i, dtype=np.int64).view(np.uint64)
+    n = (len(u) - 1) // 2
+    out = {k: float(v) for k, v in zip(BUDGET_KEYS, np.asarray(f, dtype=np.float64))}
+    out.update(counts=u[:n].copy(), hashes=u[n:2 * n].copy(), segments=int(u[2 * n]))
+    return out
+
+
+def shard_trace(ctx, g: dict, precision: str, rank: int, world: int, where: str = "device", **params):
+    """Trace this rank's sources on a grid holding the whole medium.
+
+    Returns (grid, budget, kph, gamma): the partial budget and rates, the
+    rates as CUDA tensors (where='device') or numpy arrays in the grid's
+    precision."""
+    sub, s0 = shard_of(g, rank, world)
+    grid = native.Grid(ctx, dict(sub, ndot=[]), precision)  # sources added below, after the offset
+    native.rt_set_source_offset(grid.h, s0)
+    if len(sub["ndot"]):
+        native.rt_add_sources(grid.h, sub["pos_cm"], sub["ndot"], sub["e_ph_eV"], sub["sigma_cm2"])
+    b = grid.trace(**params)
+    dt = native.RT_DTYPE_F64 if precision == "fp64" else native.RT_DTYPE_F32
+    r = native.rt_get_rates(grid.h, grid.ncell, dt, where)
+    return grid, b, r["kph"], r["gamma"]
+
+
+def install(grid, kph, gamma):
+    """Write the summed rates into the grid (before rt_chem_update)."""
+    native.rt_set_rates(grid.h, kph, gamma)

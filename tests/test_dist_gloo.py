@@ -51,3 +51,64 @@ def test_replicas_report_slowest_time_and_total_work():
 def test_single_process_is_unchanged():
     import bench
     assert bench.reduce_over_ranks(1.25, 7) == (1.25, 7)
+
+
+def _shard_rank(rank, world, port, q):
+    """One rank of a source-partitioned trace, the oracle standing in for the
+    GPU tracer: trace the rank's sources, all-reduce rates and budget."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import numpy as np
+    import oracle
+    from paper_1012_2865_gb300 import shard, synth
+    g = synth.clumpy(N=20, nsrc=7, seed=21)
+    sub, s0 = shard.shard_of(g, rank, world)
+    o = oracle.trace(sub["dims"], sub["box_len_cm"], sub["n_H"], sub["x_HI"], sub["pos_cm"], sub["ndot"],
+                     sub["e_ph_eV"], sub["sigma_cm2"], src_offset=s0, **synth.DEFAULT_PARAMS)
+    k = torch.from_numpy(o["kph"].copy())
+    gm = torch.from_numpy(o["gamma"].copy())
+    f, i = shard.budget_vector(dict(emitted=o["budget"][0], absorbed=o["budget"][1], escaped=o["budget"][2],
+                                    counts=o["counts"], hashes=o["hashes"], segments=o["segments"]))
+    ft, it = torch.from_numpy(f), torch.from_numpy(i)
+    for t in (k, gm, ft, it):
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    q.put((rank, k.numpy(), gm.numpy(), shard.budget_from_vector(ft.numpy(), it.numpy()), len(sub["ndot"])))
+    dist.destroy_process_group()
+
+
+def test_source_partitioned_trace_sums_to_the_whole():
+    import numpy as np
+    import oracle
+    from paper_1012_2865_gb300 import synth
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=300) for _ in range(world)), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    g = synth.clumpy(N=20, nsrc=7, seed=21)
+    full = oracle.trace(g["dims"], g["box_len_cm"], g["n_H"], g["x_HI"], g["pos_cm"], g["ndot"], g["e_ph_eV"],
+                        g["sigma_cm2"], **synth.DEFAULT_PARAMS)
+    assert sum(t[4] for t in out) == 7 and all(t[4] > 0 for t in out)
+    for _, k, gm, b, _ in out:  # every rank holds the whole trace's results
+        np.testing.assert_array_equal(b["counts"], full["counts"])
+        np.testing.assert_array_equal(b["hashes"], full["hashes"])
+        assert b["segments"] == full["segments"]
+        for j, key in enumerate(("emitted", "absorbed", "escaped")):
+            assert abs(b[key] - full["budget"][j]) <= 1e-12 * full["budget"][0]
+        np.testing.assert_allclose(k, full["kph"], rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(gm, full["gamma"], rtol=1e-12, atol=1e-300)
+
+
+def test_source_ranges_partition_the_list():
+    from paper_1012_2865_gb300 import shard
+    for nsrc in (0, 1, 7, 1000):
+        for world in (1, 2, 3, 8):
+            got = [shard.source_range(nsrc, r, world) for r in range(world)]
+            assert got[0][0] == 0 and got[-1][1] == nsrc
+            assert all(a[1] == b[0] for a, b in zip(got, got[1:]))
+            assert max(b - a for a, b in got) - min(b - a for a, b in got) <= 1
