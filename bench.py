@@ -301,6 +301,23 @@ def run_native(args, rank, world, local):
         out["fc_path"] = {"value": q["segments"] / (sum(q["step_ms"]) / 1e3),
                           "ms_per_step": sum(q["step_ms"]) / args.steps,
                           "kernel_ms": sum(q["kern_ms"]) / args.steps, "precision": head}
+    # the adaptive RT timestep of Sec. 3.4 on the same state (one synchronous call)
+    if not args.no_timestep:
+        grid = native.Grid(ctx, g, head, stream=stream.cuda_stream)
+        grid.trace(**params)
+        t = []
+        for i in range(8):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dt_p = native.rt_timestep(grid.h, eps_ion=0.05, dt_max=DT_S)
+            t.append(time.perf_counter() - t0)
+        grid.close()
+        cells = int(np.prod(g["dims"]))
+        ms = 1e3 * float(np.median(t[3:]))
+        # per cell: n_H, x_HI (FP64), k_ph read, the per-cell value written and read back
+        out["timestep"] = {"ms": ms, "dt_s": dt_p, "cells": cells,
+                           "gb_s": cells * (8 + 8 + (8 if head == "fp64" else 4) + 4 + 4) / (ms / 1e3) / 1e9}
     # the batched and serving configurations are measured on one GPU
     if not args.no_batched and world == 1:
         out["batched"] = batched(args, ctx, stream, dev, world)
@@ -469,6 +486,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-fc", action="store_true", help="skip the covering-factor (Sec. 2.3) leg")
+    ap.add_argument("--no-timestep", action="store_true", help="skip the adaptive-timestep (Sec. 3.4) leg")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-fp64-budget-s", type=float, default=90.0)
     ap.add_argument("--grid", type=int, default=128, help="cells per side (128 = the benchmark workload)")

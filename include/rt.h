@@ -186,6 +186,19 @@ int rt_set_state(rt_grid* grid, const double* n_H, const double* x_HI, const dou
 int rt_get_rates(rt_grid* grid, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind);
 /* Copy x_HII likewise. */
 int rt_get_ionised(rt_grid* grid, void* x_HII, int dtype, int mem_kind);
+/* Adaptive radiative-transfer timestep (Sec. 3.4, Eqs. "dtelec",
+ * "dtchange") from the grid's current k_ph and state: per cell
+ * eps_ion / |k_ph + n_e alpha_B| (n_e = n_H (1 - x_HI), C_H = 0) in cells
+ * "within the ionisation front", whose optical depth sigma_front n_HI dx
+ * exceeds tau_front (the paper uses 0.5), dt_max elsewhere and at most
+ * dt_max; smoothed by a 3x3x3 Gaussian of one cell width (weights
+ * exp(-|d|^2/2), renormalised over the neighbours inside the grid); *dt_out
+ * = the minimum over the grid, capped at 2 dt_prev when dt_prev > 0.
+ * Computed in FP32 (relative error ~1e-6).  dt_max may be +inf.
+ * Synchronous. */
+int rt_timestep(rt_grid* grid, double eps_ion, double alpha_B, double sigma_front, double tau_front, double dt_max,
+                double dt_prev, double* dt_out);
+
 /* Overwrite k_ph and Gamma (the quantities rt_get_rates returns) with the
  * caller's arrays of element type dtype in memory mem_kind, converted to the
  * grid's precision: for a trace partitioned by sources over several grids or

@@ -35,7 +35,7 @@ def cell_timestep(n_H, x_HI, kph, dx_cm, eps_ion, alpha_B, sigma_front, tau_fron
     rate = np.abs(k + n_e * alpha_B)
     with np.errstate(divide="ignore"):
         dt = np.where(rate > 0, eps_ion / np.where(rate > 0, rate, 1.0), np.inf)
-    front = sigma_front * n_H * x * dx_cm > tau_front
+    front = (sigma_front * dx_cm) * n_H * x > tau_front
     return np.minimum(np.where(front, dt, dt_max), dt_max)
 
 

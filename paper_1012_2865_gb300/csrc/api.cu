@@ -26,6 +26,9 @@ cudaError_t launch_refresh(int precision, long long ncell, const double* nH, con
 cudaError_t launch_convert(long long n, const void* src, int src_dtype, void* dst, int dst_dtype,
                            cudaStream_t st);
 cudaError_t launch_complement(long long n, const double* x, double* out, cudaStream_t st);
+cudaError_t launch_timestep(long long n, int nx, int ny, int nz, const double* nH, const double* xHI, const void* K,
+                            int fp64_rates, double sdx, double tau_front, float eps, float alpha, float dt_max,
+                            float unit, float* dtc, unsigned int* out, cudaStream_t st);
 cudaError_t launch_check_state(long long n, const double* nH, const double* x, unsigned long long* bad,
                                cudaStream_t st);
 cudaError_t launch_direction_check(int level, unsigned long long* out, cudaStream_t st);
@@ -760,6 +763,42 @@ int rt_set_rates(rt_grid* g, const void* kph, const void* gamma, int dtype, int 
     if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_set_rates: %s", cudaGetErrorString(e));
   }
   if (mem_kind == RT_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+  return RT_OK;
+}
+
+int rt_timestep(rt_grid* g, double eps_ion, double alpha_B, double sigma_front, double tau_front, double dt_max,
+                double dt_prev, double* dt_out) {
+  if (!g || !dt_out) return fail(RT_ERR_INVALID_ARG, "rt_timestep: grid and dt_out are required");
+  if (!(eps_ion > 0) || !isfinite(eps_ion) || !(alpha_B >= 0) || !isfinite(alpha_B) || !(sigma_front >= 0) ||
+      !isfinite(sigma_front) || !(tau_front >= 0) || !(dt_max > 0) || !(dt_prev >= 0))
+    return fail(RT_ERR_INVALID_ARG, "rt_timestep: bad parameter");
+  if (int rcw = wait_batch(g)) return rcw;
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  cudaStream_t st = g->stream;
+  const long long n = g->ncell;
+  char* scratch = nullptr;
+  CUDA_TRY(cudaMallocAsync((void**)&scratch, (size_t)n * sizeof(float) + 256, st));
+  unsigned int* out = (unsigned int*)(scratch + (((size_t)n * sizeof(float) + 255) & ~(size_t)255));
+  unsigned int* h = (unsigned int*)((char*)g->host_rb + 3072);
+  *h = 0x7f800000u;  // +inf
+  cudaError_t e = cudaMemcpyAsync(out, h, sizeof *h, cudaMemcpyHostToDevice, st);
+  // finite dt_max: values in units of dt_max (cells outside the front hold 1)
+  const bool finite = isfinite(dt_max) && dt_max < 3.0e38;
+  const float dmax = finite ? (float)dt_max : 3.0e38f;
+  if (e == cudaSuccess)
+    e = launch_timestep(n, g->nx, g->ny, g->nz, g->nH, g->xHI, g->K, g->precision == RT_FP64,
+                        sigma_front * g->dx, tau_front, (float)eps_ion, (float)alpha_B, dmax, finite ? dmax : 1.0f,
+                        (float*)scratch, out, st);
+  if (e == cudaSuccess) g_launches.fetch_add(2);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, sizeof *h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_timestep: %s", cudaGetErrorString(e));
+  float v;
+  memcpy(&v, h, sizeof v);
+  double dt = finite ? (v >= 1.0f ? dt_max : (double)v * dt_max) : (v >= 3.0e38f ? dt_max : (double)v);
+  if (dt_prev > 0 && 2.0 * dt_prev < dt) dt = 2.0 * dt_prev;  // Eq. "dtchange"
+  *dt_out = dt;
   return RT_OK;
 }
 

@@ -168,6 +168,77 @@ __global__ void check_state_kernel(long long n, const double* __restrict__ nH, c
   }
 }
 
+// Adaptive RT timestep (Sec. 3.4), step 1, Eq. "dtelec": per cell
+// eps / |k_ph + n_e alpha_B| (C_H = 0, n_e = n_H (1 - x_HI)) where the cell's
+// optical depth sdx n_HI exceeds tau_front, else dt_max; never above dt_max.
+// The front test is FP64 (a cell's side of the threshold must not depend on
+// rounding); the value is FP32 (a timestep needs no more), in units of
+// dt_max when dt_max is finite (so cells outside the front hold exactly 1).
+template <typename KT>
+__global__ void cell_timestep_kernel(long long n, const double* __restrict__ nH, const double* __restrict__ xHI,
+                                     const KT* __restrict__ K, double sdx, double tau_front, float eps, float alpha,
+                                     float dt_max, float unit, float* __restrict__ dtc) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const double nh64 = nH[c], x64 = xHI[c];
+    const float nh = (float)nh64, x = (float)x64;
+    const float rate = fabsf((float)K[c] + nh * (1.0f - x) * alpha);
+    float dt = dt_max;
+    if (sdx * nh64 * x64 > tau_front && rate > 0.0f) dt = fminf(dt_max, eps / rate);
+    dtc[c] = dt == dt_max ? dt_max / unit : dt / unit;
+  }
+}
+
+// Steps 2-3: the 3^3 Gaussian (exp(-|d|^2/2), renormalised over neighbours
+// inside the grid) of the per-cell timestep, and its minimum over the grid
+// (atomicMin on the bit patterns, which order like the positive floats).
+__global__ void smooth_min_kernel(const float* __restrict__ dtc, int nx, int ny, int nz, unsigned int* __restrict__ out) {
+  const float w1 = 0.60653066f, w2 = 0.36787944f, w3 = 0.22313016f;  // e^-1/2, e^-1, e^-3/2
+  const long long n = (long long)nx * ny * nz;
+  float best = __int_as_float(0x7f800000);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    float acc = 0.0f, ws = 0.0f;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int kk = k + dz;
+      if (kk < 0 || kk >= nz) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int jj = j + dy;
+        if (jj < 0 || jj >= ny) continue;
+        for (int dxo = -1; dxo <= 1; ++dxo) {
+          const int ii = i + dxo;
+          if (ii < 0 || ii >= nx) continue;
+          const int d2 = dxo * dxo + dy * dy + dz * dz;
+          const float w = d2 == 0 ? 1.0f : (d2 == 1 ? w1 : (d2 == 2 ? w2 : w3));
+          acc = fmaf(w, dtc[ii + (long long)nx * (jj + (long long)ny * kk)], acc);
+          ws += w;
+        }
+      }
+    }
+    best = fminf(best, acc / ws);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMin(out, __float_as_uint(best));
+}
+
+cudaError_t launch_timestep(long long n, int nx, int ny, int nz, const double* nH, const double* xHI, const void* K,
+                            int fp64_rates, double sdx, double tau_front, float eps, float alpha, float dt_max,
+                            float unit, float* dtc, unsigned int* out, cudaStream_t st) {
+  const int block = 256;
+  long long g = (n + block - 1) / block;
+  if (g > 152 * 8) g = 152 * 8;
+  if (g < 1) g = 1;
+  if (fp64_rates)
+    cell_timestep_kernel<double><<<(int)g, block, 0, st>>>(n, nH, xHI, (const double*)K, sdx, tau_front, eps, alpha,
+                                                          dt_max, unit, dtc);
+  else
+    cell_timestep_kernel<float><<<(int)g, block, 0, st>>>(n, nH, xHI, (const float*)K, sdx, tau_front, eps, alpha,
+                                                         dt_max, unit, dtc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  smooth_min_kernel<<<(int)g, block, 0, st>>>(dtc, nx, ny, nz, out);
+  return cudaGetLastError();
+}
+
 // h alpha_B and h as FP32 pairs (host side), for the mixed update kernels
 static float4 step_pairs(double h, double alpha) {
   const double ha = h * alpha;

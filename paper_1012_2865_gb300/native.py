@@ -100,6 +100,7 @@ def lib():
             "rt_set_state": ([vp, vp, vp, vp, i], i),
             "rt_get_ionised": ([vp, vp, i, i], i),
             "rt_set_rates": ([vp, vp, vp, i, i], i),
+            "rt_timestep": ([vp, d, d, d, d, d, d, ctypes.POINTER(d)], i),
             "rt_set_source_offset": ([vp, i], i),
             "rt_synchronize": ([vp], i),
             "rt_selfcheck_directions": ([vp, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
@@ -254,6 +255,14 @@ def rt_set_rates(grid, kph, gamma):
     pk, kk, keep_k = _buf(kph)
     pg, kg, keep_g = _buf(gamma)
     check(lib().rt_set_rates(grid, pk, pg, dt, kk))
+
+
+def rt_timestep(grid, eps_ion=0.05, alpha_B=2.59e-13, sigma_front=6.3e-18, tau_front=0.5, dt_max=float("inf"),
+                dt_prev=0.0) -> float:
+    out = ctypes.c_double()
+    check(lib().rt_timestep(grid, float(eps_ion), float(alpha_B), float(sigma_front), float(tau_front),
+                            float(dt_max), float(dt_prev), ctypes.byref(out)))
+    return out.value
 
 
 def rt_chem_update(grid, dt_s, nsub, alpha_B):
