@@ -36,7 +36,7 @@
 namespace rtg {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kShInst = 16;  // grids whose level counters are kept in shared memory
+constexpr int kShInst = 64;  // grids whose budget and level counters a block keeps in shared memory
 constexpr int kBlock = 256;  // threads per block of the trace kernel
 
 enum Event { EV_NONE = 0, EV_SPLIT = 1, EV_DONE = 2 };
@@ -50,8 +50,26 @@ struct LaneAcc {
   int inst;
 };
 
-__device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A) {
-  if (a.inst >= 0) {
+// A block's budget sums per grid, in shared memory, for the first kShInst
+// grids of the launch: a lane that moves to a package of another grid adds
+// its sums here (shared atomics) instead of into global memory, and the
+// block flushes the table once at the end.
+struct BlockBudget {
+  double* sums;             // [kShInst][3]: emitted, absorbed, escaped
+  unsigned long long* segs; // [kShInst]
+  unsigned int* fb;         // [kShInst][2]: fallbacks, fallbacks_tau
+};
+
+__device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A, const BlockBudget& bb) {
+  if (a.inst >= 0 && a.inst < kShInst) {
+    double* t = bb.sums + 3 * a.inst;
+    if (a.emitted != 0.0) atomicAdd(&t[0], a.emitted);
+    if (a.absorbed != 0.0) atomicAdd(&t[1], a.absorbed);
+    if (a.escaped != 0.0) atomicAdd(&t[2], a.escaped);
+    if (a.segments) atomicAdd(&bb.segs[a.inst], a.segments);
+    if (a.fallbacks) atomicAdd(&bb.fb[2 * a.inst], a.fallbacks);
+    if (a.fallbacks_tau) atomicAdd(&bb.fb[2 * a.inst + 1], a.fallbacks_tau);
+  } else if (a.inst >= 0) {
     const InstDev& I = A.inst[a.inst];
     if (a.emitted != 0.0) atomicAdd(&I.acc[0], a.emitted);
     if (a.absorbed != 0.0) atomicAdd(&I.acc[1], a.absorbed);
@@ -68,11 +86,12 @@ __device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A) {
 
 // Switch the lane's budget to grid `inst`, flushing the previous grid's sums
 // (with the segments counted since the last switch).
-__device__ __forceinline__ void acc_switch(LaneAcc& a, unsigned& nseg, int inst, const TraceArgs& A) {
+__device__ __forceinline__ void acc_switch(LaneAcc& a, unsigned& nseg, int inst, const TraceArgs& A,
+                                           const BlockBudget& bb) {
   if (a.inst != inst) {
     a.segments += nseg;
     nseg = 0;
-    acc_flush(a, A);
+    acc_flush(a, A, bb);
     a.inst = inst;
   }
 }
@@ -703,10 +722,17 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   __shared__ unsigned int sh_cnt[kShInst * kLevels];
   __shared__ unsigned long long sh_hsh[kShInst * kLevels];
   __shared__ LaneAcc sh_acc[kBlock];
+  __shared__ double sh_bsum[kShInst * 3];
+  __shared__ unsigned long long sh_bseg[kShInst];
+  __shared__ unsigned int sh_bfb[kShInst * 2];
   for (int i = threadIdx.x; i < kShInst * kLevels; i += blockDim.x) {
     sh_cnt[i] = 0;
     sh_hsh[i] = 0;
   }
+  for (int i = threadIdx.x; i < kShInst * 3; i += blockDim.x) sh_bsum[i] = 0.0;
+  for (int i = threadIdx.x; i < kShInst * 2; i += blockDim.x) sh_bfb[i] = 0u;
+  for (int i = threadIdx.x; i < kShInst; i += blockDim.x) sh_bseg[i] = 0ULL;
+  const BlockBudget BB{sh_bsum, sh_bseg, sh_bfb};
   LaneAcc& acc = sh_acc[threadIdx.x];
   acc.emitted = acc.absorbed = acc.escaped = 0.0;
   acc.segments = acc.fallbacks = acc.fallbacks_tau = 0;
@@ -749,7 +775,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         w.load(W::root_rec(gsrc, (uint32_t)A.level0, p));
         got = true;
         const SourceDev& S = A.src[gsrc];
-        acc_switch(acc, w.nseg, S.inst, A);
+        acc_switch(acc, w.nseg, S.inst, A, BB);
         acc.emitted += S.unit;
         LC.add(A, S.inst, S.local, A.level0, p, 1);
       } else {
@@ -765,7 +791,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
       if (got) {
         ticket = -1;
         active = true;
-        acc_switch(acc, w.nseg, w.inst(A), A);
+        acc_switch(acc, w.nseg, w.inst(A), A, BB);
         if (!w.start(A)) {
           w.on_start_outside(A, acc);
           ev = EV_DONE;
@@ -860,9 +886,9 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
     }
   }
   acc.segments += w.nseg;
-  // The lanes' budget sums: where every lane of the block last worked on the
-  // same grid (or on none), reduce them in shared memory and flush once per
-  // block, instead of 256 atomics per word onto the same few addresses.
+  // Where every lane of the block last worked on the same grid (or on none),
+  // reduce the lanes' sums in shared memory first: 256 atomics onto one
+  // word would serialise.
   __shared__ int sh_inst;
   if (threadIdx.x == 0) sh_inst = -1;
   __syncthreads();
@@ -871,7 +897,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   if (__syncthreads_and(acc.inst < 0 || acc.inst == sh_inst)) {
     for (int h = kBlock / 2; h > 0; h >>= 1) {
       if (threadIdx.x < h) {
-        LaneAcc& o = sh_acc[threadIdx.x + h];
+        const LaneAcc& o = sh_acc[threadIdx.x + h];
         acc.emitted += o.emitted;
         acc.absorbed += o.absorbed;
         acc.escaped += o.escaped;
@@ -883,12 +909,21 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
     }
     if (threadIdx.x == 0) {
       acc.inst = sh_inst;
-      acc_flush(acc, A);
+      acc_flush(acc, A, BB);
     }
   } else {
-    acc_flush(acc, A);
+    acc_flush(acc, A, BB);
   }
   __syncthreads();
+  for (int i = threadIdx.x; i < kShInst && i < A.ninst; i += blockDim.x) {
+    const InstDev& I = A.inst[i];
+    if (sh_bsum[3 * i] != 0.0) atomicAdd(&I.acc[0], sh_bsum[3 * i]);
+    if (sh_bsum[3 * i + 1] != 0.0) atomicAdd(&I.acc[1], sh_bsum[3 * i + 1]);
+    if (sh_bsum[3 * i + 2] != 0.0) atomicAdd(&I.acc[2], sh_bsum[3 * i + 2]);
+    if (sh_bseg[i]) atomicAdd(&I.cnt[kCntSegments], sh_bseg[i]);
+    if (sh_bfb[2 * i]) atomicAdd(&I.cnt[kCntFallbacks], (unsigned long long)sh_bfb[2 * i]);
+    if (sh_bfb[2 * i + 1]) atomicAdd(&I.cnt[kCntFallbacksTau], (unsigned long long)sh_bfb[2 * i + 1]);
+  }
   for (int i = threadIdx.x; i < kShInst * kLevels; i += blockDim.x) {
     const int inst = i / kLevels, l = i - inst * kLevels;
     if (inst < A.ninst && sh_cnt[i]) {
