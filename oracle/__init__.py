@@ -15,6 +15,9 @@ contraction); this module only builds it and marshals numpy arrays:
   Gamma per cell (Eqs. "dtau", "flux", "kph", "gamma"), the photon budget,
   packages created per HEALPix level and a checksum of the created set.
 * ``chem`` -- backward-Euler update of Eq. "dndt" (hydrogen only).
+* ``Flight`` / ``trace(..., flight=, light_cm=)`` -- finite speed of light
+  (Sec. 2.1, Step 3j): packages halt after travelling c dt_P in a trace and
+  continue in the next one.
 """
 from __future__ import annotations
 
@@ -62,6 +65,9 @@ def _load():
             lib.orc_ray_path.restype = i
             lib.orc_trace.argtypes = [p, d, p, p, i, p, p, p, p, i, d, d, i, p, p, p, p, p, p, i, i]
             lib.orc_trace.restype = i
+            lib.orc_trace_fsl.argtypes = [p, d, p, p, i, p, p, p, p, i, d, d, i, p, p, p, p, p, p, i, i,
+                                          i, p, ctypes.c_size_t, p, ctypes.c_size_t, p, p]
+            lib.orc_trace_fsl.restype = i
             lib.orc_chem.argtypes = [ctypes.c_size_t, p, p, p, p, d, i, d]
             lib.orc_chem.restype = None
             _lib = lib
@@ -127,13 +133,54 @@ def ray_path(dims, s, n, r0: float = 0.0, max_out: int = 100000):
     return cells[:k].copy(), dr[:k].copy(), r[:k].copy()
 
 
+# A package kept between traces (finite speed of light): the layout of
+# orc_flight in rt_oracle.c.  r in cell units, P in photons/s, cell = the
+# cell it halted in, age = its index into the next trace's halting radii.
+FLIGHT_DTYPE = np.dtype([("src", "<u4"), ("level", "<u4"), ("pix", "<u8"), ("r", "<f8"), ("P", "<f8"),
+                         ("tau", "<f8"), ("cell", "<i8", (3,)), ("age", "<u4"), ("pad", "<u4")])
+
+
+class Flight:
+    """Packages of one grid in flight between traces, and the halting radii.
+
+    Sec. 2.1 (first halting condition) and Step 3j: a package travels c dt_P
+    per radiative-transfer timestep and is then saved and continued in the
+    next step, through the medium of that step.  Ages count the traces since
+    a package's lineage was emitted; in a trace whose light travel is
+    c dt_P (cell units) a package of age a halts at
+        rlim[0] = c dt_P,   rlim[a] = rlim_previous[a - 1] + c dt_P,
+    the distance light has travelled since its emission (reading R15).
+    """
+
+    def __init__(self):
+        self.rlim = np.zeros(0)
+        self.packages = np.zeros(0, dtype=FLIGHT_DTYPE)
+
+    def advance(self, c_dt_cells: float) -> np.ndarray:
+        """Halting radii of the next trace (one more age than before)."""
+        prev = self.rlim
+        new = np.empty(prev.size + 1)
+        new[0] = c_dt_cells
+        for a in range(1, new.size):
+            new[a] = prev[a - 1] + c_dt_cells
+        self.rlim = new
+        return new
+
+
 def trace(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, *,
           level0: int = 1, phi_c: float = 5.1, f_term: float = 1e-10,
-          max_level: int = MAX_LEVEL, fc: bool = False, src_offset: int = 0) -> dict:
+          max_level: int = MAX_LEVEL, fc: bool = False, src_offset: int = 0,
+          flight: Flight = None, light_cm: float = 0.0) -> dict:
     """One radiative-transfer pass (Steps 1-5).  Cell index = i + nx*(j + ny*k).
 
     Returns dict(kph, gamma (per cell, s^-1 and erg/s), budget=[emitted,
     absorbed, escaped] (photons/s), counts[15], hashes[15], segments).
+
+    With ``flight`` and ``light_cm`` = c dt_P > 0 (finite speed of light),
+    the packages in ``flight`` continue alongside the sources' new packages,
+    every package halts where it has travelled c dt_P since its emission, and ``flight`` afterwards holds the halted packages; the result
+    adds ``resumed`` and ``halted`` (photons/s) and ``n_halted``.  With
+    ``light_cm`` = 0 any packages in ``flight`` are dropped.
     """
     lib = _load()
     dims = np.ascontiguousarray(dims, dtype=np.int32)
@@ -149,18 +196,39 @@ def trace(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, 
     assert pos.size == 3 * nsrc and e.size == nsrc and sg.size == nsrc
     kph = np.empty(ncell)
     gamma = np.empty(ncell)
-    budget = np.empty(3)
+    budget = np.empty(5)
     counts = np.zeros(MAX_LEVEL + 1, dtype=np.uint64)
     hashes = np.zeros(MAX_LEVEL + 1, dtype=np.uint64)
     seg = np.zeros(1, dtype=np.uint64)
-    rc = lib.orc_trace(_ptr(dims), float(box_len_cm), _ptr(n_H), _ptr(x_HI), int(nsrc), _ptr(pos),
-                       _ptr(ndot), _ptr(e), _ptr(sg), int(level0), float(phi_c), float(f_term),
-                       int(max_level), _ptr(kph), _ptr(gamma), _ptr(budget), _ptr(counts),
-                       _ptr(hashes), _ptr(seg), 1 if fc else 0, int(src_offset))
+    finite = flight is not None and light_cm > 0
+    if flight is not None and not finite:
+        flight.rlim = np.zeros(0)
+        flight.packages = np.zeros(0, dtype=FLIGHT_DTYPE)
+    rlim = np.ascontiguousarray(flight.advance(float(light_cm) / (float(box_len_cm) / int(dims[0])))) \
+        if finite else np.zeros(1)
+    pin = np.ascontiguousarray(flight.packages if finite else np.zeros(0, dtype=FLIGHT_DTYPE))
+    cap = max(1024, 4 * pin.size)
+    n_out = ctypes.c_size_t(0)
+    while True:
+        out = np.zeros(cap, dtype=FLIGHT_DTYPE)
+        rc = lib.orc_trace_fsl(_ptr(dims), float(box_len_cm), _ptr(n_H), _ptr(x_HI), int(nsrc), _ptr(pos),
+                               _ptr(ndot), _ptr(e), _ptr(sg), int(level0), float(phi_c), float(f_term),
+                               int(max_level), _ptr(kph), _ptr(gamma), _ptr(budget), _ptr(counts),
+                               _ptr(hashes), _ptr(seg), 1 if fc else 0, int(src_offset),
+                               int(rlim.size) if finite else 0, _ptr(rlim), ctypes.c_size_t(pin.size),
+                               _ptr(pin), ctypes.c_size_t(cap), _ptr(out), ctypes.byref(n_out))
+        if rc == -2:
+            cap = int(n_out.value)
+            continue
+        break
     if rc != 0:
         raise ValueError("oracle trace rejected its arguments")
-    return dict(kph=kph, gamma=gamma, budget=budget, counts=counts, hashes=hashes,
-                segments=int(seg[0]))
+    res = dict(kph=kph, gamma=gamma, budget=budget[:3].copy(), counts=counts, hashes=hashes,
+               segments=int(seg[0]))
+    if finite:
+        flight.packages = out[:n_out.value].copy()
+        res.update(resumed=float(budget[3]), halted=float(budget[4]), n_halted=int(n_out.value))
+    return res
 
 
 def chem(n_H, x_HI, x_HII, kph, dt_s: float, nsub: int, alpha_B: float):

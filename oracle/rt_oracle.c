@@ -50,6 +50,17 @@
  *      square pixel; f_c is capped at 1 ("pixel fully contained") and is 1 at
  *      r = 0; it scales every k_ph / Gamma contribution of the segment,
  *      including the residual absorbed at termination (R3), never dP.
+ *  R15 Finite speed of light (Sec. 2.1 halting condition 1, Step 3j,
+ *      optional): a package may travel c dt_P per trace beyond the radius
+ *      at which its lineage entered the trace, so a package emitted a traces
+ *      ago halts at rlim[a] = c dt_P summed over the a + 1 traces since its
+ *      emission (same FP64 sum on both sides: rlim'[0] = c dt_P,
+ *      rlim'[a] = rlim[a - 1] + c dt_P).  The test follows the split test and
+ *      uses the crossing radius of the cell: when r_next > rlim the segment
+ *      ends at rlim, is absorbed as usual (termination is checked first),
+ *      and the package is kept with its cell; the next trace continues it
+ *      from that radius and cell through the then current medium.  Children
+ *      inherit the age.  Emitted + resumed = absorbed + escaped + halted.
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC (no FMA
  * contraction, so the rounding of every expression is the one written here).
@@ -333,7 +344,21 @@ typedef struct {
   double r;   /* distance travelled, cell units */
   double P;   /* photons per second carried */
   double tau; /* optical depth accumulated by the package and its ancestors */
+  uint32_t age;     /* traces since the lineage was emitted (R15) */
+  int has_cell;     /* resumed package: continue in cell[] (R15) */
+  int64_t cell[3];
 } orc_pkg;
+
+/* A package halted by the finite speed of light (R15), as kept between
+ * traces: its state, the cell it halted in, and its age in the next trace. */
+typedef struct {
+  uint32_t src, level;
+  uint64_t pix;
+  double r, P, tau;
+  int64_t cell[3];
+  uint32_t age;
+  uint32_t pad;
+} orc_flight;
 
 typedef struct {
   orc_pkg *v;
@@ -373,130 +398,246 @@ static double orc_fc(const double s[3], const double n[3], double r, double dr, 
   return f * f < 1.0 ? f * f : 1.0;
 }
 
+/* Everything one trace needs while it walks packages. */
+typedef struct {
+  const int *dims;
+  const double *n_abs;     /* n_H x_HI per cell */
+  double dx, vol, tau_term;
+  const double *rsplit;
+  int max_level, fc, src_offset;
+  const double *s;         /* source positions, cell units, 3 per source */
+  const double *sigma_cm2;
+  const double *heat;      /* (E_ph - 13.6 eV) in erg per source */
+  int n_ages;              /* 0: infinite speed of light */
+  const double *rlim;      /* halting radius per age (R15), cell units */
+  double *kph, *gamma;
+  uint64_t *counts, *hashes, nseg;
+  orc_ksum absorbed, escaped, halted;
+  orc_flight *out;
+  size_t out_cap, n_out;
+} orc_run;
+
+/* Steps 3a-3k for every package on the stack and its descendants, until each
+ * is split, absorbed, gone or halted.  Returns -1 on an allocation failure or
+ * a package whose age has no halting radius. */
+static int orc_walk(orc_run *R, orc_stack *st) {
+  const int *dims = R->dims;
+  while (st->n > 0) {
+    orc_pkg pk = st->v[--st->n];
+    const double *s = R->s + 3 * pk.src;
+    const double sigma_dx = R->sigma_cm2[pk.src] * R->dx;
+    double rlim = INFINITY;
+    if (R->n_ages > 0) {
+      if (pk.age >= (uint32_t)R->n_ages) return -1;
+      rlim = R->rlim[pk.age];
+    }
+    double n[3];
+    orc_pix2vec_nest((int)pk.level, pk.pix, n); /* Step 3a */
+    int64_t c[3];
+    if (pk.has_cell) { c[0] = pk.cell[0]; c[1] = pk.cell[1]; c[2] = pk.cell[2]; }
+    else orc_locate(s, n, pk.r, c); /* Step 3b */
+    for (;;) {
+      if (!orc_inside(c, dims)) { /* Step 3k, isolated boundaries */
+        orc_kadd(&R->escaped, pk.P);
+        break;
+      }
+      double t[3];
+      double rnext = orc_next_crossing(s, n, c, t); /* Step 3d */
+      if ((int)pk.level < R->max_level && rnext > R->rsplit[pk.level]) { /* Step 3e */
+        for (int kk = 3; kk >= 0; --kk) {
+          orc_pkg ch = {pk.src, pk.level + 1, 4 * pk.pix + (uint64_t)kk, pk.r, pk.P / 4.0, pk.tau,
+                        pk.age, 0, {0, 0, 0}};
+          if (orc_push(st, ch)) return -1;
+          R->counts[pk.level + 1] += 1;
+          R->hashes[pk.level + 1] +=
+              orc_pkg_hash(pk.src + (uint32_t)R->src_offset, pk.level + 1, 4 * pk.pix + (uint64_t)kk);
+        }
+        break;
+      }
+      /* Step 3j (reading R15): the segment ends where the package has
+       * travelled c dt_P since its lineage's emission */
+      double rend = rnext;
+      int halt = 0;
+      if (rnext > rlim) { rend = rlim; halt = 1; }
+      double dr = rend - pk.r;
+      if (dr < 0) dr = 0;
+      const size_t idx = (size_t)c[0] + (size_t)dims[0] * ((size_t)c[1] + (size_t)dims[1] * (size_t)c[2]);
+      /* Step 3f: Eqs. "dtau", "flux", "kph" (reading R5), "gamma" */
+      const double dtau = sigma_dx * R->n_abs[idx] * dr;
+      const double absorbed_frac = -expm1(-dtau);         /* 1 - e^-tau */
+      const double dP = pk.P * absorbed_frac;
+      const double phi = (dtau > 0) ? absorbed_frac / dtau : 1.0;
+      const double f_c =
+          R->fc ? orc_fc(s, n, pk.r, dr, c, sqrt(4.0 * M_PI / (12.0 * ldexp(1.0, 2 * (int)pk.level)))) : 1.0;
+      const double k_add = pk.P * R->sigma_cm2[pk.src] * (dr * R->dx) * phi / R->vol * f_c;
+      R->kph[idx] += k_add;
+      R->gamma[idx] += k_add * R->heat[pk.src];
+      if (dr > 0) ++R->nseg;
+      /* Step 3h */
+      pk.P -= dP;
+      pk.tau += dtau;
+      orc_kadd(&R->absorbed, dP);
+      /* Step 3i (reading R3): absorb the residual in this cell */
+      if (pk.tau > R->tau_term) {
+        const double k_res = pk.P / (R->n_abs[idx] * R->vol) * f_c;
+        R->kph[idx] += k_res;
+        R->gamma[idx] += k_res * R->heat[pk.src];
+        orc_kadd(&R->absorbed, pk.P);
+        break;
+      }
+      if (halt) { /* Step 3j: keep the package for the next trace */
+        if (R->n_out < R->out_cap) {
+          orc_flight f = {pk.src, pk.level, pk.pix, rend, pk.P, pk.tau, {c[0], c[1], c[2]}, pk.age + 1, 0};
+          R->out[R->n_out] = f;
+        }
+        R->n_out++;
+        orc_kadd(&R->halted, pk.P);
+        break;
+      }
+      orc_advance(n, t, rnext, c);
+      pk.r = rnext;
+    }
+  }
+  return 0;
+}
+
 /*
- * orc_trace: one radiative-transfer pass over a uniform grid.
+ * orc_trace_fsl: one radiative-transfer pass over a uniform grid.
  *   dims        nx, ny, nz (cells); cell index = i + nx*(j + ny*k)
  *   box_len_cm  length of the x extent; cell width dx = box_len_cm / nx
  *   n_H, x_HI   hydrogen density (cm^-3) and neutral fraction per cell
  *   nsrc, pos_cm[3*nsrc], ndot[nsrc] (photons/s), e_ph_eV[nsrc],
  *   sigma_cm2[nsrc]
  *   level0, phi_c, f_term, max_level   method parameters (Sec. 2.1)
- * outputs (overwritten):
- *   kph[ncell]   photo-ionisation rate per absorber, s^-1 (Eq. "kph")
- *   gamma[ncell] photo-heating rate per absorber, erg/s (Eq. "gamma")
- *   budget[3]    emitted, absorbed, escaped photons/s (Neumaier sums)
- *   counts[ORC_MAX_LEVEL+1]   packages created per level
- *   hashes[ORC_MAX_LEVEL+1]   checksum of the created (src, level, pixel) set
- *   segments     number of segments with dr > 0
  *   fc           nonzero: scale the k_ph and Gamma contributions by the
  *                covering factor of Eq. "fc" (photon budget unchanged)
  *   src_offset   index of the first source in the checksum (a shard of a
  *                larger source list hashes its sources as the whole list does)
- * returns 0, or -1 on a bad argument or allocation failure.
+ *   n_ages, rlim[n_ages]   halting radius per age in cell units (R15);
+ *                n_ages = 0: infinite speed of light
+ *   n_in, in[n_in]         packages halted by the previous trace, resumed
+ *                          here (photons/s as they were emitted)
+ *   out_cap, out           room for the packages this trace halts
+ * outputs (overwritten):
+ *   kph[ncell]   photo-ionisation rate per absorber, s^-1 (Eq. "kph")
+ *   gamma[ncell] photo-heating rate per absorber, erg/s (Eq. "gamma")
+ *   budget[5]    emitted, absorbed, escaped, resumed, halted photons/s
+ *                (Neumaier sums)
+ *   counts[ORC_MAX_LEVEL+1]   packages created per level
+ *   hashes[ORC_MAX_LEVEL+1]   checksum of the created (src, level, pixel) set
+ *   segments     number of segments with dr > 0
+ *   n_out        packages halted (when above out_cap, only out_cap stored)
+ * returns 0; -1 on a bad argument or allocation failure; -2 when out_cap
+ * was too small (*n_out then says how many are needed).
  */
-int orc_trace(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, int nsrc,
-              const double *pos_cm, const double *ndot, const double *e_ph_eV,
-              const double *sigma_cm2, int level0, double phi_c, double f_term, int max_level,
-              double *kph, double *gamma, double *budget, uint64_t *counts, uint64_t *hashes,
-              uint64_t *segments, int fc, int src_offset) {
+int orc_trace_fsl(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, int nsrc,
+                  const double *pos_cm, const double *ndot, const double *e_ph_eV, const double *sigma_cm2,
+                  int level0, double phi_c, double f_term, int max_level, double *kph, double *gamma,
+                  double *budget, uint64_t *counts, uint64_t *hashes, uint64_t *segments, int fc, int src_offset,
+                  int n_ages, const double *rlim, size_t n_in, const orc_flight *in, size_t out_cap,
+                  orc_flight *out, size_t *n_out) {
   if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0 || level0 < 0 || max_level > ORC_MAX_LEVEL ||
-      level0 > max_level || !(phi_c > 0) || !(f_term > 0 && f_term < 1))
+      level0 > max_level || !(phi_c > 0) || !(f_term > 0 && f_term < 1) || n_ages < 0 ||
+      (n_ages == 0 && n_in > 0))
     return -1;
+  for (size_t i = 0; i < n_in; ++i)
+    if (in[i].src >= (uint32_t)nsrc || in[i].age >= (uint32_t)n_ages || in[i].level > (uint32_t)max_level)
+      return -1;
   const size_t ncell = (size_t)dims[0] * dims[1] * dims[2];
-  const double dx = box_len_cm / dims[0];
-  const double vol = dx * dx * dx;
-  const double tau_term = -log(f_term); /* reading R3 */
   double rsplit[ORC_MAX_LEVEL + 1];
   for (int l = 0; l <= ORC_MAX_LEVEL; ++l) /* Eq. "split": Phi < Phi_c <=> R > R_split */
     rsplit[l] = sqrt((12.0 * ldexp(1.0, 2 * l)) / (4.0 * M_PI * phi_c));
 
   double *n_abs = (double *)malloc(ncell * sizeof(double));
-  if (!n_abs) return -1;
+  double *s = (double *)malloc((size_t)(nsrc > 0 ? nsrc : 1) * 3 * sizeof(double));
+  double *heat = (double *)malloc((size_t)(nsrc > 0 ? nsrc : 1) * sizeof(double));
+  if (!n_abs || !s || !heat) { free(n_abs); free(s); free(heat); return -1; }
   for (size_t c = 0; c < ncell; ++c) n_abs[c] = n_H[c] * x_HI[c];
+  orc_run R;
+  memset(&R, 0, sizeof R);
+  R.dims = dims;
+  R.n_abs = n_abs;
+  R.dx = box_len_cm / dims[0];
+  R.vol = R.dx * R.dx * R.dx;
+  R.tau_term = -log(f_term); /* reading R3 */
+  R.rsplit = rsplit;
+  R.max_level = max_level;
+  R.fc = fc;
+  R.src_offset = src_offset;
+  for (int i = 0; i < nsrc; ++i) {
+    for (int a = 0; a < 3; ++a) s[3 * i + a] = pos_cm[3 * i + a] / R.dx;
+    heat[i] = (e_ph_eV[i] - ORC_E_HI) * ORC_EV_ERG;
+  }
+  R.s = s;
+  R.sigma_cm2 = sigma_cm2;
+  R.heat = heat;
+  R.n_ages = n_ages;
+  R.rlim = rlim;
+  R.kph = kph;
+  R.gamma = gamma;
+  R.counts = counts;
+  R.hashes = hashes;
+  R.out = out;
+  R.out_cap = out_cap;
 
   /* Step 2: zero the radiation fields */
   for (size_t c = 0; c < ncell; ++c) { kph[c] = 0.0; gamma[c] = 0.0; }
   for (int l = 0; l <= ORC_MAX_LEVEL; ++l) { counts[l] = 0; hashes[l] = 0; }
-  orc_ksum emitted = {0, 0}, absorbed = {0, 0}, escaped = {0, 0};
-  uint64_t nseg = 0;
+  orc_ksum emitted = {0, 0}, resumed = {0, 0};
 
   orc_stack st = {NULL, 0, 0};
+  int rc = 0;
   const uint64_t npix0 = 12ULL << (2 * level0);
-  for (int src = 0; src < nsrc; ++src) {
-    double s[3];
-    for (int i = 0; i < 3; ++i) s[i] = pos_cm[3 * src + i] / dx;
-    const double sigma_dx = sigma_cm2[src] * dx;
-    const double heat = (e_ph_eV[src] - ORC_E_HI) * ORC_EV_ERG;
+  for (int src = 0; src < nsrc && rc == 0; ++src) {
     /* Step 1: N_pix packages on the initial level, luminosity spread equally */
     const double P0 = ndot[src] / (double)npix0;
     for (uint64_t p = 0; p < npix0; ++p) {
-      orc_pkg pk = {(uint32_t)src, (uint32_t)level0, npix0 - 1 - p, 0.0, P0, 0.0};
-      if (orc_push(&st, pk)) { free(st.v); free(n_abs); return -1; }
+      orc_pkg pk = {(uint32_t)src, (uint32_t)level0, npix0 - 1 - p, 0.0, P0, 0.0, 0, 0, {0, 0, 0}};
+      if (orc_push(&st, pk)) { rc = -1; break; }
       orc_kadd(&emitted, P0);
       counts[level0] += 1;
       hashes[level0] += orc_pkg_hash((uint32_t)(src + src_offset), (uint32_t)level0, npix0 - 1 - p);
     }
-    /* Steps 3-5: trace until every package is split, absorbed or gone */
-    while (st.n > 0) {
-      orc_pkg pk = st.v[--st.n];
-      double n[3];
-      orc_pix2vec_nest((int)pk.level, pk.pix, n); /* Step 3a */
-      int64_t c[3];
-      orc_locate(s, n, pk.r, c); /* Step 3b */
-      for (;;) {
-        if (!orc_inside(c, dims)) { /* Step 3k, isolated boundaries */
-          orc_kadd(&escaped, pk.P);
-          break;
-        }
-        double t[3];
-        double rnext = orc_next_crossing(s, n, c, t); /* Step 3d */
-        if ((int)pk.level < max_level && rnext > rsplit[pk.level]) { /* Step 3e */
-          for (int kk = 3; kk >= 0; --kk) {
-            orc_pkg ch = {pk.src, pk.level + 1, 4 * pk.pix + (uint64_t)kk, pk.r, pk.P / 4.0, pk.tau};
-            if (orc_push(&st, ch)) { free(st.v); free(n_abs); return -1; }
-            counts[pk.level + 1] += 1;
-            hashes[pk.level + 1] += orc_pkg_hash(pk.src + (uint32_t)src_offset, pk.level + 1, 4 * pk.pix + (uint64_t)kk);
-          }
-          break;
-        }
-        double dr = rnext - pk.r;
-        if (dr < 0) dr = 0;
-        const size_t idx = (size_t)c[0] + (size_t)dims[0] * ((size_t)c[1] + (size_t)dims[1] * (size_t)c[2]);
-        /* Step 3f: Eqs. "dtau", "flux", "kph" (reading R5), "gamma" */
-        const double dtau = sigma_dx * n_abs[idx] * dr;
-        const double absorbed_frac = -expm1(-dtau);         /* 1 - e^-tau */
-        const double dP = pk.P * absorbed_frac;
-        const double phi = (dtau > 0) ? absorbed_frac / dtau : 1.0;
-        const double f_c = fc ? orc_fc(s, n, pk.r, dr, c, sqrt(4.0 * M_PI / (12.0 * ldexp(1.0, 2 * (int)pk.level))))
-                              : 1.0;
-        const double k_add = pk.P * sigma_cm2[pk.src] * (dr * dx) * phi / vol * f_c;
-        kph[idx] += k_add;
-        gamma[idx] += k_add * heat;
-        if (dr > 0) ++nseg;
-        /* Step 3h */
-        pk.P -= dP;
-        pk.tau += dtau;
-        orc_kadd(&absorbed, dP);
-        /* Step 3i (reading R3): absorb the residual in this cell */
-        if (pk.tau > tau_term) {
-          const double k_res = pk.P / (n_abs[idx] * vol) * f_c;
-          kph[idx] += k_res;
-          gamma[idx] += k_res * heat;
-          orc_kadd(&absorbed, pk.P);
-          break;
-        }
-        orc_advance(n, t, rnext, c);
-        pk.r = rnext;
-      }
-    }
+    /* Steps 3-5: trace until every package is split, absorbed, gone or halted */
+    if (rc == 0) rc = orc_walk(&R, &st);
+  }
+  /* packages halted by the previous trace continue (R15) */
+  for (size_t i = 0; i < n_in && rc == 0; ++i) {
+    orc_pkg pk = {in[i].src, in[i].level, in[i].pix, in[i].r, in[i].P, in[i].tau, in[i].age, 1,
+                  {in[i].cell[0], in[i].cell[1], in[i].cell[2]}};
+    if (orc_push(&st, pk)) { rc = -1; break; }
+    orc_kadd(&resumed, in[i].P);
+    rc = orc_walk(&R, &st);
   }
   free(st.v);
   free(n_abs);
+  free(s);
+  free(heat);
+  if (rc) return rc;
   budget[0] = orc_kval(&emitted);
-  budget[1] = orc_kval(&absorbed);
-  budget[2] = orc_kval(&escaped);
-  *segments = nseg;
-  return 0;
+  budget[1] = orc_kval(&R.absorbed);
+  budget[2] = orc_kval(&R.escaped);
+  budget[3] = orc_kval(&resumed);
+  budget[4] = orc_kval(&R.halted);
+  *segments = R.nseg;
+  *n_out = R.n_out;
+  return R.n_out > out_cap ? -2 : 0;
+}
+
+/* orc_trace: the same pass with an infinite speed of light (budget[3]:
+ * emitted, absorbed, escaped). */
+int orc_trace(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, int nsrc,
+              const double *pos_cm, const double *ndot, const double *e_ph_eV,
+              const double *sigma_cm2, int level0, double phi_c, double f_term, int max_level,
+              double *kph, double *gamma, double *budget, uint64_t *counts, uint64_t *hashes,
+              uint64_t *segments, int fc, int src_offset) {
+  double b5[5];
+  size_t n_out = 0;
+  const int rc = orc_trace_fsl(dims, box_len_cm, n_H, x_HI, nsrc, pos_cm, ndot, e_ph_eV, sigma_cm2, level0,
+                               phi_c, f_term, max_level, kph, gamma, b5, counts, hashes, segments, fc, src_offset,
+                               0, NULL, 0, NULL, 0, NULL, &n_out);
+  if (rc == 0) { budget[0] = b5[0]; budget[1] = b5[1]; budget[2] = b5[2]; }
+  return rc;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -23,6 +23,12 @@ Recipes (base seed 20101, numpy PCG64):
   same medium, 1-256 sources, Ndot log-uniform in [1e47, 1e50].
 * ``request_stream(rate, duration)`` -- Poisson arrivals; cells log-uniform in
   [64^3, 256^3], 1-500 sources, 1-20 coupled steps of 0.5 Myr.
+* ``pulse(N)`` -- Application 5 (Sec. 9): a 1 Mpc box of uniform n_H = 1e-4
+  cm^-3, kept optically thin (x_HI = 1e-5, what photo-ionisation equilibrium
+  gives there), one 29.6 eV source at the corner whose rate follows
+  ``pulse_rate(t)`` (Eq. "test12": L_max = 1e55 photons/s, t0 = 0.5 Myr,
+  A = 4); radiative-transfer timestep 50 kyr, so light crosses 1/65 of the
+  box per step.
 """
 from __future__ import annotations
 
@@ -34,6 +40,7 @@ SIGMA_HI = 6.3e-18
 ALPHA_B = 2.59e-13
 E_HI_EV = 13.6
 BASE_SEED = 20101
+C_CM_S = 2.99792458e10  # speed of light
 
 DEFAULT_PARAMS = dict(level0=1, phi_c=5.1, f_term=1e-10, max_level=14)
 
@@ -205,3 +212,23 @@ def request_grid(req: dict, box_kpc: float = 6.6) -> dict:
     n = lognormal_density(N, seed=req["seed"])
     pos, ndot, e, sg = random_sources((N, N, N), box / N, req["nsrc"], 1e47, 1e50, rng)
     return _grid(N, box, n, 1.0, pos, ndot, e, sg, alpha_B=ALPHA_B)
+
+
+def pulse_rate(t_s, L_max: float = 1e55, t0_s: float = 0.5 * MYR_S, A: float = 4.0):
+    """Eq. "test12" (Application 5): L(t) = L_max exp[A (t_f / t0 - 1)] with
+    t_f = 2 |t - t0 round(t / t0)|, a pulse of period t0 peaking at t0/2 + k t0."""
+    t = np.asarray(t_s, dtype=np.float64)
+    tf = 2.0 * np.abs(t - t0_s * np.round(t / t0_s))
+    return L_max * np.exp(A * (tf / t0_s - 1.0))
+
+
+def pulse(N: int = 128, box_kpc: float = 1000.0, n_H: float = 1e-4, x_HI: float = 1e-5,
+          e_ph: float = 29.6) -> dict:
+    """Application 5 (Sec. 9) medium on an N^3 grid: uniform, optically thin,
+    one source at the domain corner with the pulse's initial rate; the caller
+    sets the rate of every step from pulse_rate(t)."""
+    g = _grid(N, box_cm(N, box_kpc), n_H, x_HI, [[0.0, 0.0, 0.0]], [float(pulse_rate(0.0))], [e_ph], [SIGMA_HI],
+              alpha_B=ALPHA_B)
+    g["dt_s"] = 0.05 * MYR_S
+    g["light_cm"] = C_CM_S * g["dt_s"]
+    return g
