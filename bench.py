@@ -318,6 +318,9 @@ def run_native(args, rank, world, local):
         # per cell: n_H, x_HI (FP64), k_ph read, the per-cell value written and read back
         out["timestep"] = {"ms": ms, "dt_s": dt_p, "cells": cells,
                            "gb_s": cells * (8 + 8 + (8 if head == "fp64" else 4) + 4 + 4) / (ms / 1e3) / 1e9}
+    # finite speed of light: the Application 5 pulse (Sec. 9)
+    if not args.no_fsl:
+        out["finite_light"] = finite_light(args, ctx, stream, flush, head)
     # the batched and serving configurations are measured on one GPU
     if not args.no_batched and world == 1:
         out["batched"] = batched(args, ctx, stream, dev, world)
@@ -326,6 +329,65 @@ def run_native(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     return out
+
+
+def finite_light(args, ctx, stream, flush, precision) -> dict:
+    """Application 5 (Sec. 9, Eq. "test12") with a finite speed of light
+    (Sec. 2.1, Step 3j): a 1 Mpc box of 128^3 cells, optically thin, a corner
+    source whose rate pulses with period 0.5 Myr, radiative-transfer timestep
+    50 kyr (light crosses 1.96 cells per step).  After 6 Myr of steps
+    (untimed; light has crossed the box diagonal, so packages of every age
+    are in flight) each timed step sets the source's rate, traces (continuing
+    every package in flight and halting them again c dt_P further on) and
+    updates the chemistry."""
+    import torch
+    from paper_1012_2865_gb300 import native, synth
+
+    g = synth.pulse(128)
+    dt, light = g["dt_s"], g["light_cm"]
+    grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
+    params = dict(synth.DEFAULT_PARAMS, light_cm=light)
+    fill = int(round(6.0 * synth.MYR_S / dt))
+    for n in range(fill):
+        grid.set_source_rates([float(synth.pulse_rate(n * dt))])
+        grid.trace(**params)  # synchronous: sizes the queue and the stores of packages in flight
+        grid.chem(dt, 10, synth.ALPHA_B)
+    torch.cuda.synchronize()
+    step_ms, kern_ms, segs, moved, pushed = [], [], 0, 0, 0
+    launches = 0
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = native.rt_kernel_launches()
+        e0.record(stream)
+        grid.set_source_rates([float(synth.pulse_rate((fill + k) * dt))])
+        grid.trace(sync=False, **params)
+        grid.chem(dt, 10, synth.ALPHA_B)
+        e1.record(stream)
+        e1.synchronize()
+        launches += native.rt_kernel_launches() - l0
+        bb = native.rt_get_budget(grid.h)
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(bb["kernel_ms"])
+        segs += bb["segments"]
+        moved += bb["n_resumed"] + bb["n_halted"]
+        pushed += bb["queue_pushed"]
+    grid.close()
+    t = sum(step_ms) / 1e3
+    kt = sum(kern_ms) / 1e3
+    # algorithmic bytes: per segment the n_HI pair read and the k_ph and Gamma
+    # reductions; 48 bytes per package continued or halted; 96 per queue record
+    red = 8 if precision == "fp64" else 4
+    alg = segs * (8 + 2 * red) + moved * 48 + pushed * 96
+    return {"value": segs / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps,
+            "kernel_ms": 1e3 * kt / args.steps, "segments_per_step": segs // args.steps,
+            "in_flight_per_step": moved // (2 * args.steps), "precision": precision,
+            "trace_gb_s": alg / kt / 1e9, "gpu_launches": int(launches),
+            "workload": "application5-pulse-128^3: 1 Mpc box, n_H 1e-4, x_HI 1e-5, corner source "
+                        "L(t) of Eq. test12 (1e55 ph/s, t0 0.5 Myr, A 4), dt_P 50 kyr, timed after 6 Myr",
+            "l2": "flushed (512 MB write) between steps"}
 
 
 def batched(args, ctx, stream, dev, world):
@@ -487,6 +549,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-fc", action="store_true", help="skip the covering-factor (Sec. 2.3) leg")
     ap.add_argument("--no-timestep", action="store_true", help="skip the adaptive-timestep (Sec. 3.4) leg")
+    ap.add_argument("--no-fsl", action="store_true", help="skip the finite-speed-of-light (Application 5) leg")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-fp64-budget-s", type=float, default=90.0)
     ap.add_argument("--grid", type=int, default=128, help="cells per side (128 = the benchmark workload)")

@@ -87,6 +87,9 @@ typedef struct {
                             RT_TRACE_FC: covering-factor correction */
   int passes;            /* launches over equal ranges of the sources (>= 0);
                             0 = 1, or as many as the automatic sizing needs */
+  double light_cm;       /* finite speed of light (Sec. 2.1, Step 3j): c dt_P,
+                            the distance light travels in this trace (cm,
+                            >= 0); 0 = infinite speed of light.  See below. */
 } rt_trace_params;
 #define RT_TRACE_CHECKSUMS 1
 /* Geometric correction (Sec. 2.3, Eqs. "midpoint", "fc"): each segment's
@@ -98,6 +101,19 @@ typedef struct {
  * the photon budget and every decision are unchanged; k_ph is no longer
  * photon conserving (as the paper notes). */
 #define RT_TRACE_FC 2
+/* Finite speed of light (light_cm > 0).  A package halts where it has
+ * travelled c dt_P per trace since its emission: a package emitted a traces
+ * ago halts at rlim[a], rlim[0] = light_cm / dx and rlim[a] = the previous
+ * trace's rlim[a - 1] + light_cm / dx (cell units, FP64).  The test follows
+ * the split test and uses the crossing radius of the current cell; the cut
+ * segment is deposited as usual and the termination test comes first.  The
+ * grid keeps halted packages in device memory (photons/s, radius, optical
+ * depth, cell, age); the next trace with light_cm > 0 continues them from
+ * their cells through the medium of that trace, alongside the new packages
+ * of its sources, and they do not count as created packages (counts,
+ * hashes).  A trace with light_cm = 0, rt_clear_sources, and adding the grid
+ * to a batch drop the packages in flight.  Batches and rt_trace_noalloc
+ * trace with an infinite speed of light only (light_cm must be 0). */
 
 /* Result of a trace, per grid. */
 typedef struct {
@@ -117,7 +133,26 @@ typedef struct {
                                           (CUDA events on the grid's stream) */
   uint64_t queue_peak;                 /* records of the largest pass */
   int passes;                          /* launches the sources were split into */
+  double resumed;                      /* photons/s of the packages continued from
+                                          the previous trace (light_cm > 0) */
+  double halted;                       /* photons/s of the packages halted at c dt_P;
+                                          emitted + resumed = absorbed + escaped + halted */
+  uint64_t n_resumed, n_halted;        /* their numbers */
 } rt_budget;
+
+/* A package in flight between traces (finite speed of light), as returned by
+ * rt_get_in_flight. */
+typedef struct {
+  double r_cm;          /* distance from its source */
+  double P;             /* photons/s it carries */
+  double tau;           /* optical depth accumulated since emission */
+  int32_t src;          /* index of its source in the grid (order of addition) */
+  int32_t level;        /* HEALPix level */
+  uint32_t pix;         /* nested pixel number */
+  uint32_t age;         /* traces since its emission */
+  int32_t cell[3];      /* cell it halted in */
+  int32_t pad;
+} rt_flight;
 /* hashes[l] is the sum modulo 2^64 over created packages of
  * mix(((uint64)src << 40) ^ ((uint64)l << 34) ^ pixel), where mix is the
  * 64-bit finaliser x ^= x>>31; x *= 0x7fb5d329728ea185; x ^= x>>27;
@@ -148,6 +183,15 @@ int rt_clear_sources(rt_grid* grid);
  * a source-partitioned trace) then contributes the same checksum terms as
  * the whole set traced in one grid.  first + number of sources <= 2^23. */
 int rt_set_source_offset(rt_grid* grid, int first);
+/* Set the emission rate of every source (n = number of sources, ndot[n]
+ * photons/s >= 0), e.g. a time-varying luminosity such as Eq. "test12".
+ * The next trace emits with the new rates; packages already in flight keep
+ * the photons they were emitted with. */
+int rt_set_source_rates(rt_grid* grid, int n, const double* ndot);
+/* Copy the packages in flight after the last trace (finite speed of light)
+ * into out[cap] (host memory); *n receives their number (all of them, also
+ * when above cap).  Synchronous. */
+int rt_get_in_flight(rt_grid* grid, rt_flight* out, uint64_t cap, uint64_t* n);
 
 /* One radiative-transfer pass, Steps 1-5: zero k_ph and Gamma, emit
  * 12*4^level0 packages per source, trace every package through the grid

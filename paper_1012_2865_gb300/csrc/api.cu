@@ -16,15 +16,19 @@
 #include "rt_internal.cuh"
 
 namespace rtg {
-cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass, cudaStream_t st);
-cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm);
-cudaError_t launch_trace(int precision, const TraceArgs& A, int grid, int block, cudaStream_t st);
+cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass, int mode,
+                              unsigned long long in_cap, int pass, int passes, cudaStream_t st);
+cudaError_t trace_occupancy(int precision, int fsl, int block, int* blocks_per_sm);
+cudaError_t launch_trace(int precision, int fsl, const TraceArgs& A, int grid, int block, cudaStream_t st);
+cudaError_t launch_flight_table(const double* old, double* neu, float2* neu32, int n_new, double c_dt,
+                                cudaStream_t st);
+
 cudaError_t launch_chem(int precision, long long ncell, const double* nH, double* xHI, double* xHII,
                         const void* K, void* nhi, double h, int nsub, double alpha, cudaStream_t st);
 cudaError_t launch_refresh(int precision, long long ncell, const double* nH, const double* xHI,
                            void* nhi, cudaStream_t st);
 cudaError_t launch_convert(long long n, const void* src, int src_dtype, void* dst, int dst_dtype,
-                           cudaStream_t st);
+                           cudaStream_t st, double scale = 1.0);
 cudaError_t launch_complement(long long n, const double* x, double* out, cudaStream_t st);
 cudaError_t launch_timestep(long long n, int nx, int ny, int nz, const double* nH, const double* xHI, const void* K,
                             int fp64_rates, double sdx, double tau_front, float eps, float alpha, float dt_max,
@@ -116,6 +120,36 @@ struct TraceState {
   }
 };
 
+constexpr int kAccWords = 8;  // photon budget sums per grid (see InstDev.acc)
+
+// Packages in flight between traces (finite speed of light): two stores used
+// alternately (the next trace continues what the last one halted into
+// buf[in] and halts into the other), the halting radius per age on the
+// device (double-buffered too), and, per source, the photon unit that the
+// stored P values are expressed in.
+struct FlightState {
+  void* buf[2] = {nullptr, nullptr};
+  unsigned long long cap[2] = {0, 0};
+  int in = 0;                 // store holding the packages of the last trace
+  bool live = false;          // the last trace halted packages into buf[in]
+  int in_before = 0;          // in / live before the trace being run (a retry starts again from them)
+  bool live_before = false;
+  std::vector<double> rlim;   // halting radii of the last trace (host mirror)
+  double* rlim64[2] = {nullptr, nullptr};
+  float2* rlim32[2] = {nullptr, nullptr};
+  size_t rlim_cap[2] = {0, 0};
+  int tab = 0;                // device table holding rlim
+  std::vector<double> unit;   // per source: photons/s of P = 1 for the stored packages
+  unsigned long long last_halted = 0;  // packages halted by the last synchronous trace
+  ~FlightState() {
+    for (int i = 0; i < 2; ++i) {
+      if (buf[i]) cudaFree(buf[i]);
+      if (rlim64[i]) cudaFree(rlim64[i]);
+      if (rlim32[i]) cudaFree(rlim32[i]);
+    }
+  }
+};
+
 struct rt_grid {
   rt_ctx* ctx;
   int nx, ny, nz;
@@ -129,7 +163,7 @@ struct rt_grid {
   void* nhi = nullptr;  // FP64 or FP32
   void* K = nullptr;
   void* G = nullptr;
-  double* acc = nullptr;               // 4 doubles
+  double* acc = nullptr;               // kAccWords doubles
   unsigned long long* cnt = nullptr;   // kCntWords
   InstDev* inst_dev = nullptr;
   struct SrcIn { double pos[3], ndot, e_ph, sigma; };
@@ -140,6 +174,8 @@ struct rt_grid {
   int last_level0 = -1;
   int src_offset = 0;                  // index of the first source in checksums
   TraceState ts;
+  FlightState fl;
+  bool src_fsl = false;                // the device source table was built for a finite-c trace
   // pinned readback buffer
   void* host_rb = nullptr;
   bool traced = false;
@@ -254,7 +290,7 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
   ALLOC(g->nhi, d->precision == RT_FP32_MIXED ? 2 * ne : ne);  // mixed: (hi, lo) pairs
   ALLOC(g->K, ne);
   ALLOC(g->G, ne);
-  ALLOC(g->acc, 4 * sizeof(double));
+  ALLOC(g->acc, kAccWords * sizeof(double));
   ALLOC(g->cnt, kCntWords * sizeof(unsigned long long));
   ALLOC(g->inst_dev, sizeof(InstDev));
   ALLOC(g->ts.ctl, CTL_N * sizeof(unsigned long long));
@@ -340,9 +376,30 @@ int rt_set_source_offset(rt_grid* g, int first) {
   return RT_OK;
 }
 
+// Forget the packages in flight (finite speed of light).
+static void drop_flight(rt_grid* g) {
+  g->fl.live = false;
+  g->fl.rlim.clear();
+  g->fl.unit.clear();
+  g->fl.last_halted = 0;
+}
+
 int rt_clear_sources(rt_grid* g) {
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_clear_sources: grid is NULL");
   g->src.clear();
+  g->src_dirty = true;
+  drop_flight(g);
+  return RT_OK;
+}
+
+int rt_set_source_rates(rt_grid* g, int n, const double* ndot) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_set_source_rates: grid is NULL");
+  if (n != (int)g->src.size())
+    return fail(RT_ERR_INVALID_ARG, "rt_set_source_rates: n = %d, the grid has %zu sources", n, g->src.size());
+  if (n > 0 && !ndot) return fail(RT_ERR_INVALID_ARG, "rt_set_source_rates: ndot is NULL");
+  for (int i = 0; i < n; ++i)
+    if (!(ndot[i] >= 0) || !isfinite(ndot[i])) return fail(RT_ERR_INVALID_ARG, "rt_set_source_rates: ndot[%d] = %g", i, ndot[i]);
+  for (int i = 0; i < n; ++i) g->src[i].ndot = ndot[i];
   g->src_dirty = true;
   return RT_OK;
 }
@@ -355,7 +412,10 @@ static bool exact_in_f32(double v) { return v == ldexp(floor(ldexp(v, 4)), -4) &
 
 // Source records of grid g for a given initial level (Step 1: Ndot spread
 // over 12 * 4^level0 root packages), attributed to instance slot `inst`.
-static void build_sources(const rt_grid* g, int level0, int inst, std::vector<SourceDev>& v) {
+// unit[i] / p0[i], when given, override the photons/s carried by P = 1 and
+// the P of new packages (finite speed of light).
+static void build_sources(const rt_grid* g, int level0, int inst, std::vector<SourceDev>& v,
+                          const std::vector<double>* unit = nullptr, const std::vector<double>* p0 = nullptr) {
   const double npix0 = 12.0 * ldexp(1.0, 2 * level0);
   const double dx = g->dx, vol = dx * dx * dx;
   for (size_t i = 0; i < g->src.size(); ++i) {
@@ -365,7 +425,8 @@ static void build_sources(const rt_grid* g, int level0, int inst, std::vector<So
     for (int a = 0; a < 3; ++a) S.s[a] = H.pos[a] / dx;  // cell units
     S.sdx = H.sigma * dx;
     S.heat = (H.e_ph - kEHI) * kEvErg;
-    S.unit = H.ndot / npix0;
+    S.unit = unit ? (*unit)[i] : H.ndot / npix0;
+    S.p0 = p0 ? (*p0)[i] : 1.0;
     S.w = S.unit * H.sigma / (dx * dx);
     S.rw = S.unit / vol;
     S.inst = inst;
@@ -380,19 +441,38 @@ static void build_sources(const rt_grid* g, int level0, int inst, std::vector<So
       exact &= exact_in_f32(S.s[a]) ? 1 : 0;
     }
     S.exact32 = exact && g->nx <= 4096 && g->ny <= 4096 && g->nz <= 4096;
-    S.k32 = make_float4((float)S.sdx, (float)S.w, (float)S.rw, (float)S.heat);
+    // the FP32 walker deposits Gamma in eV/s (rt_get_rates converts to erg/s)
+    S.k32 = make_float4((float)S.sdx, (float)S.w, (float)S.rw, (float)(H.e_ph - kEHI));
     S.s32 = make_float4(s32[0], s32[1], s32[2], S.exact32 ? 1.0f : 0.0f);
     S.slo32 = make_float4(slo[0], slo[1], slo[2], (float)(S.sdx - (double)(float)S.sdx));
-    S.sabs32 = make_float4(sab[0], sab[1], sab[2], 0.0f);
+    S.sabs32 = make_float4(sab[0], sab[1], sab[2], (float)S.p0);
     v.push_back(S);
   }
 }
 
-// Build the per-source device table of a single grid for a given initial level.
-static int prepare_sources(rt_grid* g, int level0) {
-  if (!g->src_dirty && g->last_level0 == level0) return RT_OK;
+// Build the per-source device table of a single grid for a given initial
+// level.  For a finite-speed-of-light trace, while packages are in flight a
+// source keeps the unit their P values are expressed in, and its new
+// packages carry P = (current rate / N_pix) / unit, so rate and level
+// changes leave the packages in flight untouched.
+static int prepare_sources(rt_grid* g, int level0, bool fsl) {
+  if (!g->src_dirty && g->last_level0 == level0 && g->src_fsl == fsl) return RT_OK;
   std::vector<SourceDev> v;
-  build_sources(g, level0, 0, v);
+  if (fsl) {
+    const double npix0 = 12.0 * ldexp(1.0, 2 * level0);
+    const size_t n = g->src.size();
+    std::vector<double> unit(n), p0(n);
+    for (size_t i = 0; i < n; ++i) {
+      const double rate = g->src[i].ndot / npix0;
+      const bool keep = g->fl.live && i < g->fl.unit.size() && g->fl.unit[i] > 0;
+      unit[i] = keep ? g->fl.unit[i] : rate;
+      p0[i] = unit[i] > 0 ? rate / unit[i] : 0.0;
+    }
+    g->fl.unit = unit;
+    build_sources(g, level0, 0, v, &unit, &p0);
+  } else {
+    build_sources(g, level0, 0, v);
+  }
   if (v.size() > g->src_dev_cap) {
     if (g->src_dev) cudaFree(g->src_dev);
     g->src_dev = nullptr;
@@ -405,6 +485,7 @@ static int prepare_sources(rt_grid* g, int level0) {
   CUDA_TRY(cudaStreamSynchronize(g->stream));  // v goes out of scope
   g->src_dirty = false;
   g->last_level0 = level0;
+  g->src_fsl = fsl;
   return RT_OK;
 }
 
@@ -420,6 +501,7 @@ static int check_params(const rt_trace_params* p) {
     return fail(RT_ERR_INVALID_ARG, "rt_trace: blocks_per_sm = %d", p->blocks_per_sm);
   if (p->segs_per_iter < 0 || p->segs_per_iter > 1024) return fail(RT_ERR_INVALID_ARG, "rt_trace: segs_per_iter = %d", p->segs_per_iter);
   if (p->passes < 0) return fail(RT_ERR_INVALID_ARG, "rt_trace: passes = %d", p->passes);
+  if (!(p->light_cm >= 0) || !isfinite(p->light_cm)) return fail(RT_ERR_INVALID_ARG, "rt_trace: light_cm = %g", p->light_cm);
   return RT_OK;
 }
 
@@ -464,22 +546,26 @@ static void fill_common_args(TraceArgs& A, const rt_trace_params* p) {
 // ranges of the sources, for traces whose packages do not fit the queue at
 // once; deposits, budget sums and counters accumulate across the passes.
 // A.npix0, A.queue, A.cap, A.ctl and the per-trace fields are set by the
-// caller; A.src, A.nsrc and A.n_roots are set here per pass.
-static int launch_passes(TraceArgs A, const SourceDev* src, int nsrc, int passes, int precision, int blocks,
-                         cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st) {
+// caller; A.src, A.nsrc, A.src_first and A.n_roots are set here per pass.  Packages in
+// flight (fsl) are shared out over the passes on the device; `mode` and
+// `in_cap` say what the first pass takes over from the previous trace.
+static int launch_passes(TraceArgs A, const SourceDev* src, int nsrc, int passes, int precision, int fsl,
+                         int mode, unsigned long long in_cap, int blocks, cudaEvent_t ev0, cudaEvent_t ev1,
+                         cudaStream_t st) {
   if (passes > nsrc) passes = nsrc;
   if (passes < 1) passes = 1;
   for (int i = 0; i < passes; ++i) {
     const int s0 = (int)((long long)nsrc * i / passes);
     const int s1 = (int)((long long)nsrc * (i + 1) / passes);
     const unsigned long long n = (unsigned long long)A.npix0 * (unsigned long long)(s1 - s0);
-    LAUNCH_TRY(launch_trace_init(A.ctl, n, i == 0, st));
+    LAUNCH_TRY(launch_trace_init(A.ctl, n, i == 0, mode, in_cap, i, passes, st));
     if (i == 0) CUDA_TRY(cudaEventRecord(ev0, st));
-    if (n == 0) continue;
-    A.src = src + s0;
-    A.nsrc = s1 - s0;
+    if (n == 0 && !fsl) continue;
+    A.src = src;
+    A.nsrc = nsrc;
+    A.src_first = s0;
     A.n_roots = n;
-    LAUNCH_TRY(launch_trace(precision, A, blocks, 256, st));
+    LAUNCH_TRY(launch_trace(precision, fsl, A, blocks, 256, st));
   }
   CUDA_TRY(cudaEventRecord(ev1, st));
   return RT_OK;
@@ -521,18 +607,99 @@ static bool grow_after_overflow(unsigned long long peak, unsigned long long limi
   return true;
 }
 
-static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes) {
-  int rc = prepare_sources(g, p->level0);
+// Device buffer of at least `bytes`, reallocated (after the stream's work
+// is done) when smaller.
+static int ensure_buffer(void** p, size_t* have, size_t bytes, cudaStream_t st) {
+  if (*p && *have >= bytes) return RT_OK;
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  CUDA_TRY(cudaMalloc(p, bytes));
+  *have = bytes;
+  return RT_OK;
+}
+
+constexpr unsigned long long kFlightMinCap = 1ULL << 16;  // records of a new in-flight store
+constexpr size_t kFlightMaxAges = 1u << 20;
+
+// Finite speed of light, before the launches of a trace: the halting radii of
+// this trace (advanced from the last trace's on the device; on a retry of
+// the same trace they stand) and room for the packages it halts.
+static int prepare_flight(rt_grid* g, const rt_trace_params* p, bool retry, TraceArgs& A) {
+  FlightState& F = g->fl;
+  cudaStream_t st = g->stream;
+  const double c_dt = p->light_cm / g->dx;  // cell units
+  if (!retry) {
+    // ages that can still be in flight: a stored package lies inside the box,
+    // so nearer its source than the box diagonal
+    const double diag = sqrt((double)g->nx * g->nx + (double)g->ny * g->ny + (double)g->nz * g->nz);
+    size_t n_old = F.live ? F.rlim.size() : 0;
+    while (n_old > 0 && F.rlim[n_old - 1] > diag + 1.0) --n_old;
+    const size_t n_new = n_old + 1;
+    if (n_new > kFlightMaxAges)
+      return fail(RT_ERR_INVALID_ARG, "rt_trace: light_cm = %g cm is too short for this grid (%zu ages in flight)",
+                  p->light_cm, n_new);
+    std::vector<double> neu(n_new);
+    neu[0] = c_dt;
+    for (size_t a = 1; a < n_new; ++a) neu[a] = F.rlim[a - 1] + c_dt;
+    const int nt = 1 - F.tab;
+    size_t have64 = F.rlim_cap[nt] * sizeof(double), have32 = F.rlim_cap[nt] * sizeof(float2);
+    if (F.rlim_cap[nt] < n_new) {
+      const size_t cap = n_new < 64 ? 64 : 2 * n_new;
+      have64 = have32 = 0;
+      int rc = ensure_buffer((void**)&F.rlim64[nt], &have64, cap * sizeof(double), st);
+      if (!rc) rc = ensure_buffer((void**)&F.rlim32[nt], &have32, cap * sizeof(float2), st);
+      if (rc) return rc;
+      F.rlim_cap[nt] = cap;
+    }
+    LAUNCH_TRY(launch_flight_table(F.rlim64[F.tab], F.rlim64[nt], F.rlim32[nt], (int)n_new, c_dt, st));
+    F.tab = nt;
+    F.rlim.swap(neu);
+  }
+  // the output store: the other buffer than the one holding the last trace's packages
+  const int out = F.live ? 1 - F.in : F.in;
+  unsigned long long want = F.last_halted + F.last_halted / 4 + 1024;
+  if (want < kFlightMinCap) want = kFlightMinCap;
+  if (F.cap[out] < want) {
+    const size_t rec = g->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+    size_t have = 0;
+    int rc = ensure_buffer(&F.buf[out], &have, want * rec, st);
+    if (rc) return rc;
+    F.cap[out] = want;
+  }
+  A.rlim64 = F.rlim64[F.tab];
+  A.rlim32 = F.rlim32[F.tab];
+  A.n_ages = (int)F.rlim.size();
+  A.res_in = F.live ? F.buf[F.in] : nullptr;
+  A.halt_out = F.buf[out];
+  A.halt_cap = F.cap[out];
+  return RT_OK;
+}
+
+static void commit_flight(rt_grid* g, bool fsl);
+
+static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool retry = false) {
+  const bool fsl = p->light_cm > 0;
+  if (retry) {
+    g->fl.in = g->fl.in_before;
+    g->fl.live = g->fl.live_before;
+  } else {
+    g->fl.in_before = g->fl.in;
+    g->fl.live_before = g->fl.live;
+  }
+  int rc = prepare_sources(g, p->level0, fsl);
   if (rc) return rc;
   cudaStream_t st = g->stream;
   const size_t ne = (size_t)g->ncell * elem_bytes(g->precision);
   CUDA_TRY(cudaMemsetAsync(g->K, 0, ne, st));  // Step 2
   CUDA_TRY(cudaMemsetAsync(g->G, 0, ne, st));
-  CUDA_TRY(cudaMemsetAsync(g->acc, 0, 4 * sizeof(double), st));
+  CUDA_TRY(cudaMemsetAsync(g->acc, 0, kAccWords * sizeof(double), st));
   CUDA_TRY(cudaMemsetAsync(g->cnt, 0, kCntWords * sizeof(unsigned long long), st));
   const int nsrc = (int)g->src.size();
   if (nsrc == 0) {
-    LAUNCH_TRY(launch_trace_init(g->ts.ctl, 0, 1, st));
+    LAUNCH_TRY(launch_trace_init(g->ts.ctl, 0, 1, FLIGHT_OFF, 0, 0, 1, st));
+    drop_flight(g);
     g->traced = false;
     g->ts.passes_run = 0;
     return RT_OK;
@@ -560,16 +727,37 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes) {
   A.cap = g->ts.cap;
   A.ctl = g->ts.ctl;
   A.max_steps = 2 * (g->nx + g->ny + g->nz) + 16;
+  int mode = FLIGHT_OFF;
+  unsigned long long in_cap = 0;
+  if (fsl) {
+    if ((rc = prepare_flight(g, p, retry, A))) return rc;
+    mode = retry ? FLIGHT_RETRY : (g->fl.live ? FLIGHT_ADVANCE : FLIGHT_OFF);
+    in_cap = g->fl.live ? g->fl.cap[g->fl.in] : 0;
+  }
   const int block = 256;  // the trace kernel is compiled for 256-thread blocks
   int per_sm = 0;
-  CUDA_TRY(trace_occupancy(g->precision, block, &per_sm));
+  CUDA_TRY(trace_occupancy(g->precision, fsl ? 1 : 0, block, &per_sm));
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
-  if ((rc = launch_passes(A, g->src_dev, nsrc, passes, g->precision, per_sm * g->ctx->num_sms, g->ev0, g->ev1, st)))
+  if ((rc = launch_passes(A, g->src_dev, nsrc, passes, g->precision, fsl ? 1 : 0, mode, in_cap,
+                          per_sm * g->ctx->num_sms, g->ev0, g->ev1, st)))
     return rc;
+  commit_flight(g, fsl);
   g->traced = true;
   g->ts.passes_run = passes < nsrc ? passes : nsrc;
   return RT_OK;
+}
+
+// After the launches of a trace: with a finite speed of light its output
+// store now holds the packages in flight; otherwise nothing is.
+static void commit_flight(rt_grid* g, bool fsl) {
+  FlightState& F = g->fl;
+  if (!fsl) {
+    drop_flight(g);
+    return;
+  }
+  if (F.live) F.in = 1 - F.in;
+  F.live = true;
 }
 
 static int read_budget(rt_grid* g, rt_budget* out) {
@@ -577,7 +765,7 @@ static int read_budget(rt_grid* g, rt_budget* out) {
   unsigned long long* hcnt = (unsigned long long*)((char*)g->host_rb + 64);
   unsigned long long* hctl = (unsigned long long*)((char*)g->host_rb + 512);
   cudaStream_t st = g->stream;
-  CUDA_TRY(cudaMemcpyAsync(hacc, g->acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hacc, g->acc, kAccWords * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hcnt, g->cnt, kCntWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hctl, g->ts.ctl, CTL_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -596,6 +784,11 @@ static int read_budget(rt_grid* g, rt_budget* out) {
   out->queue_peak = hctl[CTL_PEAK] > hctl[CTL_TAIL] ? hctl[CTL_PEAK] : hctl[CTL_TAIL];
   out->passes = g->ts.passes_run;
   out->status = (int)hctl[CTL_STATUS];
+  out->resumed = hacc[3];
+  out->halted = hacc[4];
+  out->n_resumed = hctl[CTL_RESUME];
+  out->n_halted = hctl[CTL_HALTED];
+  if (g->fl.live) g->fl.last_halted = out->n_halted;
   float ms = 0.f;
   if (g->traced && cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) out->kernel_ms = ms;
   else cudaGetLastError();
@@ -622,14 +815,21 @@ int rt_trace(rt_grid* g, const rt_trace_params* p, rt_budget* out) {
   const int p_min = p->passes > 1 ? p->passes : 1;
   int passes = automatic && g->ts.passes > p_min ? g->ts.passes : p_min;
   const int nsrc = (int)g->src.size();
+  const bool fsl = p->light_cm > 0;
   for (int attempt = 0;; ++attempt) {
     if ((rc = ensure_queue(g, cap))) return rc;
-    if ((rc = enqueue_trace(g, p, passes))) return rc;
+    if ((rc = enqueue_trace(g, p, passes, attempt > 0))) return rc;
     if (!out) return RT_OK;
     if ((rc = read_budget(g, out))) return rc;
-    if (out->status == RT_ERR_QUEUE_OVERFLOW && automatic && attempt < 40) {
-      const unsigned long long limit = queue_cap_limit(rec, (size_t)g->ts.cap * g->ts.rec_bytes);
-      if (grow_after_overflow(out->queue_peak, limit, nsrc, &cap, &passes)) continue;
+    if (out->status == RT_ERR_QUEUE_OVERFLOW && attempt < 40) {
+      // the store of halted packages grows by itself (read_budget noted how
+      // many there were); the queue when it is sized automatically
+      bool again = fsl && out->n_halted > g->fl.cap[g->fl.in];
+      if (out->queue_peak > g->ts.cap) {
+        const unsigned long long limit = queue_cap_limit(rec, (size_t)g->ts.cap * g->ts.rec_bytes);
+        again = automatic && grow_after_overflow(out->queue_peak, limit, nsrc, &cap, &passes);
+      }
+      if (again) continue;
     }
     if (out->status != RT_OK)
       return fail(out->status, "rt_trace: device status %d (queue capacity %llu, largest pass %llu, passes %d)",
@@ -697,22 +897,27 @@ int rt_set_state(rt_grid* g, const double* n_H, const double* x_HI, const double
   return RT_OK;
 }
 
-static int copy_field(rt_grid* g, const void* src, int src_dtype, void* dst, int dtype, int mem_kind) {
+// The FP32-mixed grid keeps Gamma in eV/s (FP32 erg/s values of faint cells
+// fall below the FP32 normal range); this scale turns it into erg/s.
+static double gamma_scale(const rt_grid* g) { return g->precision == RT_FP64 ? 1.0 : kEvErg; }
+
+static int copy_field(rt_grid* g, const void* src, int src_dtype, void* dst, int dtype, int mem_kind,
+                      double scale = 1.0) {
   if (!dst) return RT_OK;
   const long long n = g->ncell;
   const size_t eb = dtype == RT_DTYPE_F64 ? 8 : 4;
   cudaStream_t st = g->stream;
   if (mem_kind == RT_MEM_DEVICE) {
-    LAUNCH_TRY(launch_convert(n, src, src_dtype, dst, dtype, st));
+    LAUNCH_TRY(launch_convert(n, src, src_dtype, dst, dtype, st, scale));
     return RT_OK;
   }
-  if (src_dtype == dtype) {  // same type: straight to the host
+  if (src_dtype == dtype && scale == 1.0) {  // same type: straight to the host
     CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)n * eb, cudaMemcpyDeviceToHost, st));
     return RT_OK;
   }
   void* tmp = nullptr;
   CUDA_TRY(cudaMallocAsync(&tmp, (size_t)n * eb, st));
-  cudaError_t e = launch_convert(n, src, src_dtype, tmp, dtype, st);
+  cudaError_t e = launch_convert(n, src, src_dtype, tmp, dtype, st, scale);
   if (e == cudaSuccess) {
     g_launches.fetch_add(1);
     e = cudaMemcpyAsync(dst, tmp, (size_t)n * eb, cudaMemcpyDeviceToHost, st);
@@ -731,7 +936,7 @@ int rt_get_rates(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype, int 
   const int kd = g->precision == RT_FP64 ? RT_DTYPE_F64 : RT_DTYPE_F32;
   int rc;
   if ((rc = copy_field(g, g->K, kd, kph, dtype, mem_kind))) return rc;
-  if ((rc = copy_field(g, g->G, kd, gamma, dtype, mem_kind))) return rc;
+  if ((rc = copy_field(g, g->G, kd, gamma, dtype, mem_kind, gamma_scale(g)))) return rc;
   if ((rc = copy_field(g, g->xHI, RT_DTYPE_F64, x_HI, dtype, mem_kind))) return rc;
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   return RT_OK;
@@ -749,15 +954,16 @@ int rt_set_rates(rt_grid* g, const void* kph, const void* gamma, int dtype, int 
   cudaStream_t st = g->stream;
   const void* src[2] = {kph, gamma};
   void* dst[2] = {g->K, g->G};
+  const double scale[2] = {1.0, 1.0 / gamma_scale(g)};
   for (int f = 0; f < 2; ++f) {
     if (mem_kind == RT_MEM_DEVICE) {
-      LAUNCH_TRY(launch_convert(n, src[f], dtype, dst[f], kd, st));
+      LAUNCH_TRY(launch_convert(n, src[f], dtype, dst[f], kd, st, scale[f]));
       continue;
     }
     void* tmp = nullptr;
     CUDA_TRY(cudaMallocAsync(&tmp, (size_t)n * eb, st));
     cudaError_t e = cudaMemcpyAsync(tmp, src[f], (size_t)n * eb, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_convert(n, tmp, dtype, dst[f], kd, st);
+    if (e == cudaSuccess) e = launch_convert(n, tmp, dtype, dst[f], kd, st, scale[f]);
     if (e == cudaSuccess) g_launches.fetch_add(1);
     cudaFreeAsync(tmp, st);
     if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_set_rates: %s", cudaGetErrorString(e));
@@ -799,6 +1005,60 @@ int rt_timestep(rt_grid* g, double eps_ion, double alpha_B, double sigma_front, 
   double dt = finite ? (v >= 1.0f ? dt_max : (double)v * dt_max) : (v >= 3.0e38f ? dt_max : (double)v);
   if (dt_prev > 0 && 2.0 * dt_prev < dt) dt = 2.0 * dt_prev;  // Eq. "dtchange"
   *dt_out = dt;
+  return RT_OK;
+}
+
+int rt_get_in_flight(rt_grid* g, rt_flight* out, uint64_t cap, uint64_t* n) {
+  if (!g || !n || (cap > 0 && !out)) return fail(RT_ERR_INVALID_ARG, "rt_get_in_flight: NULL argument");
+  if (int rcw = wait_batch(g)) return rcw;
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  *n = 0;
+  if (!g->fl.live) return RT_OK;
+  unsigned long long cnt = 0;
+  CUDA_TRY(cudaMemcpyAsync(&cnt, g->ts.ctl + CTL_HALTED, sizeof cnt, cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  const FlightState& F = g->fl;
+  const unsigned long long stored = cnt < F.cap[F.in] ? cnt : F.cap[F.in];
+  *n = stored;
+  const unsigned long long m = stored < cap ? stored : cap;
+  if (m == 0) return RT_OK;
+  const bool f64 = g->precision == RT_FP64;
+  const size_t rec = f64 ? sizeof(Rec64) : sizeof(Rec32);
+  std::vector<unsigned char> raw((size_t)m * rec);
+  CUDA_TRY(cudaMemcpyAsync(raw.data(), F.buf[F.in], raw.size(), cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  const unsigned nx = (unsigned)g->nx, ny = (unsigned)g->ny;
+  for (unsigned long long i = 0; i < m; ++i) {
+    rt_flight& o = out[i];
+    memset(&o, 0, sizeof o);
+    uint32_t cell;
+    double P;
+    if (f64) {
+      const Rec64& q = ((const Rec64*)raw.data())[i];
+      o.r_cm = q.r * g->dx;
+      P = q.P;
+      o.tau = q.tau;
+      o.src = (int32_t)q.src;
+      o.level = (int32_t)(q.level & 15u);
+      o.pix = q.pix;
+      o.age = q.level >> 4;
+      cell = q.tag;
+    } else {
+      const Rec32& q = ((const Rec32*)raw.data())[i];
+      o.r_cm = ((double)q.r + (double)q.r_lo) * g->dx;
+      P = q.P;
+      o.tau = (double)q.tau + (double)q.tau_lo;
+      o.src = (int32_t)q.src;
+      o.level = (int32_t)(q.tag & 15u);
+      o.pix = q.pix;
+      o.age = q.age;
+      cell = q.cell;
+    }
+    o.P = (size_t)o.src < F.unit.size() ? P * F.unit[o.src] : 0.0;
+    o.cell[0] = (int32_t)(cell % nx);
+    o.cell[1] = (int32_t)((cell / nx) % ny);
+    o.cell[2] = (int32_t)(cell / (nx * ny));
+  }
   return RT_OK;
 }
 
@@ -953,7 +1213,7 @@ static int batch_enqueue(rt_batch* b, const rt_trace_params* p, int passes) {
   cudaStream_t st = b->stream;
   LAUNCH_TRY(launch_batch_zero(b->inst_dev, ninst, b->precision, b->max_cells, st));  // Step 2
   if (b->nsrc == 0) {
-    LAUNCH_TRY(launch_trace_init(b->ts.ctl, 0, 1, st));
+    LAUNCH_TRY(launch_trace_init(b->ts.ctl, 0, 1, FLIGHT_OFF, 0, 0, 1, st));
     b->traced = false;
     b->ts.passes_run = 0;
     return RT_OK;
@@ -980,11 +1240,11 @@ static int batch_enqueue(rt_batch* b, const rt_trace_params* p, int passes) {
     A.dir_levels = b->ctx->dir_levels;
   }
   int per_sm = 0;
-  CUDA_TRY(trace_occupancy(b->precision, 256, &per_sm));
+  CUDA_TRY(trace_occupancy(b->precision, 0, 256, &per_sm));
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
-  if ((rc = launch_passes(A, b->src_dev, b->nsrc, passes, b->precision, per_sm * b->ctx->num_sms, b->ev0, b->ev1,
-                          st)))
+  if ((rc = launch_passes(A, b->src_dev, b->nsrc, passes, b->precision, 0, FLIGHT_OFF, 0, per_sm * b->ctx->num_sms,
+                          b->ev0, b->ev1, st)))
     return rc;
   b->traced = true;
   b->ts.passes_run = passes < b->nsrc ? passes : b->nsrc;
@@ -1074,6 +1334,7 @@ int rt_batch_add(rt_batch* b, rt_grid* g, int* slot) {
   for (rt_grid* h : b->slots)
     if (h == g) return fail(RT_ERR_STATE, "rt_batch_add: grid is already in the batch");
   CUDA_TRY(cudaStreamSynchronize(g->stream));  // work already queued on the grid's own stream
+  drop_flight(g);  // batches trace with an infinite speed of light
   b->precision = g->precision;
   int s = -1;
   for (size_t i = 0; i < b->slots.size(); ++i)
@@ -1117,9 +1378,17 @@ static int sync_members(rt_batch* b) {
   return RT_OK;
 }
 
+// Batches trace with an infinite speed of light only.
+static int check_batch_params(const rt_trace_params* p) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->light_cm != 0.0) return fail(RT_ERR_INVALID_ARG, "batch traces take light_cm = 0 (infinite speed of light)");
+  return RT_OK;
+}
+
 int rt_batch_trace(rt_batch* b, const rt_trace_params* p, int sync) {
   if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_trace: batch is NULL");
-  int rc = check_params(p);
+  int rc = check_batch_params(p);
   if (rc) return rc;
   CUDA_TRY(cudaSetDevice(b->ctx->device));
   if (rt_batch_size(b) == 0) return RT_OK;
@@ -1181,7 +1450,7 @@ static bool same_params(const rt_trace_params& a, const rt_trace_params& b) {
 
 int rt_batch_step(rt_batch* b, const rt_trace_params* p, double dt_s, int nsub, double alpha_B, int nsteps) {
   if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_step: batch is NULL");
-  int rc = check_params(p);
+  int rc = check_batch_params(p);
   if (rc) return rc;
   if (nsteps < 0 || !(dt_s >= 0) || !isfinite(dt_s) || nsub < 1 || !(alpha_B >= 0) || !isfinite(alpha_B))
     return fail(RT_ERR_INVALID_ARG, "rt_batch_step: bad nsteps / dt_s / nsub / alpha_B");
@@ -1251,7 +1520,7 @@ int rt_batch_get_budget(rt_batch* b, int slot, rt_budget* out) {
   rt_grid* g = b->slots[slot];
   double* hacc = (double*)g->host_rb;
   unsigned long long* hcnt = (unsigned long long*)((char*)g->host_rb + 64);
-  CUDA_TRY(cudaMemcpyAsync(hacc, g->acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaMemcpyAsync(hacc, g->acc, kAccWords * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
   CUDA_TRY(cudaMemcpyAsync(hcnt, g->cnt, kCntWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream));
   CUDA_TRY(cudaStreamSynchronize(b->stream));
   memset(out, 0, sizeof *out);
@@ -1276,7 +1545,7 @@ int rt_batch_get_budget(rt_batch* b, int slot, rt_budget* out) {
 
 int rt_batch_autotune(rt_batch* b, rt_trace_params* p) {
   if (!b || !p) return fail(RT_ERR_INVALID_ARG, "rt_batch_autotune: NULL argument");
-  int rc = check_params(p);
+  int rc = check_batch_params(p);
   if (rc) return rc;
   if (rt_batch_size(b) == 0) return RT_OK;
   rt_trace_params q = *p;
@@ -1285,7 +1554,7 @@ int rt_batch_autotune(rt_batch* b, rt_trace_params* p) {
   if ((rc = rt_batch_trace(b, &q, 1))) return rc;  // sizes the queue, warms up
   const int spi[] = {4, 8, 16, 32};
   int per_sm_max = 0;
-  CUDA_TRY(trace_occupancy(b->precision, 256, &per_sm_max));
+  CUDA_TRY(trace_occupancy(b->precision, 0, 256, &per_sm_max));
   float best = 1e30f;
   rt_trace_params bestp = q;
   for (int bps = 1; bps <= (per_sm_max > 0 ? per_sm_max : 1); ++bps) {

@@ -141,10 +141,10 @@ __global__ void refresh_nhi_pair_kernel(long long ncell, const double* __restric
 }
 
 template <typename ST, typename DT>
-__global__ void convert_kernel(long long n, const ST* __restrict__ src, DT* __restrict__ dst) {
+__global__ void convert_kernel(long long n, const ST* __restrict__ src, DT* __restrict__ dst, double scale) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x)
-    dst[c] = (DT)src[c];
+    dst[c] = scale == 1.0 ? (DT)src[c] : (DT)((double)src[c] * scale);
 }
 
 __global__ void complement_kernel(long long n, const double* __restrict__ x, double* __restrict__ out) {
@@ -307,7 +307,7 @@ __global__ void batch_zero_kernel(const InstDev* __restrict__ inst, int esz) {
     G[c] = 0u;
   }
   if (blockIdx.x == 0) {
-    for (int i = threadIdx.x; i < 4; i += blockDim.x) I.acc[i] = 0.0;
+    for (int i = threadIdx.x; i < 8; i += blockDim.x) I.acc[i] = 0.0;
     for (int i = threadIdx.x; i < kCntWords; i += blockDim.x) I.cnt[i] = 0ULL;
   }
 }
@@ -364,18 +364,19 @@ cudaError_t launch_batch_chem(const InstDev* inst, int ninst, int precision, lon
   return cudaGetLastError();
 }
 
-// src_dtype / dst_dtype: RT_DTYPE_F64 or RT_DTYPE_F32
+// src_dtype / dst_dtype: RT_DTYPE_F64 or RT_DTYPE_F32; dst = src * scale
+// (the product in FP64)
 cudaError_t launch_convert(long long n, const void* src, int src_dtype, void* dst, int dst_dtype,
-                           cudaStream_t st) {
+                           cudaStream_t st, double scale) {
   const int block = 256, grid = grid_for(n, block);
   if (src_dtype == RT_DTYPE_F64 && dst_dtype == RT_DTYPE_F64)
-    convert_kernel<double, double><<<grid, block, 0, st>>>(n, (const double*)src, (double*)dst);
+    convert_kernel<double, double><<<grid, block, 0, st>>>(n, (const double*)src, (double*)dst, scale);
   else if (src_dtype == RT_DTYPE_F64 && dst_dtype == RT_DTYPE_F32)
-    convert_kernel<double, float><<<grid, block, 0, st>>>(n, (const double*)src, (float*)dst);
+    convert_kernel<double, float><<<grid, block, 0, st>>>(n, (const double*)src, (float*)dst, scale);
   else if (src_dtype == RT_DTYPE_F32 && dst_dtype == RT_DTYPE_F64)
-    convert_kernel<float, double><<<grid, block, 0, st>>>(n, (const float*)src, (double*)dst);
+    convert_kernel<float, double><<<grid, block, 0, st>>>(n, (const float*)src, (double*)dst, scale);
   else
-    convert_kernel<float, float><<<grid, block, 0, st>>>(n, (const float*)src, (float*)dst);
+    convert_kernel<float, float><<<grid, block, 0, st>>>(n, (const float*)src, (float*)dst, scale);
   return cudaGetLastError();
 }
 

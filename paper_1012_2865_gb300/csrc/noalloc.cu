@@ -30,9 +30,10 @@
 #include "rt_internal.cuh"
 
 namespace rtg {
-cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass, cudaStream_t st);
-cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm);
-cudaError_t launch_trace(int precision, const TraceArgs& A, int grid, int block, cudaStream_t st);
+cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass, int mode,
+                              unsigned long long in_cap, int pass, int passes, cudaStream_t st);
+cudaError_t trace_occupancy(int precision, int fsl, int block, int* blocks_per_sm);
+cudaError_t launch_trace(int precision, int fsl, const TraceArgs& A, int grid, int block, cudaStream_t st);
 cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st);
 }  // namespace rtg
 
@@ -120,7 +121,7 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
   if (nsrc > 0 && (!pos_cm || !ndot || !e_ph_eV || !sigma_cm2)) return na_fail(RT_ERR_INVALID_ARG, "source arrays");
   if (p->level0 < 0 || p->max_level < p->level0 || p->max_level > RT_MAX_LEVEL || !(p->phi_c > 0) ||
       !(p->f_term > 0 && p->f_term < 1) || p->segs_per_iter < 0 || p->segs_per_iter > 1024 ||
-      p->blocks_per_sm < 0 || p->blocks_per_sm > 32 || p->passes < 0 || p->passes > 1)
+      p->blocks_per_sm < 0 || p->blocks_per_sm > 32 || p->passes < 0 || p->passes > 1 || p->light_cm != 0.0)
     return na_fail(RT_ERR_INVALID_ARG, "trace parameters");
   if (p->queue_capacity > RT_NOALLOC_MAX_RECORDS)
     return na_fail(RT_ERR_INVALID_ARG, "queue_capacity above RT_NOALLOC_MAX_RECORDS (262144)");
@@ -201,7 +202,8 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
   }
 
   const unsigned long long n_roots = (unsigned long long)npix0 * (unsigned long long)nsrc;
-  if ((e = launch_trace_init(ctl, n_roots, 1, st)) != cudaSuccess) return na_fail(RT_ERR_CUDA, "trace init", e);
+  if ((e = launch_trace_init(ctl, n_roots, 1, FLIGHT_OFF, 0, 0, 1, st)) != cudaSuccess)
+    return na_fail(RT_ERR_CUDA, "trace init", e);
   if (n_roots > 0) {
     TraceArgs A;
     memset(&A, 0, sizeof A);
@@ -223,7 +225,6 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
     A.tau_term = -log(p->f_term);
     A.tau_term32 = (float)A.tau_term;
     A.tau_term32lo = (float)(A.tau_term - (double)A.tau_term32);
-  A.tau_term32lo = (float)(A.tau_term - (double)A.tau_term32);
     A.queue = base + kNaQueueOff;
     A.cap = p->queue_capacity > 0 ? (unsigned long long)p->queue_capacity : (unsigned long long)RT_NOALLOC_MAX_RECORDS;
     A.ctl = ctl;
@@ -237,10 +238,10 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
       A.theta32[l] = (float)A.theta[l];
     }
     int per_sm = 0;
-    if ((e = trace_occupancy(RT_FP32_MIXED, 256, &per_sm)) != cudaSuccess) return na_fail(RT_ERR_CUDA, "occupancy", e);
+    if ((e = trace_occupancy(RT_FP32_MIXED, 0, 256, &per_sm)) != cudaSuccess) return na_fail(RT_ERR_CUDA, "occupancy", e);
     if (per_sm < 1) per_sm = 1;
     if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
-    if ((e = launch_trace(RT_FP32_MIXED, A, per_sm * sms, 256, st)) != cudaSuccess)
+    if ((e = launch_trace(RT_FP32_MIXED, 0, A, per_sm * sms, 256, st)) != cudaSuccess)
       return na_fail(RT_ERR_CUDA, "trace launch", e);
   }
   // result: budget, counters and control words

@@ -23,7 +23,18 @@ enum CtlWord {
   CTL_EPOCH = 49,        // tag of this trace's queue records
   CTL_PEAK = 50,         // largest TAIL of the earlier passes of this trace
   CTL_PUSHED = 51,       // sum of TAIL over the earlier passes of this trace
+  CTL_RESUME = 52,       // packages in flight from the previous trace (input store)
+  CTL_RES_A = 53,        // this pass continues input records [RES_A, RES_B)
+  CTL_RES_B = 54,
+  CTL_HALTED = 56,       // packages halted so far in this trace (output store slots)
   CTL_N = 64             // words (512 bytes)
+};
+
+// trace_init_kernel modes for the in-flight stores (finite speed of light)
+enum FlightMode {
+  FLIGHT_OFF = 0,      // nothing in flight: RESUME = HALTED = 0
+  FLIGHT_ADVANCE = 1,  // a new trace continues what the previous one halted
+  FLIGHT_RETRY = 2     // the same trace again (after growing a store): keep RESUME
 };
 
 // One point source, prepared on the host for the kernels.  P of a package is
@@ -34,7 +45,7 @@ struct __align__(16) SourceDev {
   float4 k32;     // sdx, w, rw, heat (see the FP64 fields)
   float4 s32;     // position as FP32 pair, high part; .w = 1 if exact32
   float4 slo32;   // low part (s - s32); .w = sdx - k32.x
-  float4 sabs32;  // 2^-46 |s| where the pair does not hold s exactly, else 0
+  float4 sabs32;  // 2^-46 |s| where the pair does not hold s exactly, else 0; .w = p0
   // FP64 view
   double s[3];    // position in cell units (pos_cm / dx)
   double sdx;     // sigma * dx: optical depth per unit n_HI per cell length
@@ -42,6 +53,9 @@ struct __align__(16) SourceDev {
   double rw;      // unit / dx^3: k_ph per unit P per unit n_HI (residual absorption)
   double heat;    // (E_ph - 13.6 eV) in erg
   double unit;    // photons/s carried by P = 1
+  double p0;      // P of a new package (finite speed of light; sabs32.w in FP32):
+                  // 1, unless the unit is kept for packages still in flight
+                  // while the source's rate has changed
   int inst;       // owning grid slot
   int local;      // index of the source within its grid (checksum)
   int exact32;    // position on a 1/16-cell lattice within 4096 cells (see api.cu)
@@ -63,7 +77,7 @@ struct InstDev {
   double* xHII;             // ionised fraction, FP64 (chemistry)
   void* K;                  // k_ph accumulator (double or float)
   void* G;                  // Gamma accumulator (double or float)
-  double* acc;              // [0] emitted [1] absorbed [2] escaped (photons/s)
+  double* acc;              // [0] emitted [1] absorbed [2] escaped [3] resumed [4] halted (photons/s)
   unsigned long long* cnt;  // [0,15) counts, [15,30) hashes, [30] segments, [31], [32] fallbacks
 };
 constexpr int kCntSegments = 2 * kLevels;
@@ -72,10 +86,14 @@ constexpr int kCntFallbacksTau = 2 * kLevels + 2;
 constexpr int kCntWords = 2 * kLevels + 3;
 
 // Queue records.  The tag word is written last with release semantics and
-// equals the trace's epoch once the record is complete.
+// equals the trace's epoch once the record is complete.  The same layouts
+// hold packages in flight between traces (finite speed of light), where the
+// tag is not used as one.
 struct __align__(16) Rec64 {
   double r, P, tau;
-  uint32_t src, pix, level, tag;
+  uint32_t src, pix;
+  uint32_t level;  // level | age << 4
+  uint32_t tag;    // epoch; in flight: the cell index
 };
 struct __align__(16) Rec32 {
   float r, r_lo;  // radius as an FP32 pair
@@ -84,7 +102,9 @@ struct __align__(16) Rec32 {
   float tau_err;  // bound on |tau (pair) - tau (FP64 evaluation)|
   uint32_t src, pix;
   uint32_t tag;   // (epoch << 4) | level
-  uint32_t pad[3];
+  uint32_t age;   // traces since emission (finite speed of light)
+  uint32_t cell;  // in flight: the cell index
+  uint32_t pad;
 };
 static_assert(sizeof(Rec64) == 48, "record layout");
 static_assert(sizeof(Rec32) == 48, "record layout");
@@ -92,8 +112,9 @@ static_assert(sizeof(Rec32) == 48, "record layout");
 struct TraceArgs {
   const InstDev* inst;
   int ninst;
-  const SourceDev* src;
+  const SourceDev* src;     // every source of the launch (packages name them by index)
   int nsrc;
+  int src_first;            // this pass emits sources [src_first, src_first + n_roots / npix0)
   int level0, max_level;
   uint32_t npix0;
   unsigned long long n_roots;
@@ -114,6 +135,13 @@ struct TraceArgs {
   int fc;         // scale k_ph and Gamma deposits by the covering factor (Eq. "fc")
   double theta[kLevels];    // pixel width sqrt(4 pi / N_pix(l)) in radians
   float theta32[kLevels];
+  // finite speed of light (the kernel instantiated for it reads these)
+  const double* rlim64;     // halting radius per age, cell units
+  const float2* rlim32;     // the same as FP32 pairs
+  int n_ages;
+  const void* res_in;       // packages halted by the previous trace (Rec)
+  void* halt_out;           // packages this trace halts (Rec)
+  unsigned long long halt_cap;
 };
 
 // 64-bit finaliser used for the created-package checksum (documented in rt.h).

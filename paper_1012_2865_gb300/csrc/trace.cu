@@ -21,6 +21,13 @@
 // with phi = (1 - e^-tau)/tau (Eq. "kph"), Gamma += k_ph (E - 13.6 eV)
 // (Eq. "gamma"), then termination at tau_tot > -ln f_term with the residual
 // absorbed in place, and exit at the box boundary.
+//
+// Finite speed of light (Step 3j; the kernel instantiated with FSL): a
+// package of age a (traces since its emission) halts where its crossing
+// radius would pass rlim[a]; the cut segment is deposited, the termination
+// test comes first, and the package is appended to an output store with its
+// cell.  The next trace's tickets n_roots .. n_roots + n_res - 1 name the
+// stored packages, which continue from their cells.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -39,12 +46,13 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kShInst = 64;  // grids whose budget and level counters a block keeps in shared memory
 constexpr int kBlock = 256;  // threads per block of the trace kernel
 
-enum Event { EV_NONE = 0, EV_SPLIT = 1, EV_DONE = 2 };
+enum Event { EV_NONE = 0, EV_SPLIT = 1, EV_DONE = 2, EV_HALT = 3 };
+constexpr int kAcc = 5;  // budget sums per grid: emitted, absorbed, escaped, resumed, halted
 
 // Photon budget of one lane for the grid it is working on; lives in shared
 // memory (one slot per thread) and is touched only at package events.
 struct LaneAcc {
-  double emitted, absorbed, escaped;
+  double emitted, absorbed, escaped, resumed, halted;
   unsigned long long segments;
   unsigned int fallbacks, fallbacks_tau;
   int inst;
@@ -55,17 +63,19 @@ struct LaneAcc {
 // its sums here (shared atomics) instead of into global memory, and the
 // block flushes the table once at the end.
 struct BlockBudget {
-  double* sums;             // [kShInst][3]: emitted, absorbed, escaped
+  double* sums;             // [kShInst][kAcc]: emitted, absorbed, escaped, resumed, halted
   unsigned long long* segs; // [kShInst]
   unsigned int* fb;         // [kShInst][2]: fallbacks, fallbacks_tau
 };
 
 __device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A, const BlockBudget& bb) {
   if (a.inst >= 0 && a.inst < kShInst) {
-    double* t = bb.sums + 3 * a.inst;
+    double* t = bb.sums + kAcc * a.inst;
     if (a.emitted != 0.0) atomicAdd(&t[0], a.emitted);
     if (a.absorbed != 0.0) atomicAdd(&t[1], a.absorbed);
     if (a.escaped != 0.0) atomicAdd(&t[2], a.escaped);
+    if (a.resumed != 0.0) atomicAdd(&t[3], a.resumed);
+    if (a.halted != 0.0) atomicAdd(&t[4], a.halted);
     if (a.segments) atomicAdd(&bb.segs[a.inst], a.segments);
     if (a.fallbacks) atomicAdd(&bb.fb[2 * a.inst], a.fallbacks);
     if (a.fallbacks_tau) atomicAdd(&bb.fb[2 * a.inst + 1], a.fallbacks_tau);
@@ -74,11 +84,13 @@ __device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A, const 
     if (a.emitted != 0.0) atomicAdd(&I.acc[0], a.emitted);
     if (a.absorbed != 0.0) atomicAdd(&I.acc[1], a.absorbed);
     if (a.escaped != 0.0) atomicAdd(&I.acc[2], a.escaped);
+    if (a.resumed != 0.0) atomicAdd(&I.acc[3], a.resumed);
+    if (a.halted != 0.0) atomicAdd(&I.acc[4], a.halted);
     if (a.segments) atomicAdd(&I.cnt[kCntSegments], a.segments);
     if (a.fallbacks) atomicAdd(&I.cnt[kCntFallbacks], (unsigned long long)a.fallbacks);
     if (a.fallbacks_tau) atomicAdd(&I.cnt[kCntFallbacksTau], (unsigned long long)a.fallbacks_tau);
   }
-  a.emitted = a.absorbed = a.escaped = 0.0;
+  a.emitted = a.absorbed = a.escaped = a.resumed = a.halted = 0.0;
   a.segments = 0;
   a.fallbacks = 0;
   a.fallbacks_tau = 0;
@@ -135,7 +147,9 @@ __device__ __forceinline__ double next_t64(int c, double s, double n) {
 struct Walk64 {
   using Rec = Rec64;
   uint32_t src, level, pix;
+  uint32_t age;   // traces since emission (finite speed of light)
   double r, P, tau, Pstart;
+  double rlim;    // halting radius of this age
   double s0, s1, s2, n0, n1, n2, t0, t1, t2;
   int c0, c1, c2;
   int nx, ny, nz, steps;
@@ -151,11 +165,13 @@ struct Walk64 {
   __device__ __forceinline__ int inst(const TraceArgs& A) const { return A.src[src].inst; }
   __device__ __forceinline__ double unit(const TraceArgs& A) const { return A.src[src].unit; }
   __device__ __forceinline__ int lvl() const { return (int)level; }
-  __device__ __forceinline__ bool is_root() const { return P == 1.0 && r == 0.0 && tau == 0.0; }
+  // P of a new package of source S (finite speed of light)
+  __device__ __forceinline__ double emit(const SourceDev& S) {
+    P = S.p0;
+    return P;
+  }
 
-  // Steps 3a-3b: direction and cell at radius r.  Returns false if the
-  // package starts outside the box.
-  __device__ __forceinline__ bool start(const TraceArgs& A) {
+  __device__ __forceinline__ void bind(const TraceArgs& A) {
     const SourceDev& S = A.src[src];
     s0 = S.s[0]; s1 = S.s[1]; s2 = S.s[2];
     sdx = S.sdx; w = S.w; rw = S.rw; heat = S.heat;
@@ -167,29 +183,57 @@ struct Walk64 {
     double n[3];
     pix2vec64((int)level, pix, n);
     n0 = n[0]; n1 = n[1]; n2 = n[2];
+    Pstart = P;
+    steps = 0;
+  }
+  // Steps 3a-3b: direction and cell at radius r.  Returns false if the
+  // package starts outside the box.
+  __device__ __forceinline__ bool start(const TraceArgs& A) {
+    bind(A);
     c0 = cell_of64(__dadd_rn(s0, __dmul_rn(r, n0)), n0);
     c1 = cell_of64(__dadd_rn(s1, __dmul_rn(r, n1)), n1);
     c2 = cell_of64(__dadd_rn(s2, __dmul_rn(r, n2)), n2);
-    Pstart = P;
-    steps = 0;
     if (!inside()) return false;
     t0 = next_t64(c0, s0, n0);
     t1 = next_t64(c1, s1, n1);
     t2 = next_t64(c2, s2, n2);
     return true;
   }
+  // A package continued from the previous trace: the cell it halted in.
+  __device__ __forceinline__ void resume(const TraceArgs& A, uint32_t cell) {
+    bind(A);
+    c0 = (int)(cell % (uint32_t)nx);
+    c1 = (int)((cell / (uint32_t)nx) % (uint32_t)ny);
+    c2 = (int)(cell / ((uint32_t)nx * (uint32_t)ny));
+    t0 = next_t64(c0, s0, n0);
+    t1 = next_t64(c1, s1, n1);
+    t2 = next_t64(c2, s2, n2);
+  }
+  __device__ __forceinline__ void set_rlim(const TraceArgs& A) {
+    if ((int)age < A.n_ages) rlim = A.rlim64[age];
+    else { set_status(A.ctl, RT_ERR_STATE); rlim = 0.0; }
+  }
 
   __device__ __forceinline__ void load(const Rec& q) {
-    r = q.r; P = q.P; tau = q.tau; src = q.src; pix = q.pix; level = q.level;
+    r = q.r; P = q.P; tau = q.tau; src = q.src; pix = q.pix; level = q.level & 15u; age = q.level >> 4;
   }
-  // Record of child cpix (level + 1, P/4, same radius and optical depth).
+  // Record of child cpix (level + 1, P/4, same radius, optical depth and age).
   __device__ __forceinline__ Rec make_child(uint32_t cpix) const {
     Rec c;
-    c.r = r; c.P = P * 0.25; c.tau = tau; c.src = src; c.pix = cpix; c.level = level + 1; c.tag = 0;
+    c.r = r; c.P = P * 0.25; c.tau = tau; c.src = src; c.pix = cpix; c.level = (level + 1) | (age << 4); c.tag = 0;
     return c;
   }
+  __device__ __forceinline__ static uint32_t cell_of_record(const Rec& q) { return q.tag; }
+  // A halted package as the next trace continues it (one trace older).
+  __device__ __forceinline__ void store_halted(Rec* q) const {
+    Rec c;
+    c.r = r; c.P = P; c.tau = tau; c.src = src; c.pix = pix; c.level = level | ((age + 1) << 4);
+    c.tag = (uint32_t)(c0 + nx * (c1 + ny * c2));
+    *q = c;
+  }
   // Publish a record in the global queue: payload first, then the tag with
-  // release semantics.
+  // release semantics.  (The age travels in the level word either way.)
+  template <bool FSL>
   __device__ __forceinline__ static void publish(Rec* q, const Rec& c, uint32_t epoch) {
     __stcg(reinterpret_cast<double2*>(&q->r), make_double2(c.r, c.P));
     __stcg(reinterpret_cast<double*>(&q->tau), c.tau);
@@ -199,6 +243,7 @@ struct Walk64 {
   }
   // Poll with a relaxed load; only a successful poll pays for the fence that
   // orders the payload reads after the tag.
+  template <bool FSL>
   __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
     if (ld_relaxed_u32(&q->tag) != epoch) return false;
     __threadfence();
@@ -222,11 +267,14 @@ struct Walk64 {
   }
 
   // One segment.  Returns EV_SPLIT before traversing a cell whose exit radius
-  // exceeds R_split, EV_DONE when the package is absorbed or leaves the box.
+  // exceeds R_split, EV_DONE when the package is absorbed or leaves the box,
+  // EV_HALT (FSL) when it has travelled to its halting radius.
+  template <bool FSL>
   __device__ __forceinline__ int step(const TraceArgs& A, LaneAcc& acc) {
     const double rn = fmin(t0, fmin(t1, t2));
     if ((int)level < A.max_level && rn > A.rsplit[level]) return EV_SPLIT;
-    double dr = __dsub_rn(rn, r);
+    const bool halt = FSL && rn > rlim;  // Step 3j
+    double dr = __dsub_rn(halt ? rlim : rn, r);
     if (dr < 0) dr = 0;
     const int idx = c0 + nx * (c1 + ny * c2);
     const double nh = __ldg(&nhi[idx]);
@@ -257,6 +305,13 @@ struct Walk64 {
       if (heat != 0.0) atomicAdd(&G[idx], kres * heat);
       acc.absorbed += Pstart * unit(A);
       return EV_DONE;
+    }
+    if (halt) {
+      r = rlim;
+      const double u = unit(A);
+      acc.absorbed += (Pstart - P) * u;
+      acc.halted += P * u;
+      return EV_HALT;
     }
     if (n0 != 0 && t0 == rn) { c0 += n0 > 0 ? 1 : -1; t0 = next_t64(c0, s0, n0); }
     if (n1 != 0 && t1 == rn) { c1 += n1 > 0 ? 1 : -1; t1 = next_t64(c1, s1, n1); }
@@ -378,10 +433,12 @@ __device__ __forceinline__ int dir_pair(const TraceArgs& A, int level, uint32_t 
 
 // Exact (FP64) crossing decision for cell (c0, c1, c2) of package (level,
 // pix) of source src: bit 3 = split, bits 0-2 = axes that reach the next
-// plane first.  A free function taking values, so that calling it does not
-// force the caller's walker state into local memory.
+// plane first, bit 6 = the crossing lies beyond the halting radius rlim
+// (+inf without a finite speed of light).  A free function taking values,
+// so that calling it does not force the caller's walker state into local
+// memory.
 __device__ __noinline__ int decide64(const TraceArgs& A, uint32_t src, int level, uint32_t pix, int c0, int c1,
-                                     int c2) {
+                                     int c2, double rlim) {
   const SourceDev& S = A.src[src];
   double n[3];
   pix2vec64(level, pix, n);
@@ -391,6 +448,7 @@ __device__ __noinline__ int decide64(const TraceArgs& A, uint32_t src, int level
   const double rn = fmin(u0, fmin(u1, u2));
   int out = 0;
   if (level < A.max_level && rn > A.rsplit[level]) out |= 8;
+  if (rn > rlim) out |= 64;
   if (n[0] != 0 && u0 == rn) out |= 1;
   if (n[1] != 0 && u1 == rn) out |= 2;
   if (n[2] != 0 && u2 == rn) out |= 4;
@@ -400,6 +458,8 @@ __device__ __noinline__ int decide64(const TraceArgs& A, uint32_t src, int level
 struct Walk32 {
   using Rec = Rec32;
   uint32_t src, pix;
+  uint32_t age;         // traces since emission (finite speed of light)
+  F2 rlim;              // halting radius of this age
   uint32_t level;       // bits 0-3 level, bit 8: 45-degree ray of an exact source,
                         // bit 9: n_HI stored as FP32 pairs
   F2 r;
@@ -427,7 +487,11 @@ struct Walk32 {
       nh_lo = 0.0f;
     }
   }
-  __device__ __forceinline__ bool is_root() const { return P == 1.0f && r.hi == 0.0f && tau == 0.0f; }
+  // P of a new package of source S (finite speed of light)
+  __device__ __forceinline__ double emit(const SourceDev& S) {
+    P = __ldg(&S.sabs32.w);
+    return (double)P;
+  }
   __device__ __forceinline__ int inst(const TraceArgs& A) const { return A.src[src].inst; }
   __device__ __forceinline__ double unit(const TraceArgs& A) const { return A.src[src].unit; }
   __device__ __forceinline__ bool inside() const {
@@ -453,9 +517,11 @@ struct Walk32 {
     return fmaf(t.hi, kBandT, ab);
   }
 
-  // Geometry of a package at radius r: direction pairs, first cell, next
-  // crossings.  False when that cell is outside the box.
-  __device__ __forceinline__ bool start_geom(const TraceArgs& A) {
+  // Geometry of a package at radius r: direction pairs, first cell (the
+  // cell index `cell` when given, else the cell holding the point at r),
+  // next crossings.  False when that cell is outside the box.
+  template <bool GIVEN = false>
+  __device__ __forceinline__ bool start_geom(const TraceArgs& A, uint32_t cell = 0) {
     const SourceDev& S = A.src[src];
     const float4 sh = __ldg(&S.s32);
     const float4 sl = __ldg(&S.slo32);
@@ -467,16 +533,22 @@ struct Walk32 {
     iv0 = n[0].hi != 0.0f ? f2_recip(n[0]) : F2{0.0f, 0.0f};
     iv1 = n[1].hi != 0.0f ? f2_recip(n[1]) : F2{0.0f, 0.0f};
     iv2 = n[2].hi != 0.0f ? f2_recip(n[2]) : F2{0.0f, 0.0f};
-    c0 = cell_of(f2_add(F2{sh.x, sl.x}, f2_mul(r, n[0])), n[0].hi);
-    c1 = cell_of(f2_add(F2{sh.y, sl.y}, f2_mul(r, n[1])), n[1].hi);
-    c2 = cell_of(f2_add(F2{sh.z, sl.z}, f2_mul(r, n[2])), n[2].hi);
-    if (!inside()) return false;
+    if (GIVEN) {
+      c0 = (int)(cell % (uint32_t)nx);
+      c1 = (int)((cell / (uint32_t)nx) % (uint32_t)ny);
+      c2 = (int)(cell / ((uint32_t)nx * (uint32_t)ny));
+    } else {
+      c0 = cell_of(f2_add(F2{sh.x, sl.x}, f2_mul(r, n[0])), n[0].hi);
+      c1 = cell_of(f2_add(F2{sh.y, sl.y}, f2_mul(r, n[1])), n[1].hi);
+      c2 = cell_of(f2_add(F2{sh.z, sl.z}, f2_mul(r, n[2])), n[2].hi);
+      if (!inside()) return false;
+    }
     t0 = next_t(c0, sh.x, sl.x, iv0);
     t1 = next_t(c1, sh.y, sl.y, iv1);
     t2 = next_t(c2, sh.z, sl.z, iv2);
     return true;
   }
-  __device__ __forceinline__ bool start(const TraceArgs& A) {
+  __device__ __forceinline__ void bind(const TraceArgs& A) {
     const InstDev& I = A.inst[A.src[src].inst];
     nhi = (const float*)I.nhi;
     K = (float*)I.K;
@@ -484,33 +556,63 @@ struct Walk32 {
     level = (level & ~512u) | ((I.flags & kInstNhiPair) ? 512u : 0u);
     Pstart = P;
     steps = 0;
+  }
+  __device__ __forceinline__ bool start(const TraceArgs& A) {
+    bind(A);
     if (!start_geom(A)) return false;
     load_nh(cell_index());
     return true;
+  }
+  // A package continued from the previous trace: the cell it halted in.
+  __device__ __forceinline__ void resume(const TraceArgs& A, uint32_t cell) {
+    bind(A);
+    start_geom<true>(A, cell);
+    load_nh(cell_index());
+  }
+  __device__ __forceinline__ void set_rlim(const TraceArgs& A) {
+    if ((int)age < A.n_ages) {
+      const float2 v = __ldg(&A.rlim32[age]);
+      rlim = F2{v.x, v.y};
+    } else {
+      set_status(A.ctl, RT_ERR_STATE);
+      rlim = F2{0.0f, 0.0f};
+    }
   }
 
   __device__ __forceinline__ void load(const Rec& q) {
     r = {q.r, q.r_lo}; P = q.P; tau = q.tau; tau_lo = q.tau_lo; tau_err = q.tau_err; src = q.src; pix = q.pix;
     level = q.tag & 15u;
+    age = q.age;
   }
-  // Record of child cpix (level + 1, P/4, same radius, optical depth and its
-  // error bound); the level sits in the tag's low bits until publication.
+  // Record of child cpix (level + 1, P/4, same radius, age, optical depth and
+  // its error bound); the level sits in the tag's low bits until publication.
   __device__ __forceinline__ Rec make_child(uint32_t cpix) const {
     Rec c;
     c.r = r.hi; c.r_lo = r.lo; c.P = P * 0.25f; c.tau = tau; c.tau_lo = tau_lo; c.tau_err = tau_err;
-    c.src = src; c.pix = cpix; c.tag = (uint32_t)(lvl() + 1);
+    c.src = src; c.pix = cpix; c.tag = (uint32_t)(lvl() + 1); c.age = age;
     return c;
+  }
+  __device__ __forceinline__ static uint32_t cell_of_record(const Rec& q) { return q.cell; }
+  // A halted package as the next trace continues it (one trace older).
+  __device__ __forceinline__ void store_halted(Rec* q) const {
+    reinterpret_cast<float4*>(&q->r)[0] = make_float4(r.hi, r.lo, P, tau);
+    reinterpret_cast<uint4*>(&q->tau_lo)[0] =
+        make_uint4(__float_as_uint(tau_lo), __float_as_uint(tau_err), src, pix);
+    reinterpret_cast<uint4*>(&q->tag)[0] = make_uint4((uint32_t)lvl(), age + 1, (uint32_t)cell_index(), 0u);
   }
   // Publish a record in the global queue: payload first, then the tag
   // ((epoch << 4) | level) with release semantics.
+  template <bool FSL>
   __device__ __forceinline__ static void publish(Rec* q, const Rec& c, uint32_t epoch) {
     __stcg(reinterpret_cast<float4*>(&q->r), make_float4(c.r, c.r_lo, c.P, c.tau));
     __stcg(reinterpret_cast<uint4*>(&q->tau_lo),
            make_uint4(__float_as_uint(c.tau_lo), __float_as_uint(c.tau_err), c.src, c.pix));
+    if (FSL) __stcg(&q->age, c.age);
     st_release_u32(&q->tag, (epoch << 4) | (c.tag & 15u));
   }
   // Poll with a relaxed load; only a successful poll pays for the fence that
   // orders the payload reads after the tag.
+  template <bool FSL>
   __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
     const uint32_t tg = ld_relaxed_u32(&q->tag);
     if ((tg >> 4) != (epoch & 0x0fffffffu)) return false;
@@ -519,12 +621,14 @@ struct Walk32 {
     const uint4 b = __ldcg(reinterpret_cast<const uint4*>(&q->tau_lo));
     o.r = a.x; o.r_lo = a.y; o.P = a.z; o.tau = a.w;
     o.tau_lo = __uint_as_float(b.x); o.tau_err = __uint_as_float(b.y); o.src = b.z; o.pix = b.w; o.tag = tg;
+    o.age = FSL ? __ldcg(&q->age) : 0u;
     return true;
   }
   __device__ __forceinline__ static Rec root_rec(uint32_t gsrc, uint32_t l, uint32_t p) {
     Rec c;
     c.r = 0.0f; c.r_lo = 0.0f; c.P = 1.0f; c.tau = 0.0f; c.tau_lo = 0.0f; c.tau_err = 0.0f; c.src = gsrc; c.pix = p;
     c.tag = l;
+    c.age = 0u;
     return c;
   }
   __device__ __forceinline__ void become_child0() {
@@ -532,9 +636,11 @@ struct Walk32 {
   }
 
   // The next crossing as the FP64 evaluation takes it: bits 0-2 the planes
-  // crossed, bit 3 a split first, bits 4-5 the axis of the smallest pair;
-  // rn_out receives the crossing distance.  Orders the pairs cannot prove are
-  // re-taken in FP64 (decide64) and counted in fb.
+  // crossed, bit 3 a split first, bits 4-5 the axis of the smallest pair,
+  // bit 6 (FSL) the crossing lies beyond the halting radius; rn_out receives
+  // the crossing distance.  Orders the pairs cannot prove are re-taken in
+  // FP64 (decide64) and counted in fb.
+  template <bool FSL>
   __device__ __forceinline__ int decide(const TraceArgs& A, F2& rn_out, unsigned& fb) const {
     // next crossing: the smallest pair, and whether the order is provable
     int imin = 0;
@@ -552,7 +658,11 @@ struct Walk32 {
     const bool can_split = l < A.max_level;
     const bool split_close = can_split && !(rn.hi > fmaf(R, kClose, R)) && !(rn.hi < fmaf(R, -kClose, R));
     bool split = can_split && rn.hi > R;
-    if (c_0 || c_1 || c_2 || split_close) {
+    // Step 3j: the crossing against the halting radius, decided like the split
+    bool halt = FSL && rn.hi > rlim.hi;
+    const bool halt_close = FSL && !(rn.hi > fmaf(rlim.hi, kClose, rlim.hi)) &&
+                            !(rn.hi < fmaf(rlim.hi, -kClose, rlim.hi));
+    if (c_0 || c_1 || c_2 || split_close || halt_close) {
       // a close pair: compare exactly, re-take the decision in FP64 if unprovable
       const float emin = band(A, rn, imin);
       const bool xy_tie = diag_exact() && f2_eq(t0, t1);
@@ -566,9 +676,19 @@ struct Walk32 {
         else if (-d > bnd) split = false;
         else unsure = true;
       }
+      if (halt_close) {
+        const float d = f2_diff(rn, rlim);
+        const float bnd = emin + rlim.hi * kBandT;
+        if (d > bnd) halt = true;
+        else if (-d > bnd) halt = false;
+        else unsure = true;
+      }
       if (unsure) {
-        const int d64 = decide64(A, src, l, pix, c0, c1, c2);
+        const double rlim64 = !FSL ? __longlong_as_double(0x7ff0000000000000LL)
+                                   : ((int)age < A.n_ages ? A.rlim64[age] : 0.0);
+        const int d64 = decide64(A, src, l, pix, c0, c1, c2, rlim64);
         split = (d64 & 8) != 0;
+        halt = (d64 & 64) != 0;
         m0 = (d64 & 1) != 0;
         m1 = (d64 & 2) != 0;
         m2 = (d64 & 4) != 0;
@@ -576,7 +696,7 @@ struct Walk32 {
       }
     }
     rn_out = rn;
-    return (m0 ? 1 : 0) | (m1 ? 2 : 0) | (m2 ? 4 : 0) | (split ? 8 : 0) | (imin << 4);
+    return (m0 ? 1 : 0) | (m1 ? 2 : 0) | (m2 ? 4 : 0) | (split ? 8 : 0) | (imin << 4) | (halt ? 64 : 0);
   }
   // Cross the planes of `m` (bits 0-2) at distance rn.
   // The first crossed axis is selected rather than branched on, so the lanes
@@ -603,16 +723,18 @@ struct Walk32 {
     r = rn;
   }
 
+  template <bool FSL>
   __device__ __forceinline__ int step(const TraceArgs& A, LaneAcc& acc) {
     F2 rn;
     unsigned fb = 0;
-    const int m = decide(A, rn, fb);
+    const int m = decide<FSL>(A, rn, fb);
     acc.fallbacks += fb;
     const int l = lvl();
     if (m & 8) return EV_SPLIT;
+    const bool halt = FSL && (m & 64);  // Step 3j: the segment ends at rlim
     // segment length, kappa = sigma dx n_HI and dtau as FP32 pairs: the
     // optical depth (pair) follows the FP64 sum to ~2^-44 where n_HI is a pair
-    F2 dr2 = f2_sub(rn, r);
+    F2 dr2 = f2_sub(halt ? rlim : rn, r);
     if (dr2.hi < 0.0f) dr2 = F2{0.0f, 0.0f};
     const float dr = dr2.hi;
     const int idx = cell_index();
@@ -672,8 +794,11 @@ struct Walk32 {
       const float bnd = tau_err + tau * (4.0f * kBandT) + 1e-30f;
       bool term = d > bnd;
       if (!term && !(-d > bnd)) {
-        // too close to call: the lineage's optical depth in FP64
-        const double t64 = retrace_tau64(A, src, l, pix, c0, c1, c2);
+        // too close to call: the lineage's optical depth in FP64 (a lineage
+        // emitted in an earlier trace crossed other media, and a cut segment
+        // is not the cell's: there the pair's own decision stands)
+        const double t64 = (!FSL || (age == 0 && !halt)) ? retrace_tau64(A, src, l, pix, c0, c1, c2)
+                                                         : __longlong_as_double(0x7ff8000000000000LL);
         acc.fallbacks_tau++;
         term = isnan(t64) ? (d > 0.0f) : (t64 > A.tau_term);
       }
@@ -686,6 +811,13 @@ struct Walk32 {
         acc.absorbed += (double)Pstart * unit(A);
         return EV_DONE;
       }
+    }
+    if (halt) {
+      r = rlim;
+      const double u = unit(A);
+      acc.absorbed += ((double)Pstart - (double)P) * u;
+      acc.halted += (double)P * u;
+      return EV_HALT;
     }
     advance(A, m, rn);
     if (!inside()) {
@@ -716,25 +848,25 @@ struct Walk32 {
 // ---------------------------------------------------------------------------
 // The persistent kernel, generic over the walker.
 // ---------------------------------------------------------------------------
-template <class W, int MinBlocks>
+template <class W, int MinBlocks, bool FSL>
 __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   using Rec = typename W::Rec;
   __shared__ unsigned int sh_cnt[kShInst * kLevels];
   __shared__ unsigned long long sh_hsh[kShInst * kLevels];
   __shared__ LaneAcc sh_acc[kBlock];
-  __shared__ double sh_bsum[kShInst * 3];
+  __shared__ double sh_bsum[kShInst * kAcc];
   __shared__ unsigned long long sh_bseg[kShInst];
   __shared__ unsigned int sh_bfb[kShInst * 2];
   for (int i = threadIdx.x; i < kShInst * kLevels; i += blockDim.x) {
     sh_cnt[i] = 0;
     sh_hsh[i] = 0;
   }
-  for (int i = threadIdx.x; i < kShInst * 3; i += blockDim.x) sh_bsum[i] = 0.0;
+  for (int i = threadIdx.x; i < kShInst * kAcc; i += blockDim.x) sh_bsum[i] = 0.0;
   for (int i = threadIdx.x; i < kShInst * 2; i += blockDim.x) sh_bfb[i] = 0u;
   for (int i = threadIdx.x; i < kShInst; i += blockDim.x) sh_bseg[i] = 0ULL;
   const BlockBudget BB{sh_bsum, sh_bseg, sh_bfb};
   LaneAcc& acc = sh_acc[threadIdx.x];
-  acc.emitted = acc.absorbed = acc.escaped = 0.0;
+  acc.emitted = acc.absorbed = acc.escaped = acc.resumed = acc.halted = 0.0;
   acc.segments = acc.fallbacks = acc.fallbacks_tau = 0;
   acc.inst = -1;
   __syncthreads();
@@ -744,6 +876,13 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   const unsigned lt_mask = (1u << lane) - 1u;
   const uint32_t epoch = (uint32_t)A.ctl[CTL_EPOCH];
   Rec* queue = (Rec*)A.queue;
+  // tickets: roots [0, n_roots), packages in flight [n_roots, qbase), queue slots after
+  unsigned long long res_a = 0, n_res = 0;
+  if (FSL) {
+    res_a = A.ctl[CTL_RES_A];
+    n_res = A.ctl[CTL_RES_B] - res_a;
+  }
+  const unsigned long long qbase = A.n_roots + n_res;
 
   W w;
   w.nseg = 0;
@@ -768,21 +907,31 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
     int ev = EV_NONE;
     if (!active && ticket >= 0) {
       const unsigned long long tk = (unsigned long long)ticket;
-      bool got = false;
+      bool got = false, resumed = false;
+      uint32_t cell = 0;
       if (tk < A.n_roots) {
-        const uint32_t gsrc = (uint32_t)(tk / A.npix0);
-        const uint32_t p = (uint32_t)(tk - (unsigned long long)gsrc * A.npix0);
+        const uint32_t ls = (uint32_t)(tk / A.npix0);
+        const uint32_t p = (uint32_t)(tk - (unsigned long long)ls * A.npix0);
+        const uint32_t gsrc = (uint32_t)A.src_first + ls;
         w.load(W::root_rec(gsrc, (uint32_t)A.level0, p));
         got = true;
         const SourceDev& S = A.src[gsrc];
         acc_switch(acc, w.nseg, S.inst, A, BB);
-        acc.emitted += S.unit;
+        if (FSL) acc.emitted += w.emit(S) * S.unit;
+        else acc.emitted += S.unit;
         LC.add(A, S.inst, S.local, A.level0, p, 1);
+      } else if (FSL && tk < qbase) {
+        // a package halted by the previous trace continues from its cell
+        const Rec* in = (const Rec*)A.res_in + (res_a + (tk - A.n_roots));
+        const Rec q = *in;
+        w.load(q);
+        cell = W::cell_of_record(q);
+        got = resumed = true;
       } else {
-        const unsigned long long slot = tk - A.n_roots;
+        const unsigned long long slot = tk - qbase;
         if (slot < A.cap) {
           Rec q;
-          if (W::poll(&queue[slot], epoch, q)) {
+          if (W::template poll<FSL>(&queue[slot], epoch, q)) {
             w.load(q);
             got = true;
           }
@@ -792,7 +941,11 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         ticket = -1;
         active = true;
         acc_switch(acc, w.nseg, w.inst(A), A, BB);
-        if (!w.start(A)) {
+        if (FSL) w.set_rlim(A);
+        if (FSL && resumed) {
+          acc.resumed += (double)w.P * w.unit(A);
+          w.resume(A, cell);
+        } else if (!w.start(A)) {
           w.on_start_outside(A, acc);
           ev = EV_DONE;
         }
@@ -821,8 +974,25 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
     // (4) trace a few segments
     if (active && ev == EV_NONE) {
       for (int it = 0; it < A.segs_per_iter; ++it) {
-        ev = w.step(A, acc);
+        ev = w.template step<FSL>(A, acc);
         if (ev != EV_NONE) break;
+      }
+    }
+    // (4b) halted packages go to the output store (one atomic per warp);
+    //      from here on they are finished packages
+    if (FSL) {
+      const unsigned hm = __ballot_sync(kFull, ev == EV_HALT);
+      if (hm) {
+        const int leader = __ffs(hm) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(&A.ctl[CTL_HALTED], (unsigned long long)__popc(hm));
+        base = __shfl_sync(kFull, base, leader);
+        if (ev == EV_HALT) {
+          const unsigned long long slot = base + __popc(hm & lt_mask);
+          if (slot < A.halt_cap) w.store_halted((Rec*)A.halt_out + slot);
+          else set_status(A.ctl, RT_ERR_QUEUE_OVERFLOW);
+          ev = EV_DONE;
+        }
       }
     }
     // (5) splits reserve 3 slots per splitting lane, publish children 1-3 and
@@ -861,7 +1031,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         unsigned dropped = 0;
         for (uint32_t k = 1; k < 4; ++k) {
           const unsigned long long slot = my + (k - 1);
-          if (slot < A.cap) W::publish(&queue[slot], w.make_child(4u * w.pix + k), epoch);
+          if (slot < A.cap) W::template publish<FSL>(&queue[slot], w.make_child(4u * w.pix + k), epoch);
           else ++dropped;
         }
         if (dropped) {
@@ -901,6 +1071,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         acc.emitted += o.emitted;
         acc.absorbed += o.absorbed;
         acc.escaped += o.escaped;
+        acc.resumed += o.resumed;
+        acc.halted += o.halted;
         acc.segments += o.segments;
         acc.fallbacks += o.fallbacks;
         acc.fallbacks_tau += o.fallbacks_tau;
@@ -917,9 +1089,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   __syncthreads();
   for (int i = threadIdx.x; i < kShInst && i < A.ninst; i += blockDim.x) {
     const InstDev& I = A.inst[i];
-    if (sh_bsum[3 * i] != 0.0) atomicAdd(&I.acc[0], sh_bsum[3 * i]);
-    if (sh_bsum[3 * i + 1] != 0.0) atomicAdd(&I.acc[1], sh_bsum[3 * i + 1]);
-    if (sh_bsum[3 * i + 2] != 0.0) atomicAdd(&I.acc[2], sh_bsum[3 * i + 2]);
+    for (int k = 0; k < kAcc; ++k)
+      if (sh_bsum[kAcc * i + k] != 0.0) atomicAdd(&I.acc[k], sh_bsum[kAcc * i + k]);
     if (sh_bseg[i]) atomicAdd(&I.cnt[kCntSegments], sh_bseg[i]);
     if (sh_bfb[2 * i]) atomicAdd(&I.cnt[kCntFallbacks], (unsigned long long)sh_bfb[2 * i]);
     if (sh_bfb[2 * i + 1]) atomicAdd(&I.cnt[kCntFallbacksTau], (unsigned long long)sh_bfb[2 * i + 1]);
@@ -933,50 +1104,89 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   }
 }
 
-// Resets the queue for one pass.  A trace may run as several passes over
-// ranges of its sources; the status of earlier passes stays (the first error
-// wins) and their queue use is folded into CTL_PEAK / CTL_PUSHED.
-__global__ void trace_init_kernel(unsigned long long* ctl, unsigned long long n_roots, int first_pass) {
+// Resets the queue for pass `pass` of `passes`.  A trace may run as several
+// passes over ranges of its sources; the status of earlier passes stays (the
+// first error wins) and their queue use is folded into CTL_PEAK / CTL_PUSHED.
+// Packages in flight (finite speed of light): at the first pass, mode
+// FLIGHT_ADVANCE takes what the previous trace halted (at most in_cap
+// records were stored) as this trace's input; every pass continues an equal
+// share of them.
+__global__ void trace_init_kernel(unsigned long long* ctl, unsigned long long n_roots, int first_pass, int mode,
+                                  unsigned long long in_cap, int pass, int passes) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     if (first_pass) {
       ctl[CTL_STATUS] = 0;
       ctl[CTL_PEAK] = 0;
       ctl[CTL_PUSHED] = 0;
+      if (mode == FLIGHT_OFF) ctl[CTL_RESUME] = 0;
+      else if (mode == FLIGHT_ADVANCE) ctl[CTL_RESUME] = ctl[CTL_HALTED] < in_cap ? ctl[CTL_HALTED] : in_cap;
+      ctl[CTL_HALTED] = 0;
     } else {
       const unsigned long long t = ctl[CTL_TAIL];
       if (t > ctl[CTL_PEAK]) ctl[CTL_PEAK] = t;
       ctl[CTL_PUSHED] += t;
     }
+    const unsigned long long nr = ctl[CTL_RESUME];
+    const unsigned long long a = nr * (unsigned long long)pass / (unsigned long long)passes;
+    const unsigned long long b = nr * (unsigned long long)(pass + 1) / (unsigned long long)passes;
+    ctl[CTL_RES_A] = a;
+    ctl[CTL_RES_B] = b;
     ctl[CTL_HEAD] = 0;
     ctl[CTL_TAIL] = 0;
-    ctl[CTL_OUTSTANDING] = n_roots;
+    ctl[CTL_OUTSTANDING] = n_roots + (b - a);
     ctl[CTL_EPOCH] = ctl[CTL_EPOCH] + 1;
   }
 }
 
 // Host-side launch helpers (called from api.cu).
-cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass,
-                              cudaStream_t st) {
-  trace_init_kernel<<<1, 32, 0, st>>>(ctl, n_roots, first_pass);
+cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass, int mode,
+                              unsigned long long in_cap, int pass, int passes, cudaStream_t st) {
+  trace_init_kernel<<<1, 32, 0, st>>>(ctl, n_roots, first_pass, mode, in_cap, pass, passes);
+  return cudaGetLastError();
+}
+
+// Halting radii of the next trace from those of the previous one (finite
+// speed of light): neu[0] = c_dt, neu[a] = old[a - 1] + c_dt, FP64, and
+// their FP32 pairs.
+__global__ void flight_table_kernel(const double* old, double* neu, float2* neu32, int n_new, double c_dt) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n_new; a += gridDim.x * blockDim.x) {
+    const double v = a == 0 ? c_dt : __dadd_rn(old[a - 1], c_dt);
+    neu[a] = v;
+    const float hi = __double2float_rn(v);
+    neu32[a] = make_float2(hi, __double2float_rn(__dsub_rn(v, (double)hi)));
+  }
+}
+
+cudaError_t launch_flight_table(const double* old, double* neu, float2* neu32, int n_new, double c_dt,
+                                cudaStream_t st) {
+  flight_table_kernel<<<(n_new + 255) / 256, 256, 0, st>>>(old, neu, neu32, n_new, c_dt);
   return cudaGetLastError();
 }
 
 constexpr int kMinBlocks64 = 2;
 constexpr int kMinBlocks32 = TRACE_MIN_BLOCKS;
 
-cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm) {
+cudaError_t trace_occupancy(int precision, int fsl, int block, int* blocks_per_sm) {
   if (block != kBlock) return cudaErrorInvalidValue;
   if (precision == RT_FP64)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<Walk64, kMinBlocks64>,
-                                                         block, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<Walk32, kMinBlocks32>, block,
-                                                       0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm,
+        fsl ? trace_kernel<Walk64, kMinBlocks64, true> : trace_kernel<Walk64, kMinBlocks64, false>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      blocks_per_sm, fsl ? trace_kernel<Walk32, kMinBlocks32, true> : trace_kernel<Walk32, kMinBlocks32, false>,
+      block, 0);
 }
 
-cudaError_t launch_trace(int precision, const TraceArgs& A, int grid, int block, cudaStream_t st) {
+// fsl: the finite-speed-of-light instantiation (A.rlim*, res_in, halt_out set)
+cudaError_t launch_trace(int precision, int fsl, const TraceArgs& A, int grid, int block, cudaStream_t st) {
   if (block != kBlock) return cudaErrorInvalidValue;
-  if (precision == RT_FP64) trace_kernel<Walk64, kMinBlocks64><<<grid, block, 0, st>>>(A);
-  else trace_kernel<Walk32, kMinBlocks32><<<grid, block, 0, st>>>(A);
+  if (precision == RT_FP64) {
+    if (fsl) trace_kernel<Walk64, kMinBlocks64, true><<<grid, block, 0, st>>>(A);
+    else trace_kernel<Walk64, kMinBlocks64, false><<<grid, block, 0, st>>>(A);
+  } else {
+    if (fsl) trace_kernel<Walk32, kMinBlocks32, true><<<grid, block, 0, st>>>(A);
+    else trace_kernel<Walk32, kMinBlocks32, false><<<grid, block, 0, st>>>(A);
+  }
   return cudaGetLastError();
 }
 

@@ -55,7 +55,8 @@ class rt_trace_params(ctypes.Structure):
     _fields_ = [("level0", ctypes.c_int), ("phi_c", ctypes.c_double), ("f_term", ctypes.c_double),
                 ("max_level", ctypes.c_int), ("queue_capacity", ctypes.c_int64),
                 ("timeout_s", ctypes.c_double), ("blocks_per_sm", ctypes.c_int),
-                ("segs_per_iter", ctypes.c_int), ("flags", ctypes.c_int), ("passes", ctypes.c_int)]
+                ("segs_per_iter", ctypes.c_int), ("flags", ctypes.c_int), ("passes", ctypes.c_int),
+                ("light_cm", ctypes.c_double)]
 
 
 class rt_budget(ctypes.Structure):
@@ -65,7 +66,20 @@ class rt_budget(ctypes.Structure):
                 ("fallbacks", ctypes.c_uint64), ("fallbacks_tau", ctypes.c_uint64),
                 ("queue_pushed", ctypes.c_uint64),
                 ("status", ctypes.c_int), ("kernel_ms", ctypes.c_float),
-                ("queue_peak", ctypes.c_uint64), ("passes", ctypes.c_int)]
+                ("queue_peak", ctypes.c_uint64), ("passes", ctypes.c_int),
+                ("resumed", ctypes.c_double), ("halted", ctypes.c_double),
+                ("n_resumed", ctypes.c_uint64), ("n_halted", ctypes.c_uint64)]
+
+
+class rt_flight(ctypes.Structure):
+    _fields_ = [("r_cm", ctypes.c_double), ("P", ctypes.c_double), ("tau", ctypes.c_double),
+                ("src", ctypes.c_int32), ("level", ctypes.c_int32), ("pix", ctypes.c_uint32),
+                ("age", ctypes.c_uint32), ("cell", ctypes.c_int32 * 3), ("pad", ctypes.c_int32)]
+
+
+# numpy view of an rt_flight array
+FLIGHT_DTYPE = np.dtype([("r_cm", "<f8"), ("P", "<f8"), ("tau", "<f8"), ("src", "<i4"), ("level", "<i4"),
+                         ("pix", "<u4"), ("age", "<u4"), ("cell", "<i4", (3,)), ("pad", "<i4")])
 
 
 class rt_noalloc_grid(ctypes.Structure):
@@ -102,6 +116,8 @@ def lib():
             "rt_set_rates": ([vp, vp, vp, i, i], i),
             "rt_timestep": ([vp, d, d, d, d, d, d, ctypes.POINTER(d)], i),
             "rt_set_source_offset": ([vp, i], i),
+            "rt_set_source_rates": ([vp, i, vp], i),
+            "rt_get_in_flight": ([vp, vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)], i),
             "rt_synchronize": ([vp], i),
             "rt_selfcheck_directions": ([vp, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
             "rt_kernel_launches": ([], ctypes.c_uint64),
@@ -200,11 +216,11 @@ def rt_clear_sources(grid):
 
 def trace_params(level0=1, phi_c=5.1, f_term=1e-10, max_level=RT_MAX_LEVEL, queue_capacity=0,
                  timeout_s=2.0, blocks_per_sm=0, segs_per_iter=0, checksums=False,
-                 passes=0, fc=False) -> rt_trace_params:
+                 passes=0, fc=False, light_cm=0.0) -> rt_trace_params:
     return rt_trace_params(int(level0), float(phi_c), float(f_term), int(max_level),
                            int(queue_capacity), float(timeout_s), int(blocks_per_sm),
                            int(segs_per_iter), (RT_TRACE_CHECKSUMS if checksums else 0) | (RT_TRACE_FC if fc else 0),
-                           int(passes))
+                           int(passes), float(light_cm))
 
 
 def budget_dict(b: rt_budget) -> dict:
@@ -214,7 +230,8 @@ def budget_dict(b: rt_budget) -> dict:
                 fallbacks=int(b.fallbacks), fallbacks_tau=int(b.fallbacks_tau),
                 queue_pushed=int(b.queue_pushed), queue_peak=int(b.queue_peak), passes=int(b.passes),
                 status=int(b.status),
-                kernel_ms=float(b.kernel_ms))
+                kernel_ms=float(b.kernel_ms), resumed=float(b.resumed), halted=float(b.halted),
+                n_resumed=int(b.n_resumed), n_halted=int(b.n_halted))
 
 
 def rt_trace(grid, params: rt_trace_params, sync: bool = True):
@@ -241,6 +258,21 @@ def rt_set_state(grid, x_HI, x_HII=None, n_H=None):
 
 def rt_set_source_offset(grid, first: int):
     check(lib().rt_set_source_offset(grid, int(first)))
+
+
+def rt_set_source_rates(grid, ndot):
+    nd = np.ascontiguousarray(ndot, dtype=np.float64).reshape(-1)
+    check(lib().rt_set_source_rates(grid, nd.size, nd.ctypes.data))
+
+
+def rt_get_in_flight(grid) -> np.ndarray:
+    """Packages in flight after the last trace, as a FLIGHT_DTYPE array."""
+    n = ctypes.c_uint64()
+    check(lib().rt_get_in_flight(grid, None, 0, ctypes.byref(n)))
+    out = np.zeros(int(n.value), dtype=FLIGHT_DTYPE)
+    if out.size:
+        check(lib().rt_get_in_flight(grid, out.ctypes.data, out.size, ctypes.byref(n)))
+    return out
 
 
 def rt_set_rates(grid, kph, gamma):
@@ -328,6 +360,12 @@ class Grid:
 
     def chem(self, dt_s, nsub=10, alpha_B=2.59e-13):
         rt_chem_update(self.h, dt_s, nsub, alpha_B)
+
+    def set_source_rates(self, ndot):
+        rt_set_source_rates(self.h, ndot)
+
+    def in_flight(self) -> np.ndarray:
+        return rt_get_in_flight(self.h)
 
     def rates(self, dtype=RT_DTYPE_F64, where="host"):
         return rt_get_rates(self.h, self.ncell, dtype, where)

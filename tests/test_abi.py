@@ -31,8 +31,11 @@ int main(void) {
          offsetof(rt_grid_desc, n_H), offsetof(rt_grid_desc, x_HII));
   printf("%zu %zu %zu %zu\n", sizeof(rt_trace_params), offsetof(rt_trace_params, phi_c),
          offsetof(rt_trace_params, queue_capacity), offsetof(rt_trace_params, segs_per_iter));
-  printf("%zu %zu %zu %zu %zu\n", sizeof(rt_budget), offsetof(rt_budget, counts),
-         offsetof(rt_budget, segments), offsetof(rt_budget, status), offsetof(rt_budget, passes));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(rt_budget), offsetof(rt_budget, counts),
+         offsetof(rt_budget, segments), offsetof(rt_budget, status), offsetof(rt_budget, passes),
+         offsetof(rt_budget, n_halted));
+  printf("%zu %zu\n", sizeof(rt_trace_params), offsetof(rt_trace_params, light_cm));
+  printf("%zu %zu %zu\n", sizeof(rt_flight), offsetof(rt_flight, src), offsetof(rt_flight, cell));
   return 0;
 }
 """)
@@ -43,7 +46,12 @@ int main(void) {
     D, T, B = native.rt_grid_desc, native.rt_trace_params, native.rt_budget
     assert got[0] == [ctypes.sizeof(D), D.box_len_cm.offset, D.n_H.offset, D.x_HII.offset]
     assert got[1] == [ctypes.sizeof(T), T.phi_c.offset, T.queue_capacity.offset, T.segs_per_iter.offset]
-    assert got[2] == [ctypes.sizeof(B), B.counts.offset, B.segments.offset, B.status.offset, B.passes.offset]
+    assert got[2] == [ctypes.sizeof(B), B.counts.offset, B.segments.offset, B.status.offset, B.passes.offset,
+                      B.n_halted.offset]
+    assert got[3] == [ctypes.sizeof(T), T.light_cm.offset]
+    F = native.rt_flight
+    assert got[4] == [ctypes.sizeof(F), F.src.offset, F.cell.offset]
+    assert native.FLIGHT_DTYPE.itemsize == ctypes.sizeof(F)
 
 
 def test_error_message_without_gpu_is_reported_not_raised_from_c():
