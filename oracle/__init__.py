@@ -15,6 +15,8 @@ contraction); this module only builds it and marshals numpy arrays:
   Gamma per cell (Eqs. "dtau", "flux", "kph", "gamma"), the photon budget,
   packages created per HEALPix level and a checksum of the created set.
 * ``chem`` -- backward-Euler update of Eq. "dndt" (hydrogen only).
+* ``trace(..., src_type=, n_he=)`` -- photon types (Sec. 3.2): H I, He I
+  and He II ionising packages, each absorbed by its own species.
 * ``Flight`` / ``trace(..., flight=, light_cm=)`` -- finite speed of light
   (Sec. 2.1, Step 3j): packages halt after travelling c dt_P in a trace and
   continue in the next one.
@@ -68,6 +70,9 @@ def _load():
             lib.orc_trace_fsl.argtypes = [p, d, p, p, i, p, p, p, p, i, d, d, i, p, p, p, p, p, p, i, i,
                                           i, p, ctypes.c_size_t, p, ctypes.c_size_t, p, p]
             lib.orc_trace_fsl.restype = i
+            lib.orc_trace_mf.argtypes = [p, d, p, p, p, i, p, p, p, p, p, i, d, d, i, p, p, p, p, p, p, i, i,
+                                         i, p, ctypes.c_size_t, p, ctypes.c_size_t, p, p]
+            lib.orc_trace_mf.restype = i
             lib.orc_chem.argtypes = [ctypes.c_size_t, p, p, p, p, d, i, d]
             lib.orc_chem.restype = None
             _lib = lib
@@ -170,7 +175,7 @@ class Flight:
 def trace(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, *,
           level0: int = 1, phi_c: float = 5.1, f_term: float = 1e-10,
           max_level: int = MAX_LEVEL, fc: bool = False, src_offset: int = 0,
-          flight: Flight = None, light_cm: float = 0.0) -> dict:
+          flight: Flight = None, light_cm: float = 0.0, src_type=None, n_he=None) -> dict:
     """One radiative-transfer pass (Steps 1-5).  Cell index = i + nx*(j + ny*k).
 
     Returns dict(kph, gamma (per cell, s^-1 and erg/s), budget=[emitted,
@@ -181,6 +186,12 @@ def trace(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, 
     every package halts where it has travelled c dt_P since its emission, and ``flight`` afterwards holds the halted packages; the result
     adds ``resumed`` and ``halted`` (photons/s) and ``n_halted``.  With
     ``light_cm`` = 0 any packages in ``flight`` are dropped.
+
+    Photon types (Sec. 3.2): ``src_type[s]`` in {0: H I, 1: He I, 2: He II}
+    and ``n_he`` = (n_HeI, n_HeII) per cell; a package is absorbed by its
+    type's species only.  The result then adds ``kph_types`` and
+    ``gamma_types`` of shape (3, ncell); ``kph`` / ``gamma`` stay the H I
+    rates.
     """
     lib = _load()
     dims = np.ascontiguousarray(dims, dtype=np.int32)
@@ -194,8 +205,13 @@ def trace(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, 
     e = _f64(e_ph_eV).reshape(-1)
     sg = _f64(sigma_cm2).reshape(-1)
     assert pos.size == 3 * nsrc and e.size == nsrc and sg.size == nsrc
-    kph = np.empty(ncell)
-    gamma = np.empty(ncell)
+    nt = 3 if n_he is not None else 1
+    he = _f64(n_he).reshape(-1) if n_he is not None else np.zeros(1)
+    assert n_he is None or he.size == 2 * ncell
+    st = np.ascontiguousarray(src_type, dtype=np.int32).reshape(-1) if src_type is not None else None
+    assert st is None or st.size == nsrc
+    kph_all = np.empty(nt * ncell)
+    gamma_all = np.empty(nt * ncell)
     budget = np.empty(5)
     counts = np.zeros(MAX_LEVEL + 1, dtype=np.uint64)
     hashes = np.zeros(MAX_LEVEL + 1, dtype=np.uint64)
@@ -211,20 +227,24 @@ def trace(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, 
     n_out = ctypes.c_size_t(0)
     while True:
         out = np.zeros(cap, dtype=FLIGHT_DTYPE)
-        rc = lib.orc_trace_fsl(_ptr(dims), float(box_len_cm), _ptr(n_H), _ptr(x_HI), int(nsrc), _ptr(pos),
-                               _ptr(ndot), _ptr(e), _ptr(sg), int(level0), float(phi_c), float(f_term),
-                               int(max_level), _ptr(kph), _ptr(gamma), _ptr(budget), _ptr(counts),
-                               _ptr(hashes), _ptr(seg), 1 if fc else 0, int(src_offset),
-                               int(rlim.size) if finite else 0, _ptr(rlim), ctypes.c_size_t(pin.size),
-                               _ptr(pin), ctypes.c_size_t(cap), _ptr(out), ctypes.byref(n_out))
+        rc = lib.orc_trace_mf(_ptr(dims), float(box_len_cm), _ptr(n_H), _ptr(x_HI),
+                              _ptr(he) if n_he is not None else None, int(nsrc), _ptr(pos),
+                              _ptr(ndot), _ptr(e), _ptr(sg), _ptr(st) if st is not None else None,
+                              int(level0), float(phi_c), float(f_term),
+                              int(max_level), _ptr(kph_all), _ptr(gamma_all), _ptr(budget), _ptr(counts),
+                              _ptr(hashes), _ptr(seg), 1 if fc else 0, int(src_offset),
+                              int(rlim.size) if finite else 0, _ptr(rlim), ctypes.c_size_t(pin.size),
+                              _ptr(pin), ctypes.c_size_t(cap), _ptr(out), ctypes.byref(n_out))
         if rc == -2:
             cap = int(n_out.value)
             continue
         break
     if rc != 0:
         raise ValueError("oracle trace rejected its arguments")
-    res = dict(kph=kph, gamma=gamma, budget=budget[:3].copy(), counts=counts, hashes=hashes,
-               segments=int(seg[0]))
+    res = dict(kph=kph_all[:ncell].copy(), gamma=gamma_all[:ncell].copy(), budget=budget[:3].copy(),
+               counts=counts, hashes=hashes, segments=int(seg[0]))
+    if n_he is not None:
+        res.update(kph_types=kph_all.reshape(3, ncell), gamma_types=gamma_all.reshape(3, ncell))
     if finite:
         flight.packages = out[:n_out.value].copy()
         res.update(resumed=float(budget[3]), halted=float(budget[4]), n_halted=int(n_out.value))

@@ -61,6 +61,13 @@
  *      and the package is kept with its cell; the next trace continues it
  *      from that radius and cell through the then current medium.  Children
  *      inherit the age.  Emitted + resumed = absorbed + escaped + halted.
+ *  R16 Photon types (Sec. 3.2, optional): a source emits packages of one
+ *      type -- H I, He I or He II ionising -- and a package of a type is
+ *      absorbed by that type's absorber only (Eq. "dtau" with its n_abs;
+ *      n_HI = n_H x_HI, n_HeI and n_HeII given per cell), deposits into that
+ *      type's k_ph and Gamma, and heats with E_ph - E_i, E_i = 13.6, 24.6,
+ *      54.4 eV.  The helium network that would use these rates is not part
+ *      of the method's hot path; the update stays hydrogen-only.
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC (no FMA
  * contraction, so the rounding of every expression is the one written here).
@@ -73,6 +80,9 @@
 #define ORC_EV_ERG 1.602176634e-12 /* erg per eV (exact by definition) */
 #define ORC_E_HI 13.6              /* hydrogen ionisation threshold, eV (Sec. 2.2) */
 #define ORC_MAX_LEVEL 14           /* pixel numbers at level 14 still fit 32 bits */
+#define ORC_NTYPES 3               /* photon types: H I, He I, He II ionising (Sec. 3.2) */
+/* ionisation energies of the absorbers of the photon types, eV (reading R16) */
+static const double orc_e_ion[ORC_NTYPES] = {ORC_E_HI, 24.6, 54.4};
 
 /* ------------------------------------------------------------------------- */
 /* HEALPix, nested scheme (Gorski et al. 2005), written from the projection   */
@@ -401,7 +411,9 @@ static double orc_fc(const double s[3], const double n[3], double r, double dr, 
 /* Everything one trace needs while it walks packages. */
 typedef struct {
   const int *dims;
-  const double *n_abs;     /* n_H x_HI per cell */
+  size_t ncell;
+  const double *n_abs;     /* absorber density per photon type and cell: [type][cell] (R16) */
+  const int *type;         /* photon type per source (NULL: all H I) */
   double dx, vol, tau_term;
   const double *rsplit;
   int max_level, fc, src_offset;
@@ -426,6 +438,9 @@ static int orc_walk(orc_run *R, orc_stack *st) {
     orc_pkg pk = st->v[--st->n];
     const double *s = R->s + 3 * pk.src;
     const double sigma_dx = R->sigma_cm2[pk.src] * R->dx;
+    const size_t toff = R->type ? (size_t)R->type[pk.src] * R->ncell : 0; /* R16 */
+    const double *n_abs = R->n_abs + toff;
+    double *kph = R->kph + toff, *gamma = R->gamma + toff;
     double rlim = INFINITY;
     if (R->n_ages > 0) {
       if (pk.age >= (uint32_t)R->n_ages) return -1;
@@ -463,15 +478,15 @@ static int orc_walk(orc_run *R, orc_stack *st) {
       if (dr < 0) dr = 0;
       const size_t idx = (size_t)c[0] + (size_t)dims[0] * ((size_t)c[1] + (size_t)dims[1] * (size_t)c[2]);
       /* Step 3f: Eqs. "dtau", "flux", "kph" (reading R5), "gamma" */
-      const double dtau = sigma_dx * R->n_abs[idx] * dr;
+      const double dtau = sigma_dx * n_abs[idx] * dr;
       const double absorbed_frac = -expm1(-dtau);         /* 1 - e^-tau */
       const double dP = pk.P * absorbed_frac;
       const double phi = (dtau > 0) ? absorbed_frac / dtau : 1.0;
       const double f_c =
           R->fc ? orc_fc(s, n, pk.r, dr, c, sqrt(4.0 * M_PI / (12.0 * ldexp(1.0, 2 * (int)pk.level)))) : 1.0;
       const double k_add = pk.P * R->sigma_cm2[pk.src] * (dr * R->dx) * phi / R->vol * f_c;
-      R->kph[idx] += k_add;
-      R->gamma[idx] += k_add * R->heat[pk.src];
+      kph[idx] += k_add;
+      gamma[idx] += k_add * R->heat[pk.src];
       if (dr > 0) ++R->nseg;
       /* Step 3h */
       pk.P -= dP;
@@ -479,9 +494,9 @@ static int orc_walk(orc_run *R, orc_stack *st) {
       orc_kadd(&R->absorbed, dP);
       /* Step 3i (reading R3): absorb the residual in this cell */
       if (pk.tau > R->tau_term) {
-        const double k_res = pk.P / (R->n_abs[idx] * R->vol) * f_c;
-        R->kph[idx] += k_res;
-        R->gamma[idx] += k_res * R->heat[pk.src];
+        const double k_res = pk.P / (n_abs[idx] * R->vol) * f_c;
+        kph[idx] += k_res;
+        gamma[idx] += k_res * R->heat[pk.src];
         orc_kadd(&R->absorbed, pk.P);
         break;
       }
@@ -502,12 +517,16 @@ static int orc_walk(orc_run *R, orc_stack *st) {
 }
 
 /*
- * orc_trace_fsl: one radiative-transfer pass over a uniform grid.
+ * orc_trace_mf: one radiative-transfer pass over a uniform grid.
  *   dims        nx, ny, nz (cells); cell index = i + nx*(j + ny*k)
  *   box_len_cm  length of the x extent; cell width dx = box_len_cm / nx
  *   n_H, x_HI   hydrogen density (cm^-3) and neutral fraction per cell
+ *   n_he        NULL, or [2*ncell]: n_HeI then n_HeII per cell (cm^-3), the
+ *               absorbers of the He I and He II photon types (R16)
  *   nsrc, pos_cm[3*nsrc], ndot[nsrc] (photons/s), e_ph_eV[nsrc],
  *   sigma_cm2[nsrc]
+ *   src_type    NULL (all H I), or [nsrc] photon type 0, 1, 2 (R16; types
+ *               1 and 2 need n_he)
  *   level0, phi_c, f_term, max_level   method parameters (Sec. 2.1)
  *   fc           nonzero: scale the k_ph and Gamma contributions by the
  *                covering factor of Eq. "fc" (photon budget unchanged)
@@ -519,8 +538,9 @@ static int orc_walk(orc_run *R, orc_stack *st) {
  *                          here (photons/s as they were emitted)
  *   out_cap, out           room for the packages this trace halts
  * outputs (overwritten):
- *   kph[ncell]   photo-ionisation rate per absorber, s^-1 (Eq. "kph")
- *   gamma[ncell] photo-heating rate per absorber, erg/s (Eq. "gamma")
+ *   kph[nt*ncell]   photo-ionisation rate per absorber, s^-1 (Eq. "kph"),
+ *                   per photon type (nt = 3 with n_he, else 1)
+ *   gamma[nt*ncell] photo-heating rate per absorber, erg/s (Eq. "gamma")
  *   budget[5]    emitted, absorbed, escaped, resumed, halted photons/s
  *                (Neumaier sums)
  *   counts[ORC_MAX_LEVEL+1]   packages created per level
@@ -530,16 +550,19 @@ static int orc_walk(orc_run *R, orc_stack *st) {
  * returns 0; -1 on a bad argument or allocation failure; -2 when out_cap
  * was too small (*n_out then says how many are needed).
  */
-int orc_trace_fsl(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, int nsrc,
-                  const double *pos_cm, const double *ndot, const double *e_ph_eV, const double *sigma_cm2,
-                  int level0, double phi_c, double f_term, int max_level, double *kph, double *gamma,
-                  double *budget, uint64_t *counts, uint64_t *hashes, uint64_t *segments, int fc, int src_offset,
-                  int n_ages, const double *rlim, size_t n_in, const orc_flight *in, size_t out_cap,
-                  orc_flight *out, size_t *n_out) {
+int orc_trace_mf(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, const double *n_he,
+                 int nsrc, const double *pos_cm, const double *ndot, const double *e_ph_eV, const double *sigma_cm2,
+                 const int *src_type, int level0, double phi_c, double f_term, int max_level, double *kph,
+                 double *gamma, double *budget, uint64_t *counts, uint64_t *hashes, uint64_t *segments, int fc,
+                 int src_offset, int n_ages, const double *rlim, size_t n_in, const orc_flight *in, size_t out_cap,
+                 orc_flight *out, size_t *n_out) {
   if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0 || level0 < 0 || max_level > ORC_MAX_LEVEL ||
       level0 > max_level || !(phi_c > 0) || !(f_term > 0 && f_term < 1) || n_ages < 0 ||
       (n_ages == 0 && n_in > 0))
     return -1;
+  const int nt = n_he ? ORC_NTYPES : 1;
+  for (int i = 0; src_type && i < nsrc; ++i)
+    if (src_type[i] < 0 || src_type[i] >= nt) return -1;
   for (size_t i = 0; i < n_in; ++i)
     if (in[i].src >= (uint32_t)nsrc || in[i].age >= (uint32_t)n_ages || in[i].level > (uint32_t)max_level)
       return -1;
@@ -548,15 +571,18 @@ int orc_trace_fsl(const int dims[3], double box_len_cm, const double *n_H, const
   for (int l = 0; l <= ORC_MAX_LEVEL; ++l) /* Eq. "split": Phi < Phi_c <=> R > R_split */
     rsplit[l] = sqrt((12.0 * ldexp(1.0, 2 * l)) / (4.0 * M_PI * phi_c));
 
-  double *n_abs = (double *)malloc(ncell * sizeof(double));
+  double *n_abs = (double *)malloc((size_t)nt * ncell * sizeof(double));
   double *s = (double *)malloc((size_t)(nsrc > 0 ? nsrc : 1) * 3 * sizeof(double));
   double *heat = (double *)malloc((size_t)(nsrc > 0 ? nsrc : 1) * sizeof(double));
   if (!n_abs || !s || !heat) { free(n_abs); free(s); free(heat); return -1; }
   for (size_t c = 0; c < ncell; ++c) n_abs[c] = n_H[c] * x_HI[c];
+  for (size_t c = 0; nt > 1 && c < 2 * ncell; ++c) n_abs[ncell + c] = n_he[c];
   orc_run R;
   memset(&R, 0, sizeof R);
   R.dims = dims;
+  R.ncell = ncell;
   R.n_abs = n_abs;
+  R.type = src_type;
   R.dx = box_len_cm / dims[0];
   R.vol = R.dx * R.dx * R.dx;
   R.tau_term = -log(f_term); /* reading R3 */
@@ -566,7 +592,7 @@ int orc_trace_fsl(const int dims[3], double box_len_cm, const double *n_H, const
   R.src_offset = src_offset;
   for (int i = 0; i < nsrc; ++i) {
     for (int a = 0; a < 3; ++a) s[3 * i + a] = pos_cm[3 * i + a] / R.dx;
-    heat[i] = (e_ph_eV[i] - ORC_E_HI) * ORC_EV_ERG;
+    heat[i] = (e_ph_eV[i] - orc_e_ion[src_type ? src_type[i] : 0]) * ORC_EV_ERG;
   }
   R.s = s;
   R.sigma_cm2 = sigma_cm2;
@@ -581,7 +607,7 @@ int orc_trace_fsl(const int dims[3], double box_len_cm, const double *n_H, const
   R.out_cap = out_cap;
 
   /* Step 2: zero the radiation fields */
-  for (size_t c = 0; c < ncell; ++c) { kph[c] = 0.0; gamma[c] = 0.0; }
+  for (size_t c = 0; c < (size_t)nt * ncell; ++c) { kph[c] = 0.0; gamma[c] = 0.0; }
   for (int l = 0; l <= ORC_MAX_LEVEL; ++l) { counts[l] = 0; hashes[l] = 0; }
   orc_ksum emitted = {0, 0}, resumed = {0, 0};
 
@@ -622,6 +648,18 @@ int orc_trace_fsl(const int dims[3], double box_len_cm, const double *n_H, const
   *segments = R.nseg;
   *n_out = R.n_out;
   return R.n_out > out_cap ? -2 : 0;
+}
+
+/* orc_trace_fsl: the same pass for H I photons only. */
+int orc_trace_fsl(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, int nsrc,
+                  const double *pos_cm, const double *ndot, const double *e_ph_eV, const double *sigma_cm2,
+                  int level0, double phi_c, double f_term, int max_level, double *kph, double *gamma,
+                  double *budget, uint64_t *counts, uint64_t *hashes, uint64_t *segments, int fc, int src_offset,
+                  int n_ages, const double *rlim, size_t n_in, const orc_flight *in, size_t out_cap,
+                  orc_flight *out, size_t *n_out) {
+  return orc_trace_mf(dims, box_len_cm, n_H, x_HI, NULL, nsrc, pos_cm, ndot, e_ph_eV, sigma_cm2, NULL, level0, phi_c,
+                      f_term, max_level, kph, gamma, budget, counts, hashes, segments, fc, src_offset, n_ages, rlim,
+                      n_in, in, out_cap, out, n_out);
 }
 
 /* orc_trace: the same pass with an infinite speed of light (budget[3]:
