@@ -230,6 +230,33 @@ int rt_set_state(rt_grid* grid, const double* n_H, const double* x_HI, const dou
 int rt_get_rates(rt_grid* grid, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind);
 /* Copy x_HII likewise. */
 int rt_get_ionised(rt_grid* grid, void* x_HII, int dtype, int mem_kind);
+
+/* Photon types (Sec. 3.2).  Packages are monochromatic and of one type,
+ * absorbed by that type's species only (Eq. "dtau" with its n_abs) and
+ * depositing into that type's k_ph and Gamma (Eqs. "kph", "gamma", with
+ * E_ph - E_i):
+ *   RT_PHOTON_HI   0  n_abs = n_H x_HI (the grid state), E_i = 13.6 eV
+ *   RT_PHOTON_HEI  1  n_abs = n_HeI,  E_i = 24.6 eV
+ *   RT_PHOTON_HEII 2  n_abs = n_HeII, E_i = 54.4 eV
+ * Every source starts as RT_PHOTON_HI.  The helium densities are inputs
+ * (the helium network that would evolve them is the caller's);
+ * rt_chem_update stays hydrogen-only and uses the H I rates. */
+#define RT_PHOTON_HI 0
+#define RT_PHOTON_HEI 1
+#define RT_PHOTON_HEII 2
+/* Helium absorber densities n_HeI[ncell], n_HeII[ncell] (cm^-3, finite,
+ * >= 0; x fastest) in memory mem_kind, copied.  The first call allocates
+ * their rates (and FP32 pairs on the mixed path).  Checked on the device
+ * before anything changes (RT_ERR_INVALID_ARG names the first bad cell).
+ * Synchronous. */
+int rt_set_absorbers(rt_grid* grid, const double* n_HeI, const double* n_HeII, int mem_kind);
+/* Photon type of every source (n = number of sources); a source's photon
+ * energy must reach its type's threshold.  Types 1 and 2 need
+ * rt_set_absorbers before the next trace (else RT_ERR_INVALID_ARG). */
+int rt_set_source_types(rt_grid* grid, int n, const int* type);
+/* k_ph (s^-1) and Gamma (erg/s) of photon type `type` per absorber of that
+ * type, as rt_get_rates (type 0 = rt_get_rates' k_ph and Gamma). */
+int rt_get_rates_typed(rt_grid* grid, int type, void* kph, void* gamma, int dtype, int mem_kind);
 /* Adaptive radiative-transfer timestep (Sec. 3.4, Eqs. "dtelec",
  * "dtchange") from the grid's current k_ph and state: per cell
  * eps_ion / |k_ph + n_e alpha_B| (n_e = n_H (1 - x_HI), C_H = 0) in cells

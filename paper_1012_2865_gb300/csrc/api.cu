@@ -35,6 +35,8 @@ cudaError_t launch_timestep(long long n, int nx, int ny, int nz, const double* n
                             float unit, float* dtc, unsigned int* out, cudaStream_t st);
 cudaError_t launch_check_state(long long n, const double* nH, const double* x, unsigned long long* bad,
                                cudaStream_t st);
+cudaError_t launch_check_density(long long n, const double* a, unsigned long long* bad, cudaStream_t st);
+cudaError_t launch_pair(long long n, const double* src, void* dst, cudaStream_t st);
 cudaError_t launch_direction_check(int level, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st);
 cudaError_t launch_batch_zero(const InstDev* inst, int ninst, int precision, long long max_cells, cudaStream_t st);
@@ -166,7 +168,13 @@ struct rt_grid {
   double* acc = nullptr;               // kAccWords doubles
   unsigned long long* cnt = nullptr;   // kCntWords
   InstDev* inst_dev = nullptr;
-  struct SrcIn { double pos[3], ndot, e_ph, sigma; };
+  struct SrcIn { double pos[3], ndot, e_ph, sigma; int type = 0; };
+  // helium absorbers and rates of photon types 1 (He I) and 2 (He II), once set
+  bool he = false;
+  double* nhe64[2] = {nullptr, nullptr};
+  void* nhe[2] = {nullptr, nullptr};  // FP64 grid: nhe64; FP32-mixed: FP32 pairs
+  void* Khe[2] = {nullptr, nullptr};
+  void* Ghe[2] = {nullptr, nullptr};
   std::vector<SrcIn> src;              // sources as given by the caller
   SourceDev* src_dev = nullptr;
   size_t src_dev_cap = 0;
@@ -184,6 +192,10 @@ struct rt_grid {
   ~rt_grid() {
     cudaFree(nH); cudaFree(xHI); cudaFree(xHII); cudaFree(nhi); cudaFree(K); cudaFree(G);
     cudaFree(acc); cudaFree(cnt); cudaFree(inst_dev); cudaFree(src_dev);
+    for (int t = 0; t < 2; ++t) {
+      if (nhe[t] != nhe64[t]) cudaFree(nhe[t]);
+      cudaFree(nhe64[t]); cudaFree(Khe[t]); cudaFree(Ghe[t]);
+    }
     if (host_rb) cudaFreeHost(host_rb);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -191,6 +203,20 @@ struct rt_grid {
 };
 
 static size_t elem_bytes(int precision) { return precision == RT_FP64 ? 8 : 4; }
+
+// The trace kernel's view of a grid (slot `inst` of a launch).
+static InstDev inst_of(const rt_grid* g) {
+  InstDev I;
+  memset(&I, 0, sizeof I);
+  I.nx = g->nx; I.ny = g->ny; I.nz = g->nz;
+  I.flags = g->precision == RT_FP32_MIXED ? kInstNhiPair : 0;
+  I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.xHII = g->xHII; I.K = g->K; I.G = g->G;
+  I.acc = g->acc; I.cnt = g->cnt;
+  for (int t = 0; t < 2; ++t) {
+    I.nhe[t] = g->nhe[t]; I.nhe64[t] = g->nhe64[t]; I.Khe[t] = g->Khe[t]; I.Ghe[t] = g->Ghe[t];
+  }
+  return I;
+}
 
 // A grid in a batch is updated on the batch's stream: per-grid calls first
 // wait for that work.
@@ -313,11 +339,7 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
   e = cudaMemsetAsync(g->ts.ctl, 0, CTL_N * sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->K, 0, ne, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->G, 0, ne, st);
-  InstDev I;
-  I.nx = g->nx; I.ny = g->ny; I.nz = g->nz;
-  I.flags = g->precision == RT_FP32_MIXED ? kInstNhiPair : 0;
-  I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.xHII = g->xHII; I.K = g->K; I.G = g->G; I.acc = g->acc;
-  I.cnt = g->cnt;
+  const InstDev I = inst_of(g);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->inst_dev, &I, sizeof I, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMallocHost(&g->host_rb, 4096);
   if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
@@ -424,7 +446,8 @@ static void build_sources(const rt_grid* g, int level0, int inst, std::vector<So
     memset(&S, 0, sizeof S);
     for (int a = 0; a < 3; ++a) S.s[a] = H.pos[a] / dx;  // cell units
     S.sdx = H.sigma * dx;
-    S.heat = (H.e_ph - kEHI) * kEvErg;
+    S.type = H.type;
+    S.heat = (H.e_ph - kEIon[H.type]) * kEvErg;
     S.unit = unit ? (*unit)[i] : H.ndot / npix0;
     S.p0 = p0 ? (*p0)[i] : 1.0;
     S.w = S.unit * H.sigma / (dx * dx);
@@ -442,7 +465,7 @@ static void build_sources(const rt_grid* g, int level0, int inst, std::vector<So
     }
     S.exact32 = exact && g->nx <= 4096 && g->ny <= 4096 && g->nz <= 4096;
     // the FP32 walker deposits Gamma in eV/s (rt_get_rates converts to erg/s)
-    S.k32 = make_float4((float)S.sdx, (float)S.w, (float)S.rw, (float)(H.e_ph - kEHI));
+    S.k32 = make_float4((float)S.sdx, (float)S.w, (float)S.rw, (float)(H.e_ph - kEIon[H.type]));
     S.s32 = make_float4(s32[0], s32[1], s32[2], S.exact32 ? 1.0f : 0.0f);
     S.slo32 = make_float4(slo[0], slo[1], slo[2], (float)(S.sdx - (double)(float)S.sdx));
     S.sabs32 = make_float4(sab[0], sab[1], sab[2], (float)S.p0);
@@ -681,6 +704,9 @@ static void commit_flight(rt_grid* g, bool fsl);
 
 static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool retry = false) {
   const bool fsl = p->light_cm > 0;
+  for (const rt_grid::SrcIn& S : g->src)
+    if (S.type > 0 && !g->he)
+      return fail(RT_ERR_INVALID_ARG, "rt_trace: helium photon types need rt_set_absorbers first");
   if (retry) {
     g->fl.in = g->fl.in_before;
     g->fl.live = g->fl.live_before;
@@ -694,6 +720,10 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool 
   const size_t ne = (size_t)g->ncell * elem_bytes(g->precision);
   CUDA_TRY(cudaMemsetAsync(g->K, 0, ne, st));  // Step 2
   CUDA_TRY(cudaMemsetAsync(g->G, 0, ne, st));
+  for (int t = 0; t < 2 && g->he; ++t) {
+    CUDA_TRY(cudaMemsetAsync(g->Khe[t], 0, ne, st));
+    CUDA_TRY(cudaMemsetAsync(g->Ghe[t], 0, ne, st));
+  }
   CUDA_TRY(cudaMemsetAsync(g->acc, 0, kAccWords * sizeof(double), st));
   CUDA_TRY(cudaMemsetAsync(g->cnt, 0, kCntWords * sizeof(unsigned long long), st));
   const int nsrc = (int)g->src.size();
@@ -927,6 +957,87 @@ static int copy_field(rt_grid* g, const void* src, int src_dtype, void* dst, int
   return RT_OK;
 }
 
+int rt_set_absorbers(rt_grid* g, const double* n_HeI, const double* n_HeII, int mem_kind) {
+  if (!g || !n_HeI || !n_HeII) return fail(RT_ERR_INVALID_ARG, "rt_set_absorbers: NULL argument");
+  if (int rcw = wait_batch(g)) return rcw;
+  if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE)
+    return fail(RT_ERR_INVALID_ARG, "rt_set_absorbers: mem_kind %d", mem_kind);
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  cudaStream_t st = g->stream;
+  const long long n = g->ncell;
+  const size_t n8 = (size_t)n * 8, ne = (size_t)n * elem_bytes(g->precision);
+  // staged and checked before the grid's arrays change
+  double* stage = nullptr;
+  CUDA_TRY(cudaMallocAsync((void**)&stage, 2 * n8, st));
+  unsigned long long* bad = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&bad, 2 * sizeof(unsigned long long), st);
+  unsigned long long h[2] = {~0ULL, ~0ULL};
+  const cudaMemcpyKind kind = mem_kind == RT_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage, n_HeI, n8, kind, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage + n, n_HeII, n8, kind, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0xff, 2 * sizeof(unsigned long long), st);
+  for (int t = 0; t < 2 && e == cudaSuccess; ++t) {
+    e = launch_check_density(n, stage + t * n, bad + t, st);
+    if (e == cudaSuccess) g_launches.fetch_add(1);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, bad, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(bad, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(stage, st);
+    return fail(RT_ERR_CUDA, "rt_set_absorbers: %s", cudaGetErrorString(e));
+  }
+  for (int t = 0; t < 2; ++t) {
+    if (h[t] == ~0ULL) continue;
+    cudaFreeAsync(stage, st);
+    return fail(RT_ERR_INVALID_ARG, "rt_set_absorbers: %s[%llu] is negative or not finite", t ? "n_HeII" : "n_HeI", h[t]);
+  }
+  if (!g->he) {
+    for (int t = 0; t < 2; ++t) {
+      e = cudaMalloc((void**)&g->nhe64[t], n8);
+      if (e == cudaSuccess) {
+        if (g->precision == RT_FP64) g->nhe[t] = g->nhe64[t];
+        else e = cudaMalloc(&g->nhe[t], 2 * ne);  // FP32 pairs
+      }
+      if (e == cudaSuccess) e = cudaMalloc(&g->Khe[t], ne);
+      if (e == cudaSuccess) e = cudaMalloc(&g->Ghe[t], ne);
+      if (e == cudaSuccess) e = cudaMemsetAsync(g->Khe[t], 0, ne, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(g->Ghe[t], 0, ne, st);
+      if (e != cudaSuccess) {
+        cudaFreeAsync(stage, st);
+        return fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_set_absorbers: %s",
+                    cudaGetErrorString(e));
+      }
+    }
+    g->he = true;
+    const InstDev I = inst_of(g);
+    CUDA_TRY(cudaMemcpyAsync(g->inst_dev, &I, sizeof I, cudaMemcpyHostToDevice, st));
+  }
+  for (int t = 0; t < 2; ++t) {
+    CUDA_TRY(cudaMemcpyAsync(g->nhe64[t], stage + t * n, n8, cudaMemcpyDeviceToDevice, st));
+    if (g->precision == RT_FP32_MIXED) LAUNCH_TRY(launch_pair(n, g->nhe64[t], g->nhe[t], st));
+  }
+  cudaFreeAsync(stage, st);
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return RT_OK;
+}
+
+int rt_set_source_types(rt_grid* g, int n, const int* type) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_set_source_types: grid is NULL");
+  if (n != (int)g->src.size())
+    return fail(RT_ERR_INVALID_ARG, "rt_set_source_types: n = %d, the grid has %zu sources", n, g->src.size());
+  if (n > 0 && !type) return fail(RT_ERR_INVALID_ARG, "rt_set_source_types: type is NULL");
+  for (int i = 0; i < n; ++i) {
+    if (type[i] < 0 || type[i] >= kTypes) return fail(RT_ERR_INVALID_ARG, "rt_set_source_types: type[%d] = %d", i, type[i]);
+    if (!(g->src[i].e_ph >= kEIon[type[i]]))
+      return fail(RT_ERR_INVALID_ARG, "rt_set_source_types: source %d: %g eV is below the %g eV threshold", i,
+                  g->src[i].e_ph, kEIon[type[i]]);
+  }
+  for (int i = 0; i < n; ++i) g->src[i].type = type[i];
+  g->src_dirty = true;
+  return RT_OK;
+}
+
 int rt_get_rates(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind) {
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_get_rates: grid is NULL");
   if (int rcw = wait_batch(g)) return rcw;
@@ -938,6 +1049,24 @@ int rt_get_rates(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype, int 
   if ((rc = copy_field(g, g->K, kd, kph, dtype, mem_kind))) return rc;
   if ((rc = copy_field(g, g->G, kd, gamma, dtype, mem_kind, gamma_scale(g)))) return rc;
   if ((rc = copy_field(g, g->xHI, RT_DTYPE_F64, x_HI, dtype, mem_kind))) return rc;
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return RT_OK;
+}
+
+int rt_get_rates_typed(rt_grid* g, int type, void* kph, void* gamma, int dtype, int mem_kind) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_get_rates_typed: grid is NULL");
+  if (type < 0 || type >= kTypes) return fail(RT_ERR_INVALID_ARG, "rt_get_rates_typed: type %d", type);
+  if (type == 0) return rt_get_rates(g, kph, gamma, nullptr, dtype, mem_kind);
+  if (int rcw = wait_batch(g)) return rcw;
+  if (!g->he) return fail(RT_ERR_INVALID_ARG, "rt_get_rates_typed: the grid has no helium absorbers");
+  if (dtype != RT_DTYPE_F64 && dtype != RT_DTYPE_F32) return fail(RT_ERR_INVALID_ARG, "rt_get_rates_typed: dtype %d", dtype);
+  if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE)
+    return fail(RT_ERR_INVALID_ARG, "rt_get_rates_typed: mem_kind %d", mem_kind);
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  const int kd = g->precision == RT_FP64 ? RT_DTYPE_F64 : RT_DTYPE_F32;
+  int rc;
+  if ((rc = copy_field(g, g->Khe[type - 1], kd, kph, dtype, mem_kind))) return rc;
+  if ((rc = copy_field(g, g->Ghe[type - 1], kd, gamma, dtype, mem_kind, gamma_scale(g)))) return rc;
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   return RT_OK;
 }
@@ -1161,12 +1290,10 @@ static int batch_rebuild(rt_batch* b, int level0) {
   for (size_t s = 0; s < b->slots.size(); ++s) {
     rt_grid* g = b->slots[s];
     if (!g) continue;
-    InstDev I;
-    memset(&I, 0, sizeof I);
-    I.nx = g->nx; I.ny = g->ny; I.nz = g->nz;
-    I.flags = g->precision == RT_FP32_MIXED ? kInstNhiPair : 0;
-    I.nhi = g->nhi; I.nH = g->nH; I.xHI = g->xHI; I.xHII = g->xHII; I.K = g->K; I.G = g->G;
-    I.acc = g->acc; I.cnt = g->cnt;
+    for (const rt_grid::SrcIn& S : g->src)
+      if (S.type > 0 && !g->he)
+        return fail(RT_ERR_INVALID_ARG, "batch: slot %zu has helium photon types but no rt_set_absorbers", s);
+    const InstDev I = inst_of(g);
     build_sources(g, level0, (int)inst.size(), src);
     inst.push_back(I);
     b->dev_slot.push_back((int)s);

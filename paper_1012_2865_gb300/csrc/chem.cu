@@ -140,6 +140,23 @@ __global__ void refresh_nhi_pair_kernel(long long ncell, const double* __restric
   }
 }
 
+// FP32 pairs (rounded value, remainder) of an FP64 absorber density.
+__global__ void pair_kernel(long long ncell, const double* __restrict__ src, float2* __restrict__ dst) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const F2 v = f2_from_double(src[c]);
+    dst[c] = make_float2(v.hi, v.lo);
+  }
+}
+
+// First cell whose density is negative, NaN or infinite (atomicMin into bad).
+__global__ void check_density_kernel(long long n, const double* __restrict__ a, unsigned long long* __restrict__ bad) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const double v = a[c];
+    if (!(v >= 0.0) || isinf(v)) atomicMin(bad, (unsigned long long)c);
+  }
+}
+
 template <typename ST, typename DT>
 __global__ void convert_kernel(long long n, const ST* __restrict__ src, DT* __restrict__ dst, double scale) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
@@ -275,6 +292,18 @@ cudaError_t launch_refresh(int precision, long long ncell, const double* nH, con
   return cudaGetLastError();
 }
 
+cudaError_t launch_pair(long long n, const double* src, void* dst, cudaStream_t st) {
+  const int block = 256, grid = grid_for(n, block);
+  pair_kernel<<<grid, block, 0, st>>>(n, src, (float2*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_density(long long n, const double* a, unsigned long long* bad, cudaStream_t st) {
+  const int block = 256, grid = grid_for(n, block);
+  check_density_kernel<<<grid, block, 0, st>>>(n, a, bad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_state(long long n, const double* nH, const double* x, unsigned long long* bad,
                                cudaStream_t st) {
   const int block = 256, grid = grid_for(n, block);
@@ -305,6 +334,16 @@ __global__ void batch_zero_kernel(const InstDev* __restrict__ inst, int esz) {
        c += (long long)gridDim.x * blockDim.x) {
     K[c] = 0u;
     G[c] = 0u;
+  }
+  for (int t = 0; t < 2; ++t) {  // helium photon types, where the grid has them
+    if (!I.Khe[t]) continue;
+    unsigned int* Kt = (unsigned int*)I.Khe[t];
+    unsigned int* Gt = (unsigned int*)I.Ghe[t];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < words;
+         c += (long long)gridDim.x * blockDim.x) {
+      Kt[c] = 0u;
+      Gt[c] = 0u;
+    }
   }
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i < 8; i += blockDim.x) I.acc[i] = 0.0;

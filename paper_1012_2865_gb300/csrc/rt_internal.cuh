@@ -11,6 +11,10 @@ namespace rtg {
 constexpr int kLevels = RT_MAX_LEVEL + 1;
 constexpr double kEvErg = 1.602176634e-12;  // erg per eV
 constexpr double kEHI = 13.6;               // hydrogen threshold, eV (Sec. 2.2)
+// Photon types (Sec. 3.2): 0 ionises H I, 1 He I, 2 He II; each is absorbed
+// by its own species, with these ionisation energies (eV)
+constexpr int kTypes = 3;
+constexpr double kEIon[kTypes] = {13.6, 24.6, 54.4};
 
 // Control words of one trace (64-bit each), in device memory.  The three
 // that every warp updates or polls sit in cache lines of their own, so their
@@ -59,7 +63,7 @@ struct __align__(16) SourceDev {
   int inst;       // owning grid slot
   int local;      // index of the source within its grid (checksum)
   int exact32;    // position on a 1/16-cell lattice within 4096 cells (see api.cu)
-  int pad;
+  int type;       // photon type of its packages (0 H I, 1 He I, 2 He II)
 };
 
 // InstDev.flags: the FP32-mixed grid stores n_HI as float2 pairs (n_HI
@@ -79,6 +83,11 @@ struct InstDev {
   void* G;                  // Gamma accumulator (double or float)
   double* acc;              // [0] emitted [1] absorbed [2] escaped [3] resumed [4] halted (photons/s)
   unsigned long long* cnt;  // [0,15) counts, [15,30) hashes, [30] segments, [31], [32] fallbacks
+  // helium photon types 1, 2 (null until the grid has helium absorbers):
+  const void* nhe[2];       // absorber density as nhi (FP64, or FP32 pairs)
+  const double* nhe64[2];   // the same in FP64 (decisions re-taken in FP64)
+  void* Khe[2];             // their k_ph and Gamma accumulators
+  void* Ghe[2];
 };
 constexpr int kCntSegments = 2 * kLevels;
 constexpr int kCntFallbacks = 2 * kLevels + 1;

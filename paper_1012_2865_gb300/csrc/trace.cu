@@ -177,9 +177,11 @@ struct Walk64 {
     sdx = S.sdx; w = S.w; rw = S.rw; heat = S.heat;
     const InstDev& I = A.inst[S.inst];
     nx = I.nx; ny = I.ny; nz = I.nz;
-    nhi = (const double*)I.nhi;
-    K = (double*)I.K;
-    G = (double*)I.G;
+    // the absorber and accumulators of the package's photon type (Sec. 3.2)
+    const int t = S.type;
+    nhi = (const double*)(t == 0 ? I.nhi : I.nhe[t - 1]);
+    K = (double*)(t == 0 ? I.K : I.Khe[t - 1]);
+    G = (double*)(t == 0 ? I.G : I.Ghe[t - 1]);
     double n[3];
     pix2vec64((int)level, pix, n);
     n0 = n[0]; n1 = n[1]; n2 = n[2];
@@ -371,7 +373,7 @@ __device__ __noinline__ double retrace_tau64(const TraceArgs& A, uint32_t src, i
       double dr = __dsub_rn(rn, r);
       if (dr < 0) dr = 0;
       const int idx = c0 + I.nx * (c1 + I.ny * c2);
-      const double nh = __dmul_rn(I.nH[idx], I.xHI[idx]);
+      const double nh = S.type == 0 ? __dmul_rn(I.nH[idx], I.xHI[idx]) : I.nhe64[S.type - 1][idx];
       tau = __dadd_rn(tau, __dmul_rn(__dmul_rn(S.sdx, nh), dr));
       if (l == level && c0 == tc0 && c1 == tc1 && c2 == tc2) return tau;
       if (tau > A.tau_term) return nan("");
@@ -549,10 +551,13 @@ struct Walk32 {
     return true;
   }
   __device__ __forceinline__ void bind(const TraceArgs& A) {
-    const InstDev& I = A.inst[A.src[src].inst];
-    nhi = (const float*)I.nhi;
-    K = (float*)I.K;
-    G = (float*)I.G;
+    const SourceDev& S = A.src[src];
+    const InstDev& I = A.inst[S.inst];
+    // the absorber and accumulators of the package's photon type (Sec. 3.2)
+    const int t = S.type;
+    nhi = (const float*)(t == 0 ? I.nhi : I.nhe[t - 1]);
+    K = (float*)(t == 0 ? I.K : I.Khe[t - 1]);
+    G = (float*)(t == 0 ? I.G : I.Ghe[t - 1]);
     level = (level & ~512u) | ((I.flags & kInstNhiPair) ? 512u : 0u);
     Pstart = P;
     steps = 0;

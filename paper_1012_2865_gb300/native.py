@@ -117,6 +117,9 @@ def lib():
             "rt_timestep": ([vp, d, d, d, d, d, d, ctypes.POINTER(d)], i),
             "rt_set_source_offset": ([vp, i], i),
             "rt_set_source_rates": ([vp, i, vp], i),
+            "rt_set_source_types": ([vp, i, vp], i),
+            "rt_set_absorbers": ([vp, vp, vp, i], i),
+            "rt_get_rates_typed": ([vp, i, vp, vp, i, i], i),
             "rt_get_in_flight": ([vp, vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)], i),
             "rt_synchronize": ([vp], i),
             "rt_selfcheck_directions": ([vp, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
@@ -265,6 +268,28 @@ def rt_set_source_rates(grid, ndot):
     check(lib().rt_set_source_rates(grid, nd.size, nd.ctypes.data))
 
 
+def rt_set_source_types(grid, types):
+    t = np.ascontiguousarray(types, dtype=np.int32).reshape(-1)
+    check(lib().rt_set_source_types(grid, t.size, t.ctypes.data))
+
+
+def rt_set_absorbers(grid, n_HeI, n_HeII):
+    """Helium absorber densities: host arrays or CUDA tensors (float64)."""
+    p1, k1, keep1 = _buf(n_HeI)
+    p2, k2, keep2 = _buf(n_HeII)
+    if k1 != k2:
+        raise ValueError("n_HeI and n_HeII must both live on the host or both on the device")
+    check(lib().rt_set_absorbers(grid, p1, p2, k1))
+
+
+def rt_get_rates_typed(grid, ncell, ptype, dtype=RT_DTYPE_F64, where="host"):
+    outs = {k: _out(ncell, dtype, where) for k in ("kph", "gamma")}
+    mk = RT_MEM_DEVICE if where == "device" else RT_MEM_HOST
+    ptr = {k: (v.data_ptr() if where == "device" else v.ctypes.data) for k, v in outs.items()}
+    check(lib().rt_get_rates_typed(grid, int(ptype), ptr["kph"], ptr["gamma"], int(dtype), mk))
+    return outs
+
+
 def rt_get_in_flight(grid) -> np.ndarray:
     """Packages in flight after the last trace, as a FLIGHT_DTYPE array."""
     n = ctypes.c_uint64()
@@ -366,6 +391,15 @@ class Grid:
 
     def in_flight(self) -> np.ndarray:
         return rt_get_in_flight(self.h)
+
+    def set_source_types(self, types):
+        rt_set_source_types(self.h, types)
+
+    def set_absorbers(self, n_HeI, n_HeII):
+        rt_set_absorbers(self.h, n_HeI, n_HeII)
+
+    def rates_typed(self, ptype, dtype=RT_DTYPE_F64, where="host"):
+        return rt_get_rates_typed(self.h, self.ncell, ptype, dtype, where)
 
     def rates(self, dtype=RT_DTYPE_F64, where="host"):
         return rt_get_rates(self.h, self.ncell, dtype, where)
