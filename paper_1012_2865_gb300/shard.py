@@ -11,7 +11,11 @@ stay identical.  The exchange is the only communication per step.
 
 `shard_trace` runs one rank's share and returns its partial results;
 `install` writes the summed rates back into the grid.  The all-reduce itself
-is the caller's (`torch.distributed.all_reduce` between ranks).
+is the caller's (`torch.distributed.all_reduce` between ranks).  With a
+finite speed of light the packages in flight belong to the sources that
+emitted them, so each rank keeps its own between steps: `ShardGrid` holds a
+rank's grid across steps, and the budget sums carry the photons resumed and
+halted.
 """
 from __future__ import annotations
 
@@ -19,7 +23,7 @@ import numpy as np
 
 from . import native
 
-BUDGET_KEYS = ("emitted", "absorbed", "escaped")
+BUDGET_KEYS = ("emitted", "absorbed", "escaped", "resumed", "halted")
 
 
 def source_range(nsrc: int, rank: int, world: int) -> tuple:
@@ -41,7 +45,7 @@ def shard_of(g: dict, rank: int, world: int) -> tuple:
 def budget_vector(b: dict) -> tuple:
     """(FP64 sums, int64 counters) of a budget, in a fixed order for an
     all-reduce; the checksums wrap modulo 2^64 as int64 sums do."""
-    f = np.array([b[k] for k in BUDGET_KEYS], dtype=np.float64)
+    f = np.array([b.get(k, 0.0) for k in BUDGET_KEYS], dtype=np.float64)
     i = np.concatenate([np.asarray(b["counts"], dtype=np.uint64), np.asarray(b["hashes"], dtype=np.uint64),
                         np.array([b["segments"]], dtype=np.uint64)]).view(np.int64)
     return f, i
@@ -70,6 +74,43 @@ def shard_trace(ctx, g: dict, precision: str, rank: int, world: int, where: str 
     dt = native.RT_DTYPE_F64 if precision == "fp64" else native.RT_DTYPE_F32
     r = native.rt_get_rates(grid.h, grid.ncell, dt, where)
     return grid, b, r["kph"], r["gamma"]
+
+
+class ShardGrid:
+    """One rank's share of the sources on a grid that lives across steps.
+
+    trace() returns the rank's partial (budget, kph, gamma); after the
+    all-reduce, install() writes the sums into the grid and chem() advances
+    the (identical on every rank) state."""
+
+    def __init__(self, ctx, g: dict, precision: str, rank: int, world: int):
+        sub, self.s0 = shard_of(g, rank, world)
+        self.precision = precision
+        self.nsrc = len(sub["ndot"])
+        self.grid = native.Grid(ctx, dict(sub, ndot=[]), precision)
+        native.rt_set_source_offset(self.grid.h, self.s0)
+        if self.nsrc:
+            native.rt_add_sources(self.grid.h, sub["pos_cm"], sub["ndot"], sub["e_ph_eV"], sub["sigma_cm2"])
+
+    def set_source_rates(self, ndot_all):
+        """Rates of every source of the whole list; this rank takes its range."""
+        if self.nsrc:
+            self.grid.set_source_rates(np.asarray(ndot_all)[self.s0:self.s0 + self.nsrc])
+
+    def trace(self, where: str = "device", **params):
+        b = self.grid.trace(**params)
+        dt = native.RT_DTYPE_F64 if self.precision == "fp64" else native.RT_DTYPE_F32
+        r = native.rt_get_rates(self.grid.h, self.grid.ncell, dt, where)
+        return b, r["kph"], r["gamma"]
+
+    def install(self, kph, gamma):
+        install(self.grid, kph, gamma)
+
+    def chem(self, dt_s, nsub, alpha_B):
+        self.grid.chem(dt_s, nsub, alpha_B)
+
+    def close(self):
+        self.grid.close()
 
 
 def install(grid, kph, gamma):

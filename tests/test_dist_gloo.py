@@ -104,6 +104,70 @@ def test_source_partitioned_trace_sums_to_the_whole():
         np.testing.assert_allclose(gm, full["gamma"], rtol=1e-12, atol=1e-300)
 
 
+def _shard_fsl_rank(rank, world, port, q):
+    """A source-partitioned trace with a finite speed of light: each rank keeps
+    the packages in flight of its own sources from step to step."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import numpy as np
+    import oracle
+    from paper_1012_2865_gb300 import shard, synth
+    g = synth.clumpy(N=16, nsrc=5, seed=31)
+    g["x_HI"] = np.full(16 ** 3, 0.02)
+    sub, s0 = shard.shard_of(g, rank, world)
+    light = 3.5 * g["box_len_cm"] / 16
+    fl = oracle.Flight()
+    steps = []
+    for step in range(4):
+        o = oracle.trace(sub["dims"], sub["box_len_cm"], sub["n_H"], sub["x_HI"], sub["pos_cm"], sub["ndot"],
+                         sub["e_ph_eV"], sub["sigma_cm2"], src_offset=s0, flight=fl, light_cm=light,
+                         **synth.DEFAULT_PARAMS)
+        k = torch.from_numpy(o["kph"].copy())
+        f, i = shard.budget_vector(dict(emitted=o["budget"][0], absorbed=o["budget"][1], escaped=o["budget"][2],
+                                        resumed=o["resumed"], halted=o["halted"], counts=o["counts"],
+                                        hashes=o["hashes"], segments=o["segments"]))
+        ft, it = torch.from_numpy(f), torch.from_numpy(i)
+        for t in (k, ft, it):
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        steps.append((k.numpy(), shard.budget_from_vector(ft.numpy(), it.numpy())))
+    q.put((rank, steps))
+    dist.destroy_process_group()
+
+
+def test_source_partitioned_trace_with_packages_in_flight():
+    import numpy as np
+    import oracle
+    from paper_1012_2865_gb300 import synth
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_fsl_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=300) for _ in range(world)), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    g = synth.clumpy(N=16, nsrc=5, seed=31)
+    g["x_HI"] = np.full(16 ** 3, 0.02)
+    fl = oracle.Flight()
+    for step in range(4):
+        full = oracle.trace(g["dims"], g["box_len_cm"], g["n_H"], g["x_HI"], g["pos_cm"], g["ndot"],
+                            g["e_ph_eV"], g["sigma_cm2"], flight=fl, light_cm=3.5 * g["box_len_cm"] / 16,
+                            **synth.DEFAULT_PARAMS)
+        total = full["budget"][0] + full["resumed"]
+        for _, steps in out:
+            k, b = steps[step]
+            np.testing.assert_array_equal(b["counts"], full["counts"])
+            np.testing.assert_array_equal(b["hashes"], full["hashes"])
+            assert b["segments"] == full["segments"]
+            for key, ref in (("emitted", full["budget"][0]), ("absorbed", full["budget"][1]),
+                             ("escaped", full["budget"][2]), ("resumed", full["resumed"]), ("halted", full["halted"])):
+                assert abs(b[key] - ref) <= 1e-12 * total, (step, key)
+            np.testing.assert_allclose(k, full["kph"], rtol=1e-12, atol=1e-300)
+    assert full["resumed"] > 0 and full["halted"] > 0
+
+
 def test_source_ranges_partition_the_list():
     from paper_1012_2865_gb300 import shard
     for nsrc in (0, 1, 7, 1000):
