@@ -383,7 +383,8 @@ def finite_light(args, ctx, stream, flush, precision) -> dict:
     alg = segs * (8 + 2 * red) + moved * 48 + pushed * 96
     return {"value": segs / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps,
             "kernel_ms": 1e3 * kt / args.steps, "segments_per_step": segs // args.steps,
-            "in_flight_per_step": moved // (2 * args.steps), "precision": precision,
+            "in_flight_per_step": moved // (2 * args.steps), "queue_records_per_step": pushed // args.steps,
+            "algorithmic_bytes_per_step": alg // args.steps, "precision": precision,
             "trace_gb_s": alg / kt / 1e9, "gpu_launches": int(launches),
             "workload": "application5-pulse-128^3: 1 Mpc box, n_H 1e-4, x_HI 1e-5, corner source "
                         "L(t) of Eq. test12 (1e55 ph/s, t0 0.5 Myr, A 4), dt_P 50 kyr, timed after 6 Myr",
