@@ -77,7 +77,8 @@ def test_shards_with_packages_in_flight(precision):
         np.testing.assert_array_equal(b["counts"], b_full["counts"])
         np.testing.assert_array_equal(b["hashes"], b_full["hashes"])
         for key in ("emitted", "absorbed", "escaped", "resumed", "halted"):
-            assert abs(b[key] - b_full[key]) <= 1e-9 * (b_full["emitted"] + b_full["resumed"]), key
+            # the media differ by the update's response to the rates' summation order
+            assert abs(b[key] - b_full[key]) <= parity.BUDGET_TOL[precision] * (b_full["emitted"] + b_full["resumed"]), key
         ref = full.rates()["kph"]
         m = ref > 1e-8 * ref.max()
         np.testing.assert_allclose(k.double().cpu().numpy()[m], ref[m], rtol=TOL[precision])
