@@ -141,6 +141,7 @@ struct FlightState {
   float2* rlim32[2] = {nullptr, nullptr};
   size_t rlim_cap[2] = {0, 0};
   int tab = 0;                // device table holding rlim
+  std::vector<double> pend;   // radii of the trace being launched (become rlim when it is)
   std::vector<double> unit;   // per source: photons/s of P = 1 for the stored packages
   unsigned long long last_halted = 0;  // packages halted by the last synchronous trace
   ~FlightState() {
@@ -402,6 +403,7 @@ int rt_set_source_offset(rt_grid* g, int first) {
 static void drop_flight(rt_grid* g) {
   g->fl.live = false;
   g->fl.rlim.clear();
+  g->fl.pend.clear();
   g->fl.unit.clear();
   g->fl.last_halted = 0;
 }
@@ -677,9 +679,10 @@ static int prepare_flight(rt_grid* g, const rt_trace_params* p, bool retry, Trac
       F.rlim_cap[nt] = cap;
     }
     LAUNCH_TRY(launch_flight_table(F.rlim64[F.tab], F.rlim64[nt], F.rlim32[nt], (int)n_new, c_dt, st));
-    F.tab = nt;
-    F.rlim.swap(neu);
+    F.pend.swap(neu);  // the launch adopts them (commit_flight); a failed one leaves rlim as it was
   }
+  const int tab = retry ? F.tab : 1 - F.tab;
+  const size_t n_ages = retry ? F.rlim.size() : F.pend.size();
   // the output store: the other buffer than the one holding the last trace's packages
   const int out = F.live ? 1 - F.in : F.in;
   unsigned long long want = F.last_halted + F.last_halted / 4 + 1024;
@@ -691,9 +694,9 @@ static int prepare_flight(rt_grid* g, const rt_trace_params* p, bool retry, Trac
     if (rc) return rc;
     F.cap[out] = want;
   }
-  A.rlim64 = F.rlim64[F.tab];
-  A.rlim32 = F.rlim32[F.tab];
-  A.n_ages = (int)F.rlim.size();
+  A.rlim64 = F.rlim64[tab];
+  A.rlim32 = F.rlim32[tab];
+  A.n_ages = (int)n_ages;
   A.res_in = F.live ? F.buf[F.in] : nullptr;
   A.halt_out = F.buf[out];
   A.halt_cap = F.cap[out];
@@ -779,12 +782,18 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool 
 }
 
 // After the launches of a trace: with a finite speed of light its output
-// store now holds the packages in flight; otherwise nothing is.
+// store now holds the packages in flight and its halting radii are the
+// current ones; otherwise nothing is in flight.
 static void commit_flight(rt_grid* g, bool fsl) {
   FlightState& F = g->fl;
   if (!fsl) {
     drop_flight(g);
     return;
+  }
+  if (!F.pend.empty()) {
+    F.tab = 1 - F.tab;
+    F.rlim.swap(F.pend);
+    F.pend.clear();
   }
   if (F.live) F.in = 1 - F.in;
   F.live = true;
