@@ -101,19 +101,23 @@ typedef struct {
  * the photon budget and every decision are unchanged; k_ph is no longer
  * photon conserving (as the paper notes). */
 #define RT_TRACE_FC 2
-/* Finite speed of light (light_cm > 0).  A package halts where it has
- * travelled c dt_P per trace since its emission: a package emitted a traces
- * ago halts at rlim[a], rlim[0] = light_cm / dx and rlim[a] = the previous
- * trace's rlim[a - 1] + light_cm / dx (cell units, FP64).  The test follows
- * the split test and uses the crossing radius of the current cell; the cut
- * segment is deposited as usual and the termination test comes first.  The
- * grid keeps halted packages in device memory (photons/s, radius, optical
- * depth, cell, age); the next trace with light_cm > 0 continues them from
- * their cells through the medium of that trace, alongside the new packages
- * of its sources, and they do not count as created packages (counts,
- * hashes).  A trace with light_cm = 0, rt_clear_sources, and adding the grid
- * to a batch drop the packages in flight.  Batches and rt_trace_noalloc
- * trace with an infinite speed of light only (light_cm must be 0). */
+/* Finite speed of light (light_cm > 0).  A package halts where light
+ * emitted with it has travelled: a package emitted a traces ago halts at
+ * radius rlim[a], rlim[0] = light_cm / dx and rlim[a] = the previous trace's
+ * rlim[a - 1] + light_cm / dx (cell units, FP64).  The test follows the split
+ * test and uses the crossing radius of the current cell; the cut segment is
+ * deposited as usual and the termination test comes first.  The grid keeps
+ * halted packages in device memory (photons/s, radius, optical depth, cell,
+ * age); the next trace with light_cm > 0 continues them from their cells
+ * through the medium of that trace, alongside the new packages of its
+ * sources, and they do not count as created packages (counts, hashes).  The
+ * store of halted packages grows by itself in a synchronous trace (out !=
+ * NULL); an enqueued trace that fills it reports RT_ERR_QUEUE_OVERFLOW.  A
+ * light_cm so short that more than 2^20 ages would be in flight is
+ * RT_ERR_INVALID_ARG.  A trace with light_cm = 0, rt_clear_sources, and
+ * adding the grid to a batch drop the packages in flight.  Batches and
+ * rt_trace_noalloc trace with an infinite speed of light only (light_cm must
+ * be 0). */
 
 /* Result of a trace, per grid. */
 typedef struct {
