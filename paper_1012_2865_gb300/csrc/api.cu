@@ -1014,6 +1014,13 @@ int rt_set_absorbers(rt_grid* g, const double* n_HeI, const double* n_HeII, int 
       if (e == cudaSuccess) e = cudaMemsetAsync(g->Ghe[t], 0, ne, st);
       if (e != cudaSuccess) {
         cudaFreeAsync(stage, st);
+        cudaStreamSynchronize(st);
+        for (int u = 0; u < 2; ++u) {  // leave the grid as it was
+          if (g->nhe[u] != g->nhe64[u]) cudaFree(g->nhe[u]);
+          cudaFree(g->nhe64[u]); cudaFree(g->Khe[u]); cudaFree(g->Ghe[u]);
+          g->nhe[u] = g->Khe[u] = g->Ghe[u] = nullptr;
+          g->nhe64[u] = nullptr;
+        }
         return fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_set_absorbers: %s",
                     cudaGetErrorString(e));
       }
