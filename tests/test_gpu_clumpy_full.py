@@ -3,7 +3,6 @@
 The oracle traces the whole configuration (about 1.5e8 segments, ~10 s of
 one CPU core), so the comparison is element by element at full size.
 """
-import numpy as np
 import pytest
 
 import parity

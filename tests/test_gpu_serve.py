@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import parity
-from paper_1012_2865_gb300 import serve, synth
+from paper_1012_2865_gb300 import serve
 
 pytestmark = pytest.mark.gpu
 

@@ -20,7 +20,6 @@ TOL = {"fp64": 1e-12, "fp32_mixed": 2e-5}
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
 def test_two_shards_equal_the_whole(precision):
-    import torch
     ctx = parity.ctx()
     g = synth.clumpy(N=24, nsrc=9, seed=31)
     full, b_full, r_full = parity.run_gpu(g, precision)
