@@ -204,3 +204,25 @@ def test_api_edges():
         native.rt_batch_trace(batch.h, native.trace_params(light_cm=1.0, **synth.DEFAULT_PARAMS))
     batch.close()
     grid.close()
+
+
+def test_queue_growth_keeps_the_packages_in_flight():
+    """A trace whose children overflow the first automatic queue (2^20 records)
+    is redone with a larger queue; the redo starts from the same packages in
+    flight and halting radii, and the sequence still equals the oracle's."""
+    N = 48
+    g = synth.pulse(N)
+    rng = np.random.default_rng(9)
+    pos, ndot, e, sg = synth.random_sources((N, N, N), g["box_len_cm"] / N, 24, 1e52, 1e54, rng)
+    g.update(pos_cm=pos, ndot=ndot, e_ph_eV=e, sigma_cm2=sg)
+    light = 14.0 * g["box_len_cm"] / N
+    grid = native.Grid(parity.ctx(), g, "fp32_mixed")
+    fl = oracle.Flight()
+    for step in range(2):
+        b = grid.trace(checksums=True, light_cm=light, level0=2, phi_c=5.1, f_term=1e-10, max_level=14)
+        o = _oracle(g, fl, light, level0=2)
+        _compare_step(g, b, grid.rates(), o, "fp32_mixed")
+        _compare_flight(g, grid.in_flight(), fl.packages, "fp32_mixed")
+        if step == 1:
+            assert b["queue_pushed"] > (1 << 20)  # more children than the first queue held
+    grid.close()
