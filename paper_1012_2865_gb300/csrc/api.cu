@@ -673,6 +673,7 @@ static int prepare_flight(rt_grid* g, const rt_trace_params* p, bool retry, Trac
     if (F.rlim_cap[nt] < n_new) {
       const size_t cap = n_new < 64 ? 64 : 2 * n_new;
       have64 = have32 = 0;
+      F.rlim_cap[nt] = 0;  // the old tables are released even if the new ones cannot be had
       int rc = ensure_buffer((void**)&F.rlim64[nt], &have64, cap * sizeof(double), st);
       if (!rc) rc = ensure_buffer((void**)&F.rlim32[nt], &have32, cap * sizeof(float2), st);
       if (rc) return rc;
@@ -690,6 +691,7 @@ static int prepare_flight(rt_grid* g, const rt_trace_params* p, bool retry, Trac
   if (F.cap[out] < want) {
     const size_t rec = g->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
     size_t have = 0;
+    F.cap[out] = 0;  // the old store is released even if the new one cannot be had
     int rc = ensure_buffer(&F.buf[out], &have, want * rec, st);
     if (rc) return rc;
     F.cap[out] = want;
