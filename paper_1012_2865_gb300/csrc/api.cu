@@ -501,6 +501,7 @@ static int prepare_sources(rt_grid* g, int level0, bool fsl) {
   if (v.size() > g->src_dev_cap) {
     if (g->src_dev) cudaFree(g->src_dev);
     g->src_dev = nullptr;
+    g->src_dev_cap = 0;
     const size_t cap = v.size() < 64 ? 64 : v.size();
     CUDA_TRY(cudaMalloc((void**)&g->src_dev, cap * sizeof(SourceDev)));
     g->src_dev_cap = cap;
