@@ -82,7 +82,9 @@ typedef struct {
   double timeout_s;      /* bound on any device-side wait; <= 0 = 2 s */
   int blocks_per_sm;     /* resident 256-thread blocks of the trace kernel per SM;
                             0 = as many as fit (lower it to share the GPU) */
-  int segs_per_iter;     /* segments a lane traces between queue visits; 0 = tuned */
+  int segs_per_iter;     /* segments a lane traces between queue visits; 0 = tuned
+                            (from the mean package length of the grid's last
+                            trace read back: half of it, a power of two in [8, 64]) */
   int flags;             /* RT_TRACE_CHECKSUMS: also fill rt_budget.hashes;
                             RT_TRACE_FC: covering-factor correction */
   int passes;            /* launches over equal ranges of the sources (>= 0);

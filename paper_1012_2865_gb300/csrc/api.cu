@@ -185,6 +185,7 @@ struct rt_grid {
   TraceState ts;
   FlightState fl;
   bool src_fsl = false;                // the device source table was built for a finite-c trace
+  double seg_per_pkg = 0.0;            // segments per package of the last trace read back
   // pinned readback buffer
   void* host_rb = nullptr;
   bool traced = false;
@@ -706,6 +707,18 @@ static int prepare_flight(rt_grid* g, const rt_trace_params* p, bool retry, Trac
   return RT_OK;
 }
 
+// Segments a lane traces between visits to the queue, from the packages'
+// mean length in the grid's last trace: long rays (optically thin media)
+// gain from fewer warp-wide queue visits, short ones (dense media) from
+// lanes that finish being refilled sooner.  Half the mean, as a power of two
+// in [8, 64]; 16 before any trace was read back.
+static int tuned_segs_per_iter(double seg_per_pkg) {
+  if (!(seg_per_pkg > 0)) return 16;
+  int s = 8;
+  while (s < 64 && s < 0.5 * seg_per_pkg) s *= 2;
+  return s;
+}
+
 static void commit_flight(rt_grid* g, bool fsl);
 
 static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool retry = false) {
@@ -763,6 +776,7 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool 
   A.cap = g->ts.cap;
   A.ctl = g->ts.ctl;
   A.max_steps = 2 * (g->nx + g->ny + g->nz) + 16;
+  if (p->segs_per_iter == 0) A.segs_per_iter = tuned_segs_per_iter(g->seg_per_pkg);
   int mode = FLIGHT_OFF;
   unsigned long long in_cap = 0;
   if (fsl) {
@@ -831,6 +845,9 @@ static int read_budget(rt_grid* g, rt_budget* out) {
   out->n_resumed = hctl[CTL_RESUME];
   out->n_halted = hctl[CTL_HALTED];
   if (g->fl.live) g->fl.last_halted = out->n_halted;
+  unsigned long long pkgs = out->n_resumed;
+  for (int l = 0; l < kLevels; ++l) pkgs += out->counts[l];
+  if (out->status == RT_OK && pkgs > 0) g->seg_per_pkg = (double)out->segments / (double)pkgs;
   float ms = 0.f;
   if (g->traced && cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) out->kernel_ms = ms;
   else cudaGetLastError();
@@ -1698,7 +1715,7 @@ int rt_batch_autotune(rt_batch* b, rt_trace_params* p) {
   q.segs_per_iter = 8;
   q.blocks_per_sm = 0;
   if ((rc = rt_batch_trace(b, &q, 1))) return rc;  // sizes the queue, warms up
-  const int spi[] = {4, 8, 16, 32};
+  const int spi[] = {4, 8, 16, 32, 64};
   int per_sm_max = 0;
   CUDA_TRY(trace_occupancy(b->precision, 0, 256, &per_sm_max));
   float best = 1e30f;

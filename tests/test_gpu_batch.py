@@ -101,7 +101,7 @@ def test_batch_remove_add_and_autotune():
     assert native.rt_batch_size(batch.h) == len(gs)
     params = native.trace_params(checksums=True, **synth.DEFAULT_PARAMS)
     params = native.rt_batch_autotune(batch.h, params)
-    assert params.segs_per_iter in (4, 8, 16, 32) and params.blocks_per_sm >= 1
+    assert params.segs_per_iter in (4, 8, 16, 32, 64) and params.blocks_per_sm >= 1
     native.rt_batch_trace(batch.h, params)
     members = [(slots[0], gs[0], grids[0]), (s_new, extra, ge), (slots[3], gs[3], grids[3])]
     for slot, g, gr in members:
