@@ -976,6 +976,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
       continue;
     }
     backoff = 256;
+    seen_out = -1;  // the no-progress clock runs over one idle stretch only
     // (4) trace a few segments
     if (active && ev == EV_NONE) {
       for (int it = 0; it < A.segs_per_iter; ++it) {
