@@ -149,3 +149,17 @@ def test_stromgren_500myr_fp64():
             assert 0.97 < R / ana < 1.035, (t, R / ana)
     assert abs(R / rs - 1) < 0.02, R / rs
     grid.close()
+
+
+def test_long_trace_with_a_short_no_progress_limit():
+    """A trace several times longer than the no-progress limit completes: the
+    limit applies to a warp's idle stretch without any change of the
+    outstanding count, not to the trace (a warp that has been busy starts a
+    new stretch)."""
+    g = synth.stromgren_snapshot(256)
+    grid = native.Grid(parity.ctx(), g, "fp64")
+    b = grid.trace(timeout_s=0.01, **synth.DEFAULT_PARAMS)
+    assert b["status"] == 0
+    assert b["kernel_ms"] > 30.0  # the trace outlasts the limit several times over
+    assert abs(b["emitted"] - b["absorbed"] - b["escaped"]) <= 1e-12 * b["emitted"]
+    grid.close()
