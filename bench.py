@@ -318,6 +318,9 @@ def run_native(args, rank, world, local):
         # per cell: n_H, x_HI (FP64), k_ph read, the per-cell value written and read back
         out["timestep"] = {"ms": ms, "dt_s": dt_p, "cells": cells,
                            "gb_s": cells * (8 + 8 + (8 if head == "fp64" else 4) + 4 + 4) / (ms / 1e3) / 1e9}
+    # photon types (Sec. 3.2): the clumpy configuration with H I, He I and He II sources
+    if not args.no_types:
+        out["photon_types"] = photon_types(args, ctx, stream, flush, head)
     # finite speed of light: the Application 5 pulse (Sec. 9)
     if not args.no_fsl:
         out["finite_light"] = finite_light(args, ctx, stream, flush, head)
@@ -329,6 +332,57 @@ def run_native(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     return out
+
+
+def photon_types(args, ctx, stream, flush, precision) -> dict:
+    """Photon types (Sec. 3.2) on a clumpy 128^3 medium: 30 sources cycling
+    through H I, He I and He II ionising photons, each absorbed by its own
+    species (helium at 0.079 n_H, 90 % He I, so He II photons cross most of
+    the box); each timed step traces and updates from the neutral initial
+    state (restored untimed)."""
+    import torch
+    from paper_1012_2865_gb300 import native, synth
+
+    g = synth.typed_clumpy()
+    grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
+    grid.set_absorbers(g["n_he"][0], g["n_he"][1])
+    grid.set_source_types(g["types"])
+    params = dict(synth.DEFAULT_PARAMS)
+    b = grid.trace(**params)  # sizes the queue
+    qp = dict(params, queue_capacity=max(1 << 20, int(b["queue_pushed"] * 1.5)))
+    x0 = torch.tensor(g["x_HI"], dtype=torch.float64, device=stream.device)
+    for _ in range(max(3, args.warmup)):
+        native.rt_set_state(grid.h, x0)
+        grid.trace(sync=False, **qp)
+        grid.chem(DT_S, 10, synth.ALPHA_B)
+    torch.cuda.synchronize()
+    step_ms, kern_ms, segs, launches = [], [], 0, 0
+    for _ in range(args.steps):
+        native.rt_set_state(grid.h, x0)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = native.rt_kernel_launches()
+        e0.record(stream)
+        grid.trace(sync=False, **qp)
+        grid.chem(DT_S, 10, synth.ALPHA_B)
+        e1.record(stream)
+        e1.synchronize()
+        launches += native.rt_kernel_launches() - l0
+        bb = native.rt_get_budget(grid.h)
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(bb["kernel_ms"])
+        segs += bb["segments"]
+    grid.close()
+    t = sum(step_ms) / 1e3
+    return {"value": segs / t, "unit": UNIT, "ms_per_step": 1e3 * t / args.steps,
+            "kernel_ms": sum(kern_ms) / args.steps, "segments_per_step": segs // args.steps,
+            "precision": precision, "gpu_launches": int(launches),
+            "workload": "typed-clumpy-128^3: clumpy medium, 30 sources cycling H I / He I / He II ionising "
+                        "(E_i..E_i+16 eV, threshold cross sections), n_He = 0.079 n_H (90 % He I); "
+                        "step = rt_trace + rt_chem_update from the neutral state",
+            "l2": "flushed (512 MB write) between steps"}
 
 
 def finite_light(args, ctx, stream, flush, precision) -> dict:
@@ -551,6 +605,7 @@ def main():
     ap.add_argument("--no-fc", action="store_true", help="skip the covering-factor (Sec. 2.3) leg")
     ap.add_argument("--no-timestep", action="store_true", help="skip the adaptive-timestep (Sec. 3.4) leg")
     ap.add_argument("--no-fsl", action="store_true", help="skip the finite-speed-of-light (Application 5) leg")
+    ap.add_argument("--no-types", action="store_true", help="skip the photon-types (Sec. 3.2) leg")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-fp64-budget-s", type=float, default=90.0)
     ap.add_argument("--grid", type=int, default=128, help="cells per side (128 = the benchmark workload)")

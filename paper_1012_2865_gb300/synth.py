@@ -23,6 +23,11 @@ Recipes (base seed 20101, numpy PCG64):
   same medium, 1-256 sources, Ndot log-uniform in [1e47, 1e50].
 * ``request_stream(rate, duration)`` -- Poisson arrivals; cells log-uniform in
   [64^3, 256^3], 1-500 sources, 1-20 coupled steps of 0.5 Myr.
+* ``typed_clumpy(N=128, nsrc=30)`` -- the clumpy medium with photon types
+  (Sec. 3.2): sources cycle through H I, He I and He II ionising, photon energies uniform
+  in [E_i, E_i + 16] eV, threshold cross sections 6.3e-18, 7.43e-18 and
+  1.58e-18 cm^2; helium at n_He = 0.079 n_H (primordial), 90 % He I and 10 %
+  He II.
 * ``pulse(N)`` -- Application 5 (Sec. 9): a 1 Mpc box of uniform n_H = 1e-4
   cm^-3, kept optically thin (x_HI = 1e-5, what photo-ionisation equilibrium
   gives there), one 29.6 eV source at the corner whose rate follows
@@ -212,6 +217,25 @@ def request_grid(req: dict, box_kpc: float = 6.6) -> dict:
     n = lognormal_density(N, seed=req["seed"])
     pos, ndot, e, sg = random_sources((N, N, N), box / N, req["nsrc"], 1e47, 1e50, rng)
     return _grid(N, box, n, 1.0, pos, ndot, e, sg, alpha_B=ALPHA_B)
+
+
+E_ION_EV = (13.6, 24.6, 54.4)              # H I, He I, He II ionisation energies
+SIGMA_TYPE = (6.3e-18, 7.43e-18, 1.58e-18)  # threshold cross sections of the three absorbers
+
+
+def typed_clumpy(N: int = 128, nsrc: int = 30, seed: int = BASE_SEED + 6, box_kpc: float = 6.6) -> dict:
+    """The clumpy medium with sources of the three photon types and helium
+    absorbers; adds ``types`` and ``n_he`` (2, ncell) to the grid dict."""
+    g = clumpy(N, nsrc, seed, box_kpc)
+    rng = np.random.default_rng(seed + 1)
+    types = np.arange(nsrc) % 3
+    e_ion = np.asarray(E_ION_EV)[types]
+    g["e_ph_eV"] = e_ion + rng.uniform(0.0, 16.0, nsrc)
+    g["sigma_cm2"] = np.asarray(SIGMA_TYPE)[types]
+    g["types"] = types
+    n_he = 0.079 * g["n_H"]
+    g["n_he"] = np.stack([round_f32(0.9 * n_he), round_f32(0.1 * n_he)])
+    return g
 
 
 def pulse_rate(t_s, L_max: float = 1e55, t0_s: float = 0.5 * MYR_S, A: float = 4.0):
