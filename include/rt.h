@@ -103,6 +103,12 @@ typedef struct {
  * the photon budget and every decision are unchanged; k_ph is no longer
  * photon conserving (as the paper notes). */
 #define RT_TRACE_FC 2
+/* Self-test of the bounded waits: the trace also waits for one package that
+ * never exists, so it cannot end by itself; its idle warps must give up
+ * after timeout_s without progress and the trace return RT_ERR_TIMEOUT,
+ * leaving the grid usable.  No other effect on the result's validity: the
+ * trace's results are invalid (as after any RT_ERR_TIMEOUT). */
+#define RT_TRACE_SELFTEST_STALL 4
 /* Finite speed of light (light_cm > 0).  A package halts where light
  * emitted with it has travelled: a package emitted a traces ago halts at
  * radius rlim[a], rlim[0] = light_cm / dx and rlim[a] = the previous trace's

@@ -36,6 +36,7 @@ cudaError_t launch_timestep(long long n, int nx, int ny, int nz, const double* n
 cudaError_t launch_check_state(long long n, const double* nH, const double* x, unsigned long long* bad,
                                cudaStream_t st);
 cudaError_t launch_check_density(long long n, const double* a, unsigned long long* bad, cudaStream_t st);
+cudaError_t launch_add_word(unsigned long long* w, unsigned long long delta, cudaStream_t st);
 cudaError_t launch_pair(long long n, const double* src, void* dst, cudaStream_t st);
 cudaError_t launch_direction_check(int level, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st);
@@ -578,7 +579,7 @@ static void fill_common_args(TraceArgs& A, const rt_trace_params* p) {
 // `in_cap` say what the first pass takes over from the previous trace.
 static int launch_passes(TraceArgs A, const SourceDev* src, int nsrc, int passes, int precision, int fsl,
                          int mode, unsigned long long in_cap, int blocks, cudaEvent_t ev0, cudaEvent_t ev1,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool stall = false) {
   if (passes > nsrc) passes = nsrc;
   if (passes < 1) passes = 1;
   for (int i = 0; i < passes; ++i) {
@@ -586,6 +587,9 @@ static int launch_passes(TraceArgs A, const SourceDev* src, int nsrc, int passes
     const int s1 = (int)((long long)nsrc * (i + 1) / passes);
     const unsigned long long n = (unsigned long long)A.npix0 * (unsigned long long)(s1 - s0);
     LAUNCH_TRY(launch_trace_init(A.ctl, n, i == 0, mode, in_cap, i, passes, st));
+    // self-test: one package that never exists keeps the trace from ending,
+    // so its bounded waits must run out (RT_TRACE_SELFTEST_STALL)
+    if (i == 0 && stall) LAUNCH_TRY(launch_add_word(A.ctl + CTL_OUTSTANDING, 1ULL, st));
     if (i == 0) CUDA_TRY(cudaEventRecord(ev0, st));
     if (n == 0 && !fsl) continue;
     A.src = src;
@@ -790,7 +794,7 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool 
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
   if ((rc = launch_passes(A, g->src_dev, nsrc, passes, g->precision, fsl ? 1 : 0, mode, in_cap,
-                          per_sm * g->ctx->num_sms, g->ev0, g->ev1, st)))
+                          per_sm * g->ctx->num_sms, g->ev0, g->ev1, st, (p->flags & RT_TRACE_SELFTEST_STALL) != 0)))
     return rc;
   commit_flight(g, fsl);
   g->traced = true;

@@ -304,6 +304,16 @@ cudaError_t launch_check_density(long long n, const double* a, unsigned long lon
   return cudaGetLastError();
 }
 
+// Adds delta to one device word (the trace self-test's phantom package).
+__global__ void add_word_kernel(unsigned long long* w, unsigned long long delta) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *w += delta;
+}
+
+cudaError_t launch_add_word(unsigned long long* w, unsigned long long delta, cudaStream_t st) {
+  add_word_kernel<<<1, 32, 0, st>>>(w, delta);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_state(long long n, const double* nH, const double* x, unsigned long long* bad,
                                cudaStream_t st) {
   const int block = 256, grid = grid_for(n, block);

@@ -33,6 +33,7 @@ RT_DTYPE_F32 = 1
 RT_MAX_LEVEL = 14
 RT_TRACE_CHECKSUMS = 1
 RT_TRACE_FC = 2
+RT_TRACE_SELFTEST_STALL = 4
 NLEV = RT_MAX_LEVEL + 1
 
 PRECISIONS = {"fp64": RT_FP64, "fp32_mixed": RT_FP32_MIXED, "mixed": RT_FP32_MIXED}
@@ -219,11 +220,12 @@ def rt_clear_sources(grid):
 
 def trace_params(level0=1, phi_c=5.1, f_term=1e-10, max_level=RT_MAX_LEVEL, queue_capacity=0,
                  timeout_s=2.0, blocks_per_sm=0, segs_per_iter=0, checksums=False,
-                 passes=0, fc=False, light_cm=0.0) -> rt_trace_params:
+                 passes=0, fc=False, light_cm=0.0, selftest_stall=False) -> rt_trace_params:
+    flags = (RT_TRACE_CHECKSUMS if checksums else 0) | (RT_TRACE_FC if fc else 0) | \
+        (RT_TRACE_SELFTEST_STALL if selftest_stall else 0)
     return rt_trace_params(int(level0), float(phi_c), float(f_term), int(max_level),
                            int(queue_capacity), float(timeout_s), int(blocks_per_sm),
-                           int(segs_per_iter), (RT_TRACE_CHECKSUMS if checksums else 0) | (RT_TRACE_FC if fc else 0),
-                           int(passes), float(light_cm))
+                           int(segs_per_iter), flags, int(passes), float(light_cm))
 
 
 def budget_dict(b: rt_budget) -> dict:
