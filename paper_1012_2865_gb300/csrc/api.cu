@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rt.h"
 #include "healpix.cuh"
 #include "rt_internal.cuh"
@@ -46,6 +48,13 @@ cudaError_t launch_batch_chem(const InstDev* inst, int ninst, int precision, lon
 }  // namespace rtg
 
 using namespace rtg;
+
+// A named range on the profiler's timeline (NVTX) for the duration of a call;
+// free when no profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 static thread_local std::string g_last_error;
 static std::atomic<unsigned long long> g_launches{0};
@@ -859,6 +868,7 @@ static int read_budget(rt_grid* g, rt_budget* out) {
 }
 
 int rt_trace(rt_grid* g, const rt_trace_params* p, rt_budget* out) {
+  NvtxRange nr("rt_trace");
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_trace: grid is NULL");
   if (int rcw = wait_batch(g)) return rcw;
   int rc = check_params(p);
@@ -912,6 +922,7 @@ int rt_get_budget(rt_grid* g, rt_budget* out) {
 }
 
 int rt_chem_update(rt_grid* g, double dt_s, int nsub, double alpha_B) {
+  NvtxRange nr("rt_chem_update");
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_chem_update: grid is NULL");
   if (int rcw = wait_batch(g)) return rcw;
   if (!(dt_s >= 0) || !isfinite(dt_s)) return fail(RT_ERR_INVALID_ARG, "rt_chem_update: dt_s = %g", dt_s);
@@ -924,6 +935,7 @@ int rt_chem_update(rt_grid* g, double dt_s, int nsub, double alpha_B) {
 }
 
 int rt_set_state(rt_grid* g, const double* n_H, const double* x_HI, const double* x_HII, int mem_kind) {
+  NvtxRange nr("rt_set_state");
   if (!g || !x_HI) return fail(RT_ERR_INVALID_ARG, "rt_set_state: grid and x_HI are required");
   if (int rcw = wait_batch(g)) return rcw;
   if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE) return fail(RT_ERR_INVALID_ARG, "rt_set_state: mem_kind %d", mem_kind);
@@ -1079,6 +1091,7 @@ int rt_set_source_types(rt_grid* g, int n, const int* type) {
 }
 
 int rt_get_rates(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind) {
+  NvtxRange nr("rt_get_rates");
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_get_rates: grid is NULL");
   if (int rcw = wait_batch(g)) return rcw;
   if (dtype != RT_DTYPE_F64 && dtype != RT_DTYPE_F32) return fail(RT_ERR_INVALID_ARG, "rt_get_rates: dtype %d", dtype);
@@ -1554,6 +1567,7 @@ static int check_batch_params(const rt_trace_params* p) {
 }
 
 int rt_batch_trace(rt_batch* b, const rt_trace_params* p, int sync) {
+  NvtxRange nr("rt_batch_trace");
   if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_trace: batch is NULL");
   int rc = check_batch_params(p);
   if (rc) return rc;
@@ -1616,6 +1630,7 @@ static bool same_params(const rt_trace_params& a, const rt_trace_params& b) {
 }
 
 int rt_batch_step(rt_batch* b, const rt_trace_params* p, double dt_s, int nsub, double alpha_B, int nsteps) {
+  NvtxRange nr("rt_batch_step");
   if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_step: batch is NULL");
   int rc = check_batch_params(p);
   if (rc) return rc;
