@@ -160,6 +160,6 @@ def test_long_trace_with_a_short_no_progress_limit():
     grid = native.Grid(parity.ctx(), g, "fp64")
     b = grid.trace(timeout_s=0.01, **synth.DEFAULT_PARAMS)
     assert b["status"] == 0
-    assert b["kernel_ms"] > 30.0  # the trace outlasts the limit several times over
+    assert b["kernel_ms"] > 20.0  # the trace outlasts the 10 ms limit (about 30 ms on a GB300)
     assert abs(b["emitted"] - b["absorbed"] - b["escaped"]) <= 1e-12 * b["emitted"]
     grid.close()
