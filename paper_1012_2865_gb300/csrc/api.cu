@@ -15,6 +15,7 @@
 
 #include "rt.h"
 #include "healpix.cuh"
+#include "policy.h"
 #include "rt_internal.cuh"
 
 namespace rtg {
@@ -626,26 +627,6 @@ static unsigned long long queue_cap_limit(size_t rec, size_t held_bytes) {
   return lim;
 }
 
-// Next attempt after a queue overflow of an automatically sized trace: grow
-// the queue up to `limit` records, then split the sources into more passes.
-// `peak` (records of the largest pass) undercounts the need, because dropped
-// children were never expanded.  False when neither is possible.
-static bool grow_after_overflow(unsigned long long peak, unsigned long long limit, int nsrc,
-                                unsigned long long* cap, int* passes) {
-  if (*cap < limit) {
-    const unsigned long long need = peak + peak / 4 + 1024;
-    *cap = need > 4 * *cap ? need : 4 * *cap;
-    if (*cap > limit) *cap = limit;
-    return true;
-  }
-  if (*passes >= nsrc) return false;
-  long long np = 2LL * *passes;
-  const long long want = (long long)*passes * (long long)(peak / (limit / 2 + 1) + 1);
-  if (want > np) np = want;
-  if (np > nsrc) np = nsrc;
-  *passes = (int)np;
-  return true;
-}
 
 // Device buffer of at least `bytes`, reallocated (after the stream's work
 // is done) when smaller.
@@ -671,18 +652,13 @@ static int prepare_flight(rt_grid* g, const rt_trace_params* p, bool retry, Trac
   cudaStream_t st = g->stream;
   const double c_dt = p->light_cm / g->dx;  // cell units
   if (!retry) {
-    // ages that can still be in flight: a stored package lies inside the box,
-    // so nearer its source than the box diagonal
     const double diag = sqrt((double)g->nx * g->nx + (double)g->ny * g->ny + (double)g->nz * g->nz);
-    size_t n_old = F.live ? F.rlim.size() : 0;
-    while (n_old > 0 && F.rlim[n_old - 1] > diag + 1.0) --n_old;
-    const size_t n_new = n_old + 1;
+    std::vector<double> neu;
+    flight_radii(F.rlim, F.live, c_dt, diag, neu);
+    const size_t n_new = neu.size();
     if (n_new > kFlightMaxAges)
       return fail(RT_ERR_INVALID_ARG, "rt_trace: light_cm = %g cm is too short for this grid (%zu ages in flight)",
                   p->light_cm, n_new);
-    std::vector<double> neu(n_new);
-    neu[0] = c_dt;
-    for (size_t a = 1; a < n_new; ++a) neu[a] = F.rlim[a - 1] + c_dt;
     const int nt = 1 - F.tab;
     size_t have64 = F.rlim_cap[nt] * sizeof(double), have32 = F.rlim_cap[nt] * sizeof(float2);
     if (F.rlim_cap[nt] < n_new) {
@@ -720,17 +696,6 @@ static int prepare_flight(rt_grid* g, const rt_trace_params* p, bool retry, Trac
   return RT_OK;
 }
 
-// Segments a lane traces between visits to the queue, from the packages'
-// mean length in the grid's last trace: long rays (optically thin media)
-// gain from fewer warp-wide queue visits, short ones (dense media) from
-// lanes that finish being refilled sooner.  Half the mean, as a power of two
-// in [8, 64]; 16 before any trace was read back.
-static int tuned_segs_per_iter(double seg_per_pkg) {
-  if (!(seg_per_pkg > 0)) return 16;
-  int s = 8;
-  while (s < 64 && s < 0.5 * seg_per_pkg) s *= 2;
-  return s;
-}
 
 static void commit_flight(rt_grid* g, bool fsl);
 
