@@ -5,7 +5,11 @@
  * Cartesian grid with photon-conserving adaptive ray tracing (Wise & Abel,
  * arXiv:1012.2865, Sec. 2.1-2.2 and Steps 1-7 of Sec. 3.1) and the
  * hydrogen-only ionisation update that couples consecutive traces
- * (Eq. "dndt").  All work runs in CUDA kernels on one GPU; there is no CPU
+ * (Eq. "dndt"), with the paper's optional features: the covering factor
+ * (Sec. 2.3, RT_TRACE_FC), a finite speed of light with packages kept
+ * between traces (Sec. 2.1, Step 3j, rt_trace_params.light_cm), H I / He I
+ * / He II photon types (Sec. 3.2) and the adaptive timestep (Sec. 3.4,
+ * rt_timestep).  All work runs in CUDA kernels on one GPU; there is no CPU
  * fallback.
  *
  * Conventions for every call:
@@ -45,9 +49,12 @@ extern "C" {
 
 /* arithmetic of a grid */
 #define RT_FP64 0        /* traversal, optical depth and deposits in FP64 */
-#define RT_FP32_MIXED 1  /* traversal, tau and deposits in FP32; FP64 photon
-                            budget, FP64 split/termination decisions near
-                            ties, FP64 ionisation update */
+#define RT_FP32_MIXED 1  /* traversal, tau and deposits in FP32 (geometry and
+                            tau as FP32 pairs); FP64 photon budget; split,
+                            crossing and termination decisions equal to the
+                            FP64 ones (re-taken in FP64 near ties); the
+                            ionisation update in FP32 with a double-float
+                            Newton correction (~1e-13 of the FP64 one) */
 /* where a caller buffer lives */
 #define RT_MEM_HOST 0
 #define RT_MEM_DEVICE 1
