@@ -12,8 +12,11 @@ Output: one JSON line (rank 0).  ``value`` = segments/s with inputs resident
 in HBM (device-timed with CUDA events on the library's stream, L2 flushed
 between steps); ``e2e`` = the same through the C ABI with pinned host
 buffers, host->device state upload and device->host k_ph/x_HI readback inside
-the timed region.  ``--impl reference`` times the FP64 CPU oracle on the same
-step instead.
+the timed region.  Beside it: the Strömgren convergence run (1000 coupled steps
+from the neutral medium in each precision, R_IF against the closed-form R_s)
+and, in the leg that times the oracle, each GPU path's k_ph and x_HI after the
+benchmark step against the oracle's.  ``--impl reference`` times the FP64 CPU
+oracle on the same step instead.
 """
 from __future__ import annotations
 
@@ -217,9 +220,10 @@ def run_native(args, rank, world, local):
                 assert bb["segments"] == seg_per_step
         torch.cuda.synchronize()
         barrier()
+        final = grid.rates()  # one step from the snapshot: k_ph of the trace, x_HI after the update
         grid.close()
         return dict(step_ms=step_ms, kern_ms=kern_ms, segments=segs, seg_per_step=seg_per_step,
-                    pushed=pushed, launches=launches, clocks=clk.summary())
+                    pushed=pushed, launches=launches, clocks=clk.summary(), final=final)
 
     def e2e(precision):
         grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
@@ -329,8 +333,73 @@ def run_native(args, rank, world, local):
         out["batched"] = batched(args, ctx, stream, dev, world)
     if not args.no_serving and world == 1:
         out["serving"] = serving(args, ctx)
+    # the Strömgren convergence run: 500 Myr of coupled steps from the neutral medium
+    if not args.no_convergence:
+        out["stromgren_500myr"] = stromgren_500myr(ctx, stream, args.precisions)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        bench_step = args.workload == "stromgren" and args.grid == 128
+        out["cpu_baseline"], ref = cpu_baseline(args.cpu_seconds)
+        if bench_step:
+            out["precision_error"] = precision_error(g, ref, {p: res[p]["final"] for p in args.precisions})
+    return out
+
+
+def stromgren_500myr(ctx, stream, precisions) -> dict:
+    """Test 1 at 128^3 evolved over 500 Myr (1000 steps of trace + update, dt 0.5 Myr)
+    in each precision: the volume-equivalent I-front radius against the closed form
+    R_s = (3 Ndot / (4 pi alpha_B n_H^2))^(1/3) (Eq. Rstr; the analytic r_s(500 Myr)
+    is 0.9944 R_s), the two precisions against each other, and the device time of
+    the whole evolution."""
+    import torch
+    from paper_1012_2865_gb300 import native, synth
+    N = 128
+    g = synth.stromgren(N)
+    V = (g["box_len_cm"] / N) ** 3
+    rs = (3 * g["ndot"][0] / (4 * np.pi * synth.ALPHA_B * 1e-3 ** 2)) ** (1 / 3)
+    out, state = {"workload": "stromgren-128^3 from neutral, 1000 steps of 0.5 Myr",
+                  "R_s_cm": rs, "r_s_500myr_over_R_s": (1.0 - np.exp(-500 * synth.MYR_S * synth.ALPHA_B * 1e-3)) ** (1 / 3)}, {}
+    for prec in precisions:
+        grid = native.Grid(ctx, g, prec, stream=stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(1000):
+            grid.trace(sync=False, queue_capacity=1 << 22, **synth.DEFAULT_PARAMS)
+            grid.chem(DT_S, 10, synth.ALPHA_B)
+        e1.record(stream)
+        e1.synchronize()
+        b = native.rt_get_budget(grid.h)
+        z = grid.x_HII()
+        r_if = (6 * float(np.sum(z)) * V / np.pi) ** (1 / 3)
+        state[prec] = grid.rates()
+        out[prec] = {"R_IF_over_R_s": r_if / rs, "evolve_s": e0.elapsed_time(e1) / 1e3,
+                     "status": b["status"], "last_step_segments": b["segments"]}
+        grid.close()
+    if "fp32_mixed" in state and "fp64" in state:
+        a, c = state["fp32_mixed"], state["fp64"]
+        pos = c["x_HI"] > 0
+        rx = np.abs(a["x_HI"][pos] - c["x_HI"][pos]) / c["x_HI"][pos]
+        out["fp32_mixed_vs_fp64"] = {
+            "R_IF_rel": out["fp32_mixed"]["R_IF_over_R_s"] / out["fp64"]["R_IF_over_R_s"] - 1.0,
+            "x_HI_max_rel": float(rx.max()), "x_HI_median_rel": float(np.median(rx))}
+    return out
+
+
+def precision_error(g, ref, final) -> dict:
+    """Each GPU path's k_ph and x_HI after one benchmark step against the FP64 oracle's
+    step from the same snapshot: k_ph in the cells receiving more than 1e-8 of the
+    emitted photons (photon path length k_ph dx^2 / sigma), x_HI in every cell.
+    Gamma is zero on this workload (13.6 eV photons)."""
+    dx = g["box_len_cm"] / g["dims"][0]
+    kph_o, x_o, emitted = ref
+    m = kph_o * dx * dx / float(np.max(g["sigma_cm2"])) > 1e-8 * emitted
+    out = {"vs": "FP64 C oracle, the same step from the same snapshot", "cells_compared_kph": int(m.sum())}
+    for prec, r in final.items():
+        rk = np.abs(r["kph"][m] - kph_o[m]) / kph_o[m]
+        pos = x_o > 0
+        rx = np.abs(r["x_HI"][pos] - x_o[pos]) / x_o[pos]
+        out[prec] = {"kph_max_rel": float(rk.max()), "kph_median_rel": float(np.median(rk)),
+                     "x_HI_max_rel": float(rx.max()), "x_HI_median_rel": float(np.median(rx))}
     return out
 
 
@@ -543,27 +612,33 @@ def serving(args, ctx):
 
 
 def oracle_step(g, x, z):
+    """One step of the oracle: (segments, k_ph, x_HI after the update, emitted)."""
     import oracle
     from paper_1012_2865_gb300 import synth
     o = oracle.trace(g["dims"], g["box_len_cm"], g["n_H"], x, g["pos_cm"], g["ndot"], g["e_ph_eV"],
                      g["sigma_cm2"], **synth.DEFAULT_PARAMS)
-    oracle.chem(g["n_H"], x, z, o["kph"], DT_S, 10, synth.ALPHA_B)
-    return o["segments"]
+    x1, _ = oracle.chem(g["n_H"], x, z, o["kph"], DT_S, 10, synth.ALPHA_B)
+    return o["segments"], o["kph"], x1, o["budget"][0]
 
 
-def cpu_baseline(seconds: float) -> dict:
+def cpu_baseline(seconds: float):
+    """The oracle timed on the benchmark step; also returns its first step's
+    (k_ph, x_HI, emitted) for the precision report."""
     from paper_1012_2865_gb300 import synth
     g = synth.stromgren_snapshot(128)
-    segs, n = 0, 0
+    segs, n, ref = 0, 0, None
     t0 = time.perf_counter()
     while True:
-        segs += oracle_step(g, g["x_HI"], g["x_HII"])
+        s, kph, x1, em = oracle_step(g, g["x_HI"], g["x_HII"])
+        segs += s
+        if ref is None:
+            ref = (kph, x1, em)
         n += 1
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": segs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} full steps of the bench workload (FP64 C oracle, 1 thread), {dt:.1f} s"}
+    return ({"value": segs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": f"{n} full steps of the bench workload (FP64 C oracle, 1 thread), {dt:.1f} s"}, ref)
 
 
 def run_reference(args, rank, world):
@@ -578,7 +653,7 @@ def run_reference(args, rank, world):
     segs = 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        segs += oracle_step(g, g["x_HI"], g["x_HII"])
+        segs += oracle_step(g, g["x_HI"], g["x_HII"])[0]
     dt = time.perf_counter() - t0
     v = segs / dt
     return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -606,6 +681,8 @@ def main():
     ap.add_argument("--no-timestep", action="store_true", help="skip the adaptive-timestep (Sec. 3.4) leg")
     ap.add_argument("--no-fsl", action="store_true", help="skip the finite-speed-of-light (Application 5) leg")
     ap.add_argument("--no-types", action="store_true", help="skip the photon-types (Sec. 3.2) leg")
+    ap.add_argument("--no-convergence", action="store_true",
+                    help="skip the 500 Myr Strömgren evolution in each precision")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-fp64-budget-s", type=float, default=90.0)
     ap.add_argument("--grid", type=int, default=128, help="cells per side (128 = the benchmark workload)")

@@ -74,6 +74,7 @@ def assert_trace_parity(g, b, r, o, precision="fp64", exact_segments=None):
         assert abs(b["absorbed"] - o["budget"][1]) <= bt * em
         assert abs(b["escaped"] - o["budget"][2]) <= bt * em
     mask = receiving_mask(g, o["kph"], em)
+    worst = {}
     for key in ("kph", "gamma"):
         ref = o[key][mask]
         got = np.asarray(r[key], dtype=np.float64)[mask]
@@ -81,5 +82,6 @@ def assert_trace_parity(g, b, r, o, precision="fp64", exact_segments=None):
         if nz.any():
             rel = np.abs(got[nz] - ref[nz]) / np.abs(ref[nz])
             assert rel.max() <= tol, (key, float(rel.max()), int(np.argmax(rel)))
+            worst[key] = float(rel.max())
         assert np.all(got[~nz] == 0) or np.max(np.abs(got[~nz])) <= tol * max(np.abs(ref).max(), 1e-300)
-    return mask
+    return worst
