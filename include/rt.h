@@ -18,7 +18,8 @@
  *     next call on the same thread).  No exception crosses the ABI.
  *   - handles are opaque; the caller owns them and releases them with the
  *     matching *_destroy call.  A handle may be used from one host thread
- *     at a time.
+ *     at a time; grids and batches of one context may be used from
+ *     different threads (a batch and its member grids count as one handle).
  *   - a cell index is i + nx*(j + ny*k) (x fastest); all cells are cubes of
  *     width dx = box_len_cm / nx.
  *   - work is enqueued on the grid's CUDA stream (cudaStream_t passed as
@@ -311,7 +312,9 @@ int rt_set_rates(rt_grid* grid, const void* kph, const void* gamma, int dtype, i
  * (a blocking stream). */
 int rt_batch_create(rt_ctx* ctx, void* stream, rt_batch** out);
 int rt_batch_destroy(rt_batch* batch);
-/* Add a grid; *slot receives its slot number (reused after removal). */
+/* Add a grid; *slot receives its slot number (reused after removal).  A
+ * grid is in at most one batch (RT_ERR_STATE otherwise); rt_grid_destroy
+ * takes a grid out of its batch, rt_batch_destroy leaves its grids alive. */
 int rt_batch_add(rt_batch* batch, rt_grid* grid, int* slot);
 int rt_batch_remove(rt_batch* batch, int slot);
 /* Number of grids in the batch. */

@@ -89,20 +89,29 @@ struct rt_ctx {
   int device;
   int num_sms;
   // pixel directions as FP32 pairs (mixed path), levels 0..dir_levels
+  // Tables replaced by a deeper one stay allocated until the context is
+  // destroyed: a trace enqueued from another thread may still hold them.
   std::mutex dir_mu;
   float4* dir_tab = nullptr;
   int dir_levels = -1;
+  std::vector<float4*> dir_retired;
   ~rt_ctx() {
     if (dir_tab) cudaFree(dir_tab);
+    for (float4* t : dir_retired) cudaFree(t);
   }
 };
 
 constexpr int kDirTableMaxLevel = 9;  // 4.2M pixels, 134 MB
 
-// Make sure the direction table holds levels 0..want (want <= 9).
-static int ensure_dir_table(rt_ctx* c, int want) {
+// Make sure the direction table holds levels 0..want (want <= 9); the table
+// and its deepest level are returned as read under the lock.
+static int ensure_dir_table(rt_ctx* c, int want, const float4** tab, int* levels) {
   std::lock_guard<std::mutex> lk(c->dir_mu);
-  if (want <= c->dir_levels) return RT_OK;
+  if (want <= c->dir_levels) {
+    *tab = c->dir_tab;
+    *levels = c->dir_levels;
+    return RT_OK;
+  }
   const size_t entries = (size_t)4 * (((size_t)1 << (2 * (want + 1))) - 1);
   float4* t = nullptr;
   CUDA_TRY(cudaMalloc(&t, entries * 2 * sizeof(float4)));
@@ -113,9 +122,11 @@ static int ensure_dir_table(rt_ctx* c, int want) {
   }
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) { cudaFree(t); return fail(RT_ERR_CUDA, "direction table: %s", cudaGetErrorString(e)); }
-  if (c->dir_tab) cudaFree(c->dir_tab);
+  if (c->dir_tab) c->dir_retired.push_back(c->dir_tab);
   c->dir_tab = t;
   c->dir_levels = want;
+  *tab = t;
+  *levels = want;
   return RT_OK;
 }
 
@@ -201,6 +212,8 @@ struct rt_grid {
   void* host_rb = nullptr;
   bool traced = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last trace kernel
+  rt_batch* batch = nullptr;                 // the batch holding the grid (at most one)
+  int batch_slot = -1;
   cudaStream_t batch_stream = nullptr;       // set while the grid is in a batch
   ~rt_grid() {
     cudaFree(nH); cudaFree(xHI); cudaFree(xHII); cudaFree(nhi); cudaFree(K); cudaFree(G);
@@ -238,6 +251,9 @@ static int wait_batch(rt_grid* g) {
   return RT_OK;
 }
 
+// Take a grid out of its batch (defined with the batches).
+static void detach_grid(rt_grid* g);
+
 extern "C" {
 
 const char* rt_get_last_error(void) { return g_last_error.c_str(); }
@@ -250,9 +266,11 @@ int rt_ctx_create(int device, rt_ctx** out) {
   CUDA_TRY(cudaGetDeviceCount(&n));
   if (device < 0 || device >= n) return fail(RT_ERR_INVALID_ARG, "rt_ctx_create: device %d of %d", device, n);
   CUDA_TRY(cudaSetDevice(device));
+  int num_sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
   rt_ctx* c = new rt_ctx;
   c->device = device;
-  CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  c->num_sms = num_sms;
   *out = c;
   g_last_error.clear();
   return RT_OK;
@@ -367,6 +385,7 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
 int rt_grid_destroy(rt_grid* g) {
   if (!g) return RT_OK;
   wait_batch(g);
+  if (g->batch) detach_grid(g);
   cudaStreamSynchronize(g->stream);
   delete g;
   return RT_OK;
@@ -745,10 +764,8 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool 
     int need = p->level0;
     while (need < p->max_level && A.rsplit[need] < diag) ++need;
     const int want = need < kDirTableMaxLevel ? need : kDirTableMaxLevel;
-    int rc2 = ensure_dir_table(g->ctx, want);
+    int rc2 = ensure_dir_table(g->ctx, want, &A.dir_tab, &A.dir_levels);
     if (rc2) return rc2;
-    A.dir_tab = g->ctx->dir_tab;
-    A.dir_levels = g->ctx->dir_levels;
   }
   A.queue = g->ts.queue;
   A.cap = g->ts.cap;
@@ -1380,9 +1397,7 @@ static int batch_enqueue(rt_batch* b, const rt_trace_params* p, int passes) {
     int want = p->level0;
     while (want < p->max_level && A.rsplit[want] < b->max_diag) ++want;
     if (want > kDirTableMaxLevel) want = kDirTableMaxLevel;
-    if ((rc = ensure_dir_table(b->ctx, want))) return rc;
-    A.dir_tab = b->ctx->dir_tab;
-    A.dir_levels = b->ctx->dir_levels;
+    if ((rc = ensure_dir_table(b->ctx, want, &A.dir_tab, &A.dir_levels))) return rc;
   }
   int per_sm = 0;
   CUDA_TRY(trace_occupancy(b->precision, 0, 256, &per_sm));
@@ -1434,6 +1449,18 @@ static int batch_status(rt_batch* b, BatchStatus* bs) {
   return RT_OK;
 }
 
+static void detach_grid(rt_grid* g) {
+  rt_batch* b = g->batch;
+  b->slots[g->batch_slot] = nullptr;
+  b->dirty = true;
+  bool any = false;
+  for (rt_grid* h : b->slots) any |= h != nullptr;
+  if (!any) b->precision = -1;
+  g->batch = nullptr;
+  g->batch_slot = -1;
+  g->batch_stream = nullptr;
+}
+
 extern "C" {
 
 int rt_batch_create(rt_ctx* ctx, void* stream, rt_batch** out) {
@@ -1466,7 +1493,11 @@ int rt_batch_destroy(rt_batch* b) {
   if (!b) return RT_OK;
   cudaStreamSynchronize(b->stream);
   for (rt_grid* g : b->slots)
-    if (g) g->batch_stream = nullptr;
+    if (g) {
+      g->batch = nullptr;
+      g->batch_slot = -1;
+      g->batch_stream = nullptr;
+    }
   delete b;
   return RT_OK;
 }
@@ -1476,8 +1507,7 @@ int rt_batch_add(rt_batch* b, rt_grid* g, int* slot) {
   if (g->ctx != b->ctx) return fail(RT_ERR_INVALID_ARG, "rt_batch_add: grid belongs to another context");
   if (b->precision >= 0 && g->precision != b->precision)
     return fail(RT_ERR_INVALID_ARG, "rt_batch_add: every grid of a batch has the same precision");
-  for (rt_grid* h : b->slots)
-    if (h == g) return fail(RT_ERR_STATE, "rt_batch_add: grid is already in the batch");
+  if (g->batch) return fail(RT_ERR_STATE, "rt_batch_add: grid is already in a batch");
   CUDA_TRY(cudaStreamSynchronize(g->stream));  // work already queued on the grid's own stream
   drop_flight(g);  // batches trace with an infinite speed of light
   b->precision = g->precision;
@@ -1489,6 +1519,8 @@ int rt_batch_add(rt_batch* b, rt_grid* g, int* slot) {
     b->slots.push_back(nullptr);
   }
   b->slots[s] = g;
+  g->batch = b;
+  g->batch_slot = s;
   g->batch_stream = b->stream;
   b->dirty = true;
   *slot = s;
@@ -1499,12 +1531,7 @@ int rt_batch_remove(rt_batch* b, int slot) {
   if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot])
     return fail(RT_ERR_INVALID_ARG, "rt_batch_remove: no grid in slot %d", slot);
   CUDA_TRY(cudaStreamSynchronize(b->stream));
-  b->slots[slot]->batch_stream = nullptr;
-  b->slots[slot] = nullptr;
-  b->dirty = true;
-  bool any = false;
-  for (rt_grid* h : b->slots) any |= h != nullptr;
-  if (!any) b->precision = -1;
+  detach_grid(b->slots[slot]);
   return RT_OK;
 }
 

@@ -112,6 +112,39 @@ def test_batch_remove_add_and_autotune():
     batch.close()
 
 
+def test_a_grid_is_in_one_batch_and_leaves_it_when_destroyed():
+    ctx = parity.ctx()
+    gs = _grids(seed=9, n=3)
+    b1, b2 = native.Batch(ctx), native.Batch(ctx)
+    grids = [native.Grid(ctx, g, "fp32_mixed") for g in gs]
+    slots = [b1.add(gr) for gr in grids]
+    for b in (b1, b2):
+        with pytest.raises(native.RtError):
+            b.add(grids[0])  # already a member of b1
+    b1.trace(checksums=True, **synth.DEFAULT_PARAMS)
+    grids[1].close()  # destroying a member takes it out of its batch
+    b1.grids.pop(slots[1])
+    assert native.rt_batch_size(b1.h) == len(gs) - 1
+    b1.trace(checksums=True, **synth.DEFAULT_PARAMS)
+    for i in (0, 2, 3):
+        alone = native.Grid(ctx, gs[i], "fp32_mixed")
+        b_ref = alone.trace(checksums=True, **synth.DEFAULT_PARAMS)
+        _compare(b1.budget(slots[i]), grids[i].rates(), b_ref, alone.rates(), SUM_ORDER_TOL["fp32_mixed"])
+        alone.close()
+    b1.remove(slots[0])
+    s0 = b2.add(grids[0])  # free to join another batch once removed
+    b2.trace(checksums=True, **synth.DEFAULT_PARAMS)
+    alone = native.Grid(ctx, gs[0], "fp32_mixed")
+    b_ref = alone.trace(checksums=True, **synth.DEFAULT_PARAMS)
+    _compare(b2.budget(s0), grids[0].rates(), b_ref, alone.rates(), SUM_ORDER_TOL["fp32_mixed"])
+    alone.close()
+    b1.close()  # members outlive their batch
+    grids[2].trace(**synth.DEFAULT_PARAMS)
+    for gr in grids:
+        gr.close()
+    b2.close()
+
+
 def test_batch_on_a_non_blocking_stream_orders_member_work():
     """A batch on a caller's non-blocking stream sees state set on its grids' streams."""
     import torch
