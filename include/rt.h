@@ -179,7 +179,9 @@ typedef struct {
  * x *= 0x81dadef4bc2dd44d; x ^= x>>33.  src counts from 0 in the order the
  * grid's sources were added. */
 
-/* Context: one CUDA device.  device >= 0. */
+/* Context: one CUDA device.  device >= 0.  It owns the pixel-direction
+ * table of the FP32-mixed path (built on first use); its grids and batches
+ * are destroyed before it. */
 int rt_ctx_create(int device, rt_ctx** out);
 int rt_ctx_destroy(rt_ctx* ctx);
 
