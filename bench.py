@@ -232,7 +232,9 @@ def run_native(args, rank, world, local):
         n = grid.ncell
         hx = torch.tensor(g["x_HI"], dtype=torch.float64).pin_memory()
         hz = torch.tensor(g["x_HII"], dtype=torch.float64).pin_memory()
-        hk = torch.empty(n, dtype=torch.float64).pin_memory()
+        # k_ph in the path's own precision (FP32 on the mixed path), x_HI in FP64
+        kdt = native.RT_DTYPE_F64 if precision == "fp64" else native.RT_DTYPE_F32
+        hk = torch.empty(n, dtype=torch.float64 if precision == "fp64" else torch.float32).pin_memory()
         hxo = torch.empty(n, dtype=torch.float64).pin_memory()
         lib = native.lib()
         segs = 0
@@ -243,13 +245,14 @@ def run_native(args, rank, world, local):
             native.check(lib.rt_set_state(grid.h, None, hx.data_ptr(), hz.data_ptr(), native.RT_MEM_HOST))
             grid.trace(sync=False, **qp)
             grid.chem(DT_S, 10, synth.ALPHA_B)
-            native.check(lib.rt_get_rates(grid.h, hk.data_ptr(), None, hxo.data_ptr(),
-                                          native.RT_DTYPE_F64, native.RT_MEM_HOST))
+            native.check(lib.rt_get_rates(grid.h, hk.data_ptr(), None, None, kdt, native.RT_MEM_HOST))
+            native.check(lib.rt_get_rates(grid.h, None, None, hxo.data_ptr(), native.RT_DTYPE_F64,
+                                          native.RT_MEM_HOST))
             if i >= max(3, args.warmup):
                 segs += native.rt_get_budget(grid.h)["segments"]
         dt = time.perf_counter() - t0
         grid.close()
-        return dict(value=segs / dt, h2d=2 * n * 8, d2h=2 * n * 8)
+        return dict(value=segs / dt, h2d=2 * n * 8, d2h=n * (hk.element_size() + 8))
 
     res = {}
     for prec in args.precisions:
