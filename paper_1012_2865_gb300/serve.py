@@ -48,9 +48,14 @@ class Request:
 
 
 class Server:
+    """`mem_info` (free device bytes) and `backend` (a module with the
+    native.Grid and native.Batch classes) may be replaced, so that the
+    scheduling can be exercised without a device."""
+
     def __init__(self, ctx, precision: str = "fp32_mixed", max_slots: int = 64,
                  reserve_bytes: int = 4 << 30, dt_s: float = 0.5 * synth.MYR_S, nsub: int = 10,
-                 alpha_B: float = synth.ALPHA_B, params: dict = None, mem_info=None):
+                 alpha_B: float = synth.ALPHA_B, params: dict = None, mem_info=None, backend=None):
+        self.backend = backend if backend is not None else native
         self.ctx = ctx
         self.precision = precision
         self.max_slots = max_slots
@@ -59,10 +64,11 @@ class Server:
         self.params = dict(synth.DEFAULT_PARAMS)
         if params:
             self.params.update(params)
-        self.batch = native.Batch(ctx)
+        self.batch = self.backend.Batch(ctx)
         self.pending = collections.deque()
         self.active = {}
         self.done = []
+        self.rejected = []
         self.steps = 0
         self.segments = 0
         self._mem_info = mem_info
@@ -77,15 +83,23 @@ class Server:
         self.pending.append(req)
 
     def admit(self, now: float) -> int:
-        """Admit pending requests while a slot and device memory are free."""
+        """Admit pending requests while a slot and device memory are free.  A
+        request that does not fit while nothing else is resident never will:
+        it is rejected (kept in `rejected`) instead of blocking the queue."""
         n = 0
         while self.pending and len(self.active) < self.max_slots:
             req = self.pending[0]
             need = grid_bytes(int(np.prod(req.grid["dims"])), self.precision)
             if self.free_bytes() - need < self.reserve:
-                break
+                if self.active:
+                    break
+                self.pending.popleft()
+                req.finished = now
+                req.meta["rejected"] = f"needs {need} bytes beyond the {self.reserve}-byte reserve"
+                self.rejected.append(req)
+                continue
             self.pending.popleft()
-            req.handle = native.Grid(self.ctx, req.grid, self.precision)
+            req.handle = self.backend.Grid(self.ctx, req.grid, self.precision)
             req.slot = self.batch.add(req.handle)
             req.admitted = now
             self.active[req.slot] = req
@@ -138,7 +152,8 @@ class Server:
 
     def report(self, wall_s: float) -> dict:
         lat = np.array([r.latency for r in self.done]) if self.done else np.array([np.nan])
-        return dict(completed=len(self.done), wall_s=wall_s, steps=self.steps, segments=self.segments,
+        return dict(completed=len(self.done), rejected=len(self.rejected), wall_s=wall_s, steps=self.steps,
+                    segments=self.segments,
                     segments_per_s=self.segments / wall_s if wall_s > 0 else 0.0,
                     p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
                     requests_per_s=len(self.done) / wall_s if wall_s > 0 else 0.0)

@@ -1,0 +1,130 @@
+"""The serving loop's scheduling on the host, with a stand-in for the device
+library (no GPU): admission by free slots and free device memory, continuous
+batching (requests that arrive while others run join between steps),
+retirement after their own number of steps, latency accounting, and the
+rejection of a request that can never fit instead of a stalled queue.
+"""
+import time
+import types
+
+import numpy as np
+
+from paper_1012_2865_gb300 import serve
+
+
+class FakeGrid:
+    live = []
+
+    def __init__(self, ctx, g, precision):
+        self.ncell = int(np.prod(g["dims"]))
+        self.precision = precision
+        FakeGrid.live.append(self)
+
+    def rates(self):
+        return {"x_HI": np.zeros(self.ncell), "kph": np.ones(self.ncell)}
+
+    def close(self):
+        if self in FakeGrid.live:
+            FakeGrid.live.remove(self)
+
+
+class FakeBatch:
+    step_s = 0.0
+
+    def __init__(self, ctx):
+        self.slots = {}
+        self.sizes = []
+
+    def add(self, grid):
+        s = next(i for i in range(len(self.slots) + 1) if i not in self.slots)
+        self.slots[s] = grid
+        return s
+
+    def remove(self, slot):
+        del self.slots[slot]
+
+    def trace(self, sync=True, **kw):
+        self.sizes.append(len(self.slots))
+        if FakeBatch.step_s:
+            time.sleep(FakeBatch.step_s)
+
+    def chem(self, dt_s, nsub, alpha_B):
+        pass
+
+    def budget(self, slot):
+        return {"segments": self.slots[slot].ncell}
+
+    def close(self):
+        pass
+
+
+BACKEND = types.SimpleNamespace(Grid=FakeGrid, Batch=FakeBatch)
+
+
+def _request(rid, N, nsteps, arrival=0.0):
+    g = {"dims": (N, N, N)}
+    return serve.Request(rid=rid, grid=g, nsteps=nsteps, arrival=arrival)
+
+
+def _server(total_bytes, reserve, max_slots, precision="fp32_mixed"):
+    def free():
+        used = sum(serve.grid_bytes(gr.ncell, gr.precision) for gr in FakeGrid.live)
+        return total_bytes - used
+    FakeGrid.live.clear()
+    return serve.Server(None, precision, max_slots=max_slots, reserve_bytes=reserve, mem_info=free,
+                        backend=BACKEND)
+
+
+def test_admission_by_slots_and_memory():
+    FakeBatch.step_s = 0.0
+    one = serve.grid_bytes(16 ** 3, "fp32_mixed")
+    reqs = [_request(i, 16, nsteps=1 + i % 3) for i in range(9)]
+    # memory for two grids above the reserve, three slots: memory binds
+    srv = _server(total_bytes=1000 + 2 * one, reserve=1000, max_slots=3)
+    rep = srv.run(reqs)
+    assert rep["completed"] == 9 and rep["rejected"] == 0
+    assert max(srv.batch.sizes) == 2
+    for r in srv.done:
+        assert r.steps_done == r.nsteps
+        assert r.segments == r.nsteps * 16 ** 3
+        assert r.admitted >= r.arrival and r.finished >= r.admitted and r.latency >= 0
+    assert rep["segments"] == sum(r.nsteps for r in reqs) * 16 ** 3
+    assert not FakeGrid.live  # every retired grid was released
+    # plenty of memory, two slots: slots bind
+    srv = _server(total_bytes=1 << 40, reserve=0, max_slots=2)
+    srv.run([_request(i, 16, nsteps=2) for i in range(5)])
+    assert max(srv.batch.sizes) == 2 and len(srv.done) == 5
+
+
+def test_requests_join_while_others_run():
+    FakeBatch.step_s = 0.004
+    reqs = [_request(0, 20, nsteps=12, arrival=0.0), _request(1, 12, nsteps=3, arrival=0.015),
+            _request(2, 24, nsteps=4, arrival=0.02)]
+    srv = _server(total_bytes=1 << 40, reserve=0, max_slots=8)
+    rep = srv.run(reqs)
+    FakeBatch.step_s = 0.0
+    assert rep["completed"] == 3
+    done = {r.rid: r for r in srv.done}
+    # the later requests were admitted while the first was still on the device ...
+    assert done[1].admitted < done[0].finished and done[2].admitted < done[0].finished
+    # ... and the short one left before it
+    assert done[1].finished < done[0].finished
+    assert max(srv.batch.sizes) >= 2
+    assert rep["p99_ms"] >= rep["p50_ms"] > 0
+
+
+def test_a_request_that_never_fits_is_rejected():
+    FakeBatch.step_s = 0.0
+    small = serve.grid_bytes(16 ** 3, "fp64")
+    reqs = [_request(0, 64, nsteps=1), _request(1, 16, nsteps=2), _request(2, 16, nsteps=1)]
+    srv = _server(total_bytes=10 * small, reserve=0, max_slots=4, precision="fp64")
+    rep = srv.run(reqs)
+    assert rep["rejected"] == 1 and srv.rejected[0].rid == 0
+    assert "rejected" in srv.rejected[0].meta
+    assert rep["completed"] == 2 and sorted(r.rid for r in srv.done) == [1, 2]
+
+
+def test_grid_bytes_counts_the_resident_fields():
+    # n_H, x_HI, x_HII in FP64; n_HI, k_ph, Gamma in FP64 or (FP32 pair, FP32, FP32)
+    assert serve.grid_bytes(1, "fp64") == 3 * 8 + 3 * 8
+    assert serve.grid_bytes(1, "fp32_mixed") == 3 * 8 + 8 + 4 + 4
