@@ -179,9 +179,9 @@ def _thin_scatter(N, phi_c, src):
     X = (i[None, None, :] - (src[0] + 0.5)) ** 2 + (i[None, :, None] - (src[1] + 0.5)) ** 2 + \
         (i[:, None, None] - (src[2] + 0.5)) ** 2
     rc = np.sqrt(X).reshape(-1) * dx
-    k_thin = g["sigma_cm2"][0] * g["ndot"][0] / (4 * np.pi * rc ** 2)
     sel = (rc > 3 * dx) & (rc < (N / 2 - 2) * dx)
-    return r["kph"][sel] / k_thin[sel] - 1.0
+    k_thin = g["sigma_cm2"][0] * g["ndot"][0] / (4 * np.pi * rc[sel] ** 2)
+    return r["kph"][sel] / k_thin - 1.0
 
 
 def test_optically_thin_inverse_square():
