@@ -48,13 +48,14 @@ class Request:
 
 
 class Server:
-    """`mem_info` (free device bytes) and `backend` (a module with the
-    native.Grid and native.Batch classes) may be replaced, so that the
-    scheduling can be exercised without a device."""
+    """`mem_info` (free device bytes), `mem_total` (the device's bytes) and
+    `backend` (a module with the native.Grid and native.Batch classes) may be
+    replaced, so that the scheduling can be exercised without a device."""
 
     def __init__(self, ctx, precision: str = "fp32_mixed", max_slots: int = 64,
                  reserve_bytes: int = 4 << 30, dt_s: float = 0.5 * synth.MYR_S, nsub: int = 10,
-                 alpha_B: float = synth.ALPHA_B, params: dict = None, mem_info=None, backend=None):
+                 alpha_B: float = synth.ALPHA_B, params: dict = None, mem_info=None, backend=None,
+                 mem_total=None):
         self.backend = backend if backend is not None else native
         self.ctx = ctx
         self.precision = precision
@@ -72,6 +73,7 @@ class Server:
         self.steps = 0
         self.segments = 0
         self._mem_info = mem_info
+        self._mem_total = mem_total
 
     def free_bytes(self) -> int:
         if self._mem_info is not None:
@@ -79,25 +81,34 @@ class Server:
         import torch
         return torch.cuda.mem_get_info()[0]
 
+    def total_bytes(self) -> int:
+        if self._mem_total is not None:
+            return self._mem_total()
+        import torch
+        return torch.cuda.mem_get_info()[1]
+
     def submit(self, req: Request):
         self.pending.append(req)
 
     def admit(self, now: float) -> int:
-        """Admit pending requests while a slot and device memory are free.  A
-        request that does not fit while nothing else is resident never will:
-        it is rejected (kept in `rejected`) instead of blocking the queue."""
+        """Admit pending requests while a slot and device memory are free.
+        A request waits while the memory is taken (by this server's grids or
+        by other users of the device); one larger than the whole device minus
+        the reserve can never be admitted and is rejected (kept in
+        `rejected`) instead of holding up the queue."""
         n = 0
         while self.pending and len(self.active) < self.max_slots:
             req = self.pending[0]
             need = grid_bytes(int(np.prod(req.grid["dims"])), self.precision)
-            if self.free_bytes() - need < self.reserve:
-                if self.active:
-                    break
+            if need > self.total_bytes() - self.reserve:
                 self.pending.popleft()
                 req.finished = now
-                req.meta["rejected"] = f"needs {need} bytes beyond the {self.reserve}-byte reserve"
+                req.meta["rejected"] = f"needs {need} bytes; the device holds {self.total_bytes()}, " \
+                                       f"{self.reserve} of them reserved"
                 self.rejected.append(req)
                 continue
+            if self.free_bytes() - need < self.reserve:
+                break
             self.pending.popleft()
             req.handle = self.backend.Grid(self.ctx, req.grid, self.precision)
             req.slot = self.batch.add(req.handle)
@@ -144,6 +155,8 @@ class Server:
             self.admit(t)
             if self.active:
                 self.step(now)
+            elif self.pending:
+                time.sleep(0.001)  # waiting for device memory held elsewhere
             elif todo:
                 time.sleep(max(0.0, min(todo[0].arrival - now(), 0.01)))
             if time_limit_s is not None and now() > time_limit_s:

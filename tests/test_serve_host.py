@@ -14,11 +14,14 @@ from paper_1012_2865_gb300 import serve
 
 class FakeGrid:
     live = []
+    made = []
 
     def __init__(self, ctx, g, precision):
         self.ncell = int(np.prod(g["dims"]))
         self.precision = precision
+        self.created = time.perf_counter()
         FakeGrid.live.append(self)
+        FakeGrid.made.append(self)
 
     def rates(self):
         return {"x_HI": np.zeros(self.ncell), "kph": np.ones(self.ncell)}
@@ -66,13 +69,15 @@ def _request(rid, N, nsteps, arrival=0.0):
     return serve.Request(rid=rid, grid=g, nsteps=nsteps, arrival=arrival)
 
 
-def _server(total_bytes, reserve, max_slots, precision="fp32_mixed"):
+def _server(total_bytes, reserve, max_slots, precision="fp32_mixed", held=lambda: 0):
+    """A server on a device of `total_bytes`, of which `held()` belongs to
+    other users of the device."""
     def free():
         used = sum(serve.grid_bytes(gr.ncell, gr.precision) for gr in FakeGrid.live)
-        return total_bytes - used
+        return total_bytes - used - held()
     FakeGrid.live.clear()
     return serve.Server(None, precision, max_slots=max_slots, reserve_bytes=reserve, mem_info=free,
-                        backend=BACKEND)
+                        mem_total=lambda: total_bytes, backend=BACKEND)
 
 
 def test_admission_by_slots_and_memory():
@@ -111,6 +116,21 @@ def test_requests_join_while_others_run():
     assert done[1].finished < done[0].finished
     assert max(srv.batch.sizes) >= 2
     assert rep["p99_ms"] >= rep["p50_ms"] > 0
+
+
+def test_a_request_waits_for_memory_held_elsewhere():
+    FakeBatch.step_s = 0.0
+    one = serve.grid_bytes(16 ** 3, "fp32_mixed")
+    t0 = time.perf_counter()
+    # another user of the device holds all of it for the first 30 ms
+    held = lambda: 4 * one if time.perf_counter() - t0 < 0.03 else 0  # noqa: E731
+    srv = _server(total_bytes=4 * one, reserve=0, max_slots=4, held=held)
+    srv.submit(_request(0, 16, nsteps=1))
+    assert srv.admit(0.0) == 0 and len(srv.pending) == 1 and not srv.rejected
+    FakeGrid.made.clear()
+    rep = srv.run([_request(1, 16, nsteps=2, arrival=0.0)])
+    assert rep["completed"] == 2 and rep["rejected"] == 0
+    assert len(FakeGrid.made) == 2 and min(gr.created for gr in FakeGrid.made) >= t0 + 0.03
 
 
 def test_a_request_that_never_fits_is_rejected():
