@@ -46,14 +46,15 @@ constexpr size_t na_align(size_t v) { return (v + 255) & ~(size_t)255; }
 constexpr int kNaTableLevels = 6;  // directions of levels 0..6 (deeper levels: FP64 on the fly)
 constexpr size_t kNaTableEntries = 4 * ((size_t(1) << (2 * (kNaTableLevels + 1))) - 1);
 constexpr size_t kNaCtlOff = 0;     // CTL_N control words
-constexpr size_t kNaAccOff = 512;   // 4 doubles
+constexpr size_t kNaAccOff = 512;   // kNaAccWords doubles (the trace's budget sums)
 constexpr size_t kNaCntOff = 640;   // kCntWords counters
+constexpr int kNaAccWords = 8;      // emitted, absorbed, escaped, resumed, halted; spare
 constexpr size_t kNaInstOff = 1024; // one InstDev
 constexpr size_t kNaSrcOff = 2048;  // RT_NOALLOC_MAX_SOURCES SourceDev
 constexpr size_t kNaTabOff = na_align(kNaSrcOff + (size_t)RT_NOALLOC_MAX_SOURCES * sizeof(SourceDev));
 constexpr size_t kNaQueueOff = na_align(kNaTabOff + kNaTableEntries * 2 * sizeof(float4));
 constexpr size_t kNaBytes = kNaQueueOff + (size_t)RT_NOALLOC_MAX_RECORDS * sizeof(Rec32);
-static_assert(CTL_N * 8 <= kNaAccOff && kNaAccOff + 32 <= kNaCntOff && kNaCntOff + kCntWords * 8 <= kNaInstOff &&
+static_assert(CTL_N * 8 <= kNaAccOff && kNaAccOff + kNaAccWords * 8 <= kNaCntOff && kNaCntOff + kCntWords * 8 <= kNaInstOff &&
                   sizeof(InstDev) <= kNaSrcOff - kNaInstOff,
               "scratch layout");
 
@@ -152,7 +153,7 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
   // Step 2: zero the outputs and the budget sums (no allocation: memsets)
   if ((e = cudaMemsetAsync(g->kph, 0, ncell * sizeof(float), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(g->gamma, 0, ncell * sizeof(float), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(acc, 0, 4 * sizeof(double), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(acc, 0, kNaAccWords * sizeof(double), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(cnt, 0, kCntWords * sizeof(unsigned long long), st)) != cudaSuccess)
     return na_fail(RT_ERR_CUDA, "clearing outputs", e);
 
