@@ -1,0 +1,49 @@
+"""Host-side pieces of the benchmark, without a GPU: the clock summary parsed
+from nvidia-smi lines, the profiled DRAM traffic that holds only while the
+trace kernel's sources are unchanged, and the precision report's masks and
+error measures.
+"""
+import numpy as np
+
+import bench
+from paper_1012_2865_gb300 import synth
+
+
+def test_clock_summary():
+    c = bench.ClockSampler(0)
+    c.lines = ["2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "2002, 2070, 1100.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "1980, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "garbage line",
+               "[N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2002.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = []
+    assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_profiled_traffic_holds_only_for_the_profiled_sources(monkeypatch):
+    t = bench._profiled_traffic("fp32_mixed", "stromgren128")
+    assert t is not None and 1e6 < t < 1e9  # the committed summary matches the sources
+    assert bench._profiled_traffic("fp32_mixed", "no_such_workload") is None
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda: "0" * 64)
+    assert bench._profiled_traffic("fp32_mixed", "stromgren128") is None
+
+
+def test_precision_report():
+    g = synth.stromgren_snapshot(32)
+    n = g["n_H"].size
+    rng = np.random.default_rng(0)
+    kph = rng.uniform(1e-14, 1e-12, n)
+    kph[:10] = 0.0  # cells receiving nothing are not compared
+    x = rng.uniform(1e-6, 1.0, n)
+    emitted = 1e40
+    ref = (kph, x, emitted)
+    final = {"fp64": {"kph": kph.copy(), "x_HI": x.copy()},
+             "fp32_mixed": {"kph": kph * (1 + 3e-6), "x_HI": x * (1 - 1e-6)}}
+    rep = bench.precision_error(g, ref, final)
+    assert rep["cells_compared_kph"] == n - 10
+    assert rep["fp64"]["kph_max_rel"] == 0.0 and rep["fp64"]["x_HI_max_rel"] == 0.0
+    np.testing.assert_allclose(rep["fp32_mixed"]["kph_max_rel"], 3e-6, rtol=1e-6)
+    np.testing.assert_allclose(rep["fp32_mixed"]["x_HI_median_rel"], 1e-6, rtol=1e-6)
