@@ -60,3 +60,14 @@ def test_error_message_without_gpu_is_reported_not_raised_from_c():
     rc = L.rt_ctx_create(-1, ctypes.byref(h))
     assert rc != 0
     assert len(L.rt_get_last_error()) > 0
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the built library every call raises: there is no CPU fallback."""
+    import pytest
+    monkeypatch.setattr(native, "_lib", None)
+    monkeypatch.setattr(native, "LIB", native.LIB + ".absent")
+    with pytest.raises(RuntimeError, match="no fallback"):
+        native.lib()
+    with pytest.raises(RuntimeError):
+        native.rt_ctx_create(0)
