@@ -191,6 +191,8 @@ int rt_ctx_destroy(rt_ctx* ctx);
  * the device; RT_ERR_INVALID_ARG names the first failing cell).
  * stream: cudaStream_t for all later work on this grid. */
 int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* desc, void* stream, rt_grid** out);
+/* Wait for the grid's work, take it out of its batch (if any) and free its
+ * device memory.  NULL is accepted. */
 int rt_grid_destroy(rt_grid* grid);
 
 /* Append n point sources (Sec. 2.1, Step 1).  Host arrays, copied:
@@ -199,6 +201,8 @@ int rt_grid_destroy(rt_grid* grid);
  *   (>= 0).  Sources keep the order of addition (their index in hashes). */
 int rt_add_sources(rt_grid* grid, int n, const double* pos_cm, const double* ndot,
                    const double* e_ph_eV, const double* sigma_cm2);
+/* Remove every source; packages in flight (finite speed of light) are
+ * dropped with them. */
 int rt_clear_sources(rt_grid* grid);
 /* Index of the grid's first source in the created-set checksum (default 0):
  * a grid that holds sources [first, first + n) of a larger set (one shard of
@@ -313,11 +317,14 @@ int rt_set_rates(rt_grid* grid, const void* kph, const void* gamma, int dtype, i
 /* stream: cudaStream_t for the batch's work; NULL = the batch creates its own
  * (a blocking stream). */
 int rt_batch_create(rt_ctx* ctx, void* stream, rt_batch** out);
+/* Wait for the batch's work and free it; its grids stay alive. */
 int rt_batch_destroy(rt_batch* batch);
 /* Add a grid; *slot receives its slot number (reused after removal).  A
  * grid is in at most one batch (RT_ERR_STATE otherwise); rt_grid_destroy
  * takes a grid out of its batch, rt_batch_destroy leaves its grids alive. */
 int rt_batch_add(rt_batch* batch, rt_grid* grid, int* slot);
+/* Take the grid in `slot` out of the batch (after the batch's work); the
+ * slot is then free.  RT_ERR_INVALID_ARG for an empty slot. */
 int rt_batch_remove(rt_batch* batch, int slot);
 /* Number of grids in the batch. */
 int rt_batch_size(rt_batch* batch);
@@ -390,6 +397,7 @@ typedef struct {
 int rt_trace_noalloc(const rt_noalloc_grid* grid, int nsrc, const double* pos_cm, const double* ndot,
                      const double* e_ph_eV, const double* sigma_cm2, const rt_trace_params* params,
                      void* stream, rt_budget* out);
+/* Message for the last failed rt_trace_noalloc on this host thread. */
 const char* rt_noalloc_last_error(void);
 
 /* Wait for all work enqueued on the grid's stream. */
