@@ -311,7 +311,9 @@ int rt_set_rates(rt_grid* grid, const void* kph, const void* gamma, int dtype, i
  * (up to the order of floating-point sums).  All grids of a batch have the
  * same precision and context.  Batch launches start after the work already
  * queued on each member grid's own stream (rt_set_state, say); per-grid calls
- * on a member wait for the batch's stream first.  Queue sizing and
+ * on a member wait for the batch's stream first.  Changes to a member's
+ * sources (rates, types, offset) or absorbers take effect at the batch's
+ * next launch (its tables and captured step are rebuilt).  Queue sizing and
  * source passes follow rt_trace.
  * ------------------------------------------------------------------------- */
 /* stream: cudaStream_t for the batch's work; NULL = the batch creates its own

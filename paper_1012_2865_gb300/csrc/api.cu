@@ -251,8 +251,10 @@ static int wait_batch(rt_grid* g) {
   return RT_OK;
 }
 
-// Take a grid out of its batch (defined with the batches).
+// Take a grid out of its batch; have its batch rebuild its tables before
+// the next launch (both defined with the batches).
 static void detach_grid(rt_grid* g);
+static void mark_batch_dirty(rt_grid* g);
 
 extern "C" {
 
@@ -418,6 +420,7 @@ int rt_add_sources(rt_grid* g, int n, const double* pos, const double* ndot, con
     g->src.push_back(S);
   }
   g->src_dirty = true;
+  mark_batch_dirty(g);
   return RT_OK;
 }
 
@@ -427,6 +430,7 @@ int rt_set_source_offset(rt_grid* g, int first) {
     return fail(RT_ERR_INVALID_ARG, "rt_set_source_offset: first = %d", first);
   g->src_offset = first;
   g->src_dirty = true;
+  mark_batch_dirty(g);
   return RT_OK;
 }
 
@@ -443,6 +447,7 @@ int rt_clear_sources(rt_grid* g) {
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_clear_sources: grid is NULL");
   g->src.clear();
   g->src_dirty = true;
+  mark_batch_dirty(g);
   drop_flight(g);
   return RT_OK;
 }
@@ -456,6 +461,7 @@ int rt_set_source_rates(rt_grid* g, int n, const double* ndot) {
     if (!(ndot[i] >= 0) || !isfinite(ndot[i])) return fail(RT_ERR_INVALID_ARG, "rt_set_source_rates: ndot[%d] = %g", i, ndot[i]);
   for (int i = 0; i < n; ++i) g->src[i].ndot = ndot[i];
   g->src_dirty = true;
+  mark_batch_dirty(g);
   return RT_OK;
 }
 
@@ -1053,6 +1059,7 @@ int rt_set_absorbers(rt_grid* g, const double* n_HeI, const double* n_HeII, int 
   }
   cudaFreeAsync(stage, st);
   CUDA_TRY(cudaStreamSynchronize(st));
+  mark_batch_dirty(g);
   return RT_OK;
 }
 
@@ -1069,6 +1076,7 @@ int rt_set_source_types(rt_grid* g, int n, const int* type) {
   }
   for (int i = 0; i < n; ++i) g->src[i].type = type[i];
   g->src_dirty = true;
+  mark_batch_dirty(g);
   return RT_OK;
 }
 
@@ -1447,6 +1455,12 @@ static int batch_status(rt_batch* b, BatchStatus* bs) {
     cudaGetLastError();
   }
   return RT_OK;
+}
+
+// A member's sources or absorbers changed: the batch's source and grid
+// tables (and a captured step) no longer describe it.
+static void mark_batch_dirty(rt_grid* g) {
+  if (g->batch) g->batch->dirty = true;
 }
 
 static void detach_grid(rt_grid* g) {
