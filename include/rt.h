@@ -194,6 +194,8 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* desc, void* stream, rt_grid*
 /* Wait for the grid's work, take it out of its batch (if any) and free its
  * device memory.  NULL is accepted. */
 int rt_grid_destroy(rt_grid* grid);
+/* Cells per axis of a grid (every per-cell array has nx*ny*nz elements). */
+int rt_get_dims(rt_grid* grid, int* nx, int* ny, int* nz);
 
 /* Append n point sources (Sec. 2.1, Step 1).  Host arrays, copied:
  *   pos_cm[3n] position in [0, box]^3, ndot[n] photons/s (>= 0),

@@ -393,6 +393,14 @@ int rt_grid_destroy(rt_grid* g) {
   return RT_OK;
 }
 
+int rt_get_dims(rt_grid* g, int* nx, int* ny, int* nz) {
+  if (!g || !nx || !ny || !nz) return fail(RT_ERR_INVALID_ARG, "rt_get_dims: NULL argument");
+  *nx = g->nx;
+  *ny = g->ny;
+  *nz = g->nz;
+  return RT_OK;
+}
+
 int rt_add_sources(rt_grid* g, int n, const double* pos, const double* ndot, const double* e_ph,
                    const double* sigma) {
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_add_sources: grid is NULL");

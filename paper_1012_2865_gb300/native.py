@@ -123,6 +123,7 @@ def lib():
             "rt_get_rates_typed": ([vp, i, vp, vp, i, i], i),
             "rt_get_in_flight": ([vp, vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)], i),
             "rt_synchronize": ([vp], i),
+            "rt_get_dims": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
             "rt_selfcheck_directions": ([vp, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
             "rt_kernel_launches": ([], ctypes.c_uint64),
             "rt_get_last_error": ([], ctypes.c_char_p),
@@ -162,17 +163,44 @@ def check(code):
         raise RtError(code, lib().rt_get_last_error().decode(errors="replace"))
 
 
-def _buf(a, dtype=np.float64):
-    """(pointer, mem_kind, keepalive) for a numpy array or a torch tensor."""
+_TORCH_DTYPE = {np.dtype(np.float64): "torch.float64", np.dtype(np.float32): "torch.float32"}
+
+
+def _buf(a, dtype=np.float64, n=None):
+    """(pointer, mem_kind, keepalive) for a numpy array or a torch tensor.
+
+    A host array is converted to a contiguous array of `dtype`; a CUDA tensor
+    is passed as it is and must already have that element type and be
+    contiguous.  With `n` given, the element count must be n: the library
+    reads n elements through the pointer."""
     if a is None:
         return None, RT_MEM_HOST, None
     if type(a).__module__.startswith("torch"):
         if a.is_cuda:
-            assert a.is_contiguous()
+            want = _TORCH_DTYPE[np.dtype(dtype)]
+            if str(a.dtype) != want:
+                raise TypeError(f"device array of {a.dtype}; expected {want}")
+            if not a.is_contiguous():
+                raise ValueError("device array is not contiguous")
+            if n is not None and a.numel() != n:
+                raise ValueError(f"device array of {a.numel()} elements; expected {n}")
             return a.data_ptr(), RT_MEM_DEVICE, a
         a = a.numpy()
-    arr = np.ascontiguousarray(a, dtype=dtype)
+    arr = np.ascontiguousarray(a, dtype=dtype).reshape(-1)
+    if n is not None and arr.size != n:
+        raise ValueError(f"array of {arr.size} elements; expected {n}")
     return arr.ctypes.data, RT_MEM_HOST, arr
+
+
+def rt_get_dims(grid) -> tuple:
+    nx, ny, nz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().rt_get_dims(grid, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nz)))
+    return nx.value, ny.value, nz.value
+
+
+def _ncell(grid) -> int:
+    nx, ny, nz = rt_get_dims(grid)
+    return nx * ny * nz
 
 
 def rt_ctx_create(device: int = 0):
@@ -187,9 +215,10 @@ def rt_ctx_destroy(ctx):
 
 def rt_create_grid(ctx, dims, box_len_cm, n_H, x_HI, x_HII=None, precision="fp64", stream=None):
     nx, ny, nz = (int(v) for v in dims)
-    pn, kn, kn_ = _buf(n_H)
-    px, kx, kx_ = _buf(x_HI)
-    pz, kz, kz_ = _buf(x_HII)
+    n = nx * ny * nz if min(nx, ny, nz) > 0 else None  # the library rejects empty dims itself
+    pn, kn, kn_ = _buf(n_H, n=n)
+    px, kx, kx_ = _buf(x_HI, n=n)
+    pz, kz, kz_ = _buf(x_HII, n=n)
     if len({k for k, p in ((kn, pn), (kx, px), (kz, pz)) if p is not None}) > 1:
         raise ValueError("n_H, x_HI, x_HII must all live on the host or all on the device")
     d = rt_grid_desc(nx, ny, nz, float(box_len_cm), PRECISIONS[precision] if isinstance(precision, str)
@@ -255,9 +284,12 @@ def rt_get_budget(grid) -> dict:
 
 
 def rt_set_state(grid, x_HI, x_HII=None, n_H=None):
-    px, kx, kx_ = _buf(x_HI)
-    pz, kz, kz_ = _buf(x_HII)
-    pn, kn, kn_ = _buf(n_H)
+    n = _ncell(grid)
+    px, kx, kx_ = _buf(x_HI, n=n)
+    pz, kz, kz_ = _buf(x_HII, n=n)
+    pn, kn, kn_ = _buf(n_H, n=n)
+    if len({k for k, p in ((kn, pn), (kx, px), (kz, pz)) if p is not None}) > 1:
+        raise ValueError("n_H, x_HI, x_HII must all live on the host or all on the device")
     check(lib().rt_set_state(grid, pn, px, pz, kx))
 
 
@@ -277,8 +309,9 @@ def rt_set_source_types(grid, types):
 
 def rt_set_absorbers(grid, n_HeI, n_HeII):
     """Helium absorber densities: host arrays or CUDA tensors (float64)."""
-    p1, k1, keep1 = _buf(n_HeI)
-    p2, k2, keep2 = _buf(n_HeII)
+    n = _ncell(grid)
+    p1, k1, keep1 = _buf(n_HeI, n=n)
+    p2, k2, keep2 = _buf(n_HeII, n=n)
     if k1 != k2:
         raise ValueError("n_HeI and n_HeII must both live on the host or both on the device")
     check(lib().rt_set_absorbers(grid, p1, p2, k1))
@@ -305,14 +338,19 @@ def rt_get_in_flight(grid) -> np.ndarray:
 def rt_set_rates(grid, kph, gamma):
     """Install k_ph and Gamma: host arrays (sent as FP64) or CUDA tensors of
     one dtype (float32 or float64)."""
+    n = _ncell(grid)
     dev = type(kph).__module__.startswith("torch") and kph.is_cuda
     if dev:
-        assert kph.dtype == gamma.dtype and gamma.is_cuda
+        if not (type(gamma).__module__.startswith("torch") and gamma.is_cuda and kph.dtype == gamma.dtype):
+            raise TypeError("kph and gamma: CUDA tensors of one dtype")
         dt = RT_DTYPE_F64 if str(kph.dtype) == "torch.float64" else RT_DTYPE_F32
     else:
         dt = RT_DTYPE_F64
-    pk, kk, keep_k = _buf(kph)
-    pg, kg, keep_g = _buf(gamma)
+    npdt = np.float64 if dt == RT_DTYPE_F64 else np.float32
+    pk, kk, keep_k = _buf(kph, npdt, n=n)
+    pg, kg, keep_g = _buf(gamma, npdt, n=n)
+    if kk != kg:
+        raise ValueError("kph and gamma must both live on the host or both on the device")
     check(lib().rt_set_rates(grid, pk, pg, dt, kk))
 
 

@@ -71,3 +71,9 @@ def test_missing_library_fails_loudly(monkeypatch):
         native.lib()
     with pytest.raises(RuntimeError):
         native.rt_ctx_create(0)
+
+
+def test_dims_query_rejects_a_null_grid():
+    L = native.lib()
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert L.rt_get_dims(None, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == native.RT_ERR_INVALID_ARG
