@@ -461,14 +461,24 @@ class Grid:
 
 def rt_trace_noalloc(dims, box_len_cm, n_HI, n_H, x_HI, kph, gamma, pos_cm, ndot, e_ph_eV, sigma_cm2,
                      params: rt_trace_params, stream=None) -> dict:
-    """Allocation-free trace; every grid array is a CUDA tensor (n_HI, kph, gamma float32)."""
+    """Allocation-free trace; every grid array is a CUDA tensor of nx*ny*nz
+    elements (n_HI, kph, gamma float32; n_H, x_HI float64)."""
     nx, ny, nz = (int(v) for v in dims)
-    g = rt_noalloc_grid(nx, ny, nz, float(box_len_cm), n_HI.data_ptr(), n_H.data_ptr(), x_HI.data_ptr(),
-                        kph.data_ptr(), gamma.data_ptr())
+    n = nx * ny * nz if min(nx, ny, nz) > 0 else None  # the library rejects empty dims itself
+    ptr = []
+    for a, dt in ((n_HI, np.float32), (n_H, np.float64), (x_HI, np.float64), (kph, np.float32),
+                  (gamma, np.float32)):
+        p, kind, _ = _buf(a, dt, n=n)
+        if kind != RT_MEM_DEVICE:
+            raise ValueError("rt_trace_noalloc: the grid arrays are CUDA tensors")
+        ptr.append(p)
+    g = rt_noalloc_grid(nx, ny, nz, float(box_len_cm), *ptr)
     pos = np.ascontiguousarray(pos_cm, dtype=np.float64).reshape(-1)
     nd = np.ascontiguousarray(ndot, dtype=np.float64).reshape(-1)
     e = np.ascontiguousarray(e_ph_eV, dtype=np.float64).reshape(-1)
     sg = np.ascontiguousarray(sigma_cm2, dtype=np.float64).reshape(-1)
+    if pos.size != 3 * nd.size or e.size != nd.size or sg.size != nd.size:
+        raise ValueError("source arrays disagree in length")
     b = rt_budget()
     code = lib().rt_trace_noalloc(ctypes.byref(g), nd.size, pos.ctypes.data, nd.ctypes.data, e.ctypes.data,
                                   sg.ctypes.data, ctypes.byref(params), ctypes.c_void_p(stream or 0),

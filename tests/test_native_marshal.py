@@ -74,6 +74,14 @@ class FakeLib:
         self.calls.append(("rates", pk, pg, dt, kind))
         return native.RT_OK
 
+    def rt_trace_noalloc(self, pg, nsrc, pos, nd, e, sg, params, stream, pb):
+        g = pg._obj
+        self.calls.append(("noalloc", g.n_HI, g.n_H, g.x_HI, g.kph, g.gamma, nsrc))
+        return native.RT_OK
+
+    def rt_noalloc_last_error(self):
+        return b"fake"
+
 
 @pytest.fixture
 def fake(monkeypatch):
@@ -135,3 +143,26 @@ def test_set_absorbers_and_rates(fake):
         native.rt_set_rates("g", FakeCudaTensor(N + 1), FakeCudaTensor(N + 1))
     native.rt_set_rates("g", np.ones(N, dtype=np.float32), np.ones(N))  # host: sent as FP64
     assert fake.calls[-1][3] == native.RT_DTYPE_F64 and fake.calls[-1][4] == native.RT_MEM_HOST
+
+
+def test_noalloc_grid_arrays(fake):
+    params = native.trace_params()
+    f32 = dict(dtype="torch.float32")
+
+    def arrays(**over):
+        a = dict(n_HI=FakeCudaTensor(N, ptr=1, **f32), n_H=FakeCudaTensor(N, ptr=2), x_HI=FakeCudaTensor(N, ptr=3),
+                 kph=FakeCudaTensor(N, ptr=4, **f32), gamma=FakeCudaTensor(N, ptr=5, **f32))
+        a.update(over)
+        return a
+
+    src = dict(pos_cm=np.zeros((2, 3)), ndot=[1e48, 1e48], e_ph_eV=[13.6, 13.6], sigma_cm2=[6.3e-18, 6.3e-18])
+    native.rt_trace_noalloc((4, 5, 6), 1.0, **arrays(), **src, params=params)
+    assert fake.calls[-1] == ("noalloc", 1, 2, 3, 4, 5, 2)
+    with pytest.raises(TypeError):  # n_HI must be float32
+        native.rt_trace_noalloc((4, 5, 6), 1.0, **arrays(n_HI=FakeCudaTensor(N)), **src, params=params)
+    with pytest.raises(ValueError):  # host arrays are not accepted here
+        native.rt_trace_noalloc((4, 5, 6), 1.0, **arrays(x_HI=np.zeros(N)), **src, params=params)
+    with pytest.raises(ValueError):
+        native.rt_trace_noalloc((4, 5, 6), 1.0, **arrays(kph=FakeCudaTensor(N - 1, **f32)), **src, params=params)
+    with pytest.raises(ValueError):
+        native.rt_trace_noalloc((4, 5, 6), 1.0, **arrays(), **dict(src, ndot=[1e48]), params=params)
