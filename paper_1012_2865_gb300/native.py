@@ -317,7 +317,16 @@ def rt_set_absorbers(grid, n_HeI, n_HeII):
     check(lib().rt_set_absorbers(grid, p1, p2, k1))
 
 
+def _check_ncell(grid, ncell):
+    """The library writes the grid's number of cells: the caller's count must be it."""
+    n = _ncell(grid)
+    if int(ncell) != n:
+        raise ValueError(f"ncell = {ncell}; the grid has {n} cells")
+    return n
+
+
 def rt_get_rates_typed(grid, ncell, ptype, dtype=RT_DTYPE_F64, where="host"):
+    ncell = _check_ncell(grid, ncell)
     outs = {k: _out(ncell, dtype, where) for k in ("kph", "gamma")}
     mk = RT_MEM_DEVICE if where == "device" else RT_MEM_HOST
     ptr = {k: (v.data_ptr() if where == "device" else v.ctypes.data) for k, v in outs.items()}
@@ -375,6 +384,7 @@ def _out(n, dtype, where):
 
 
 def rt_get_rates(grid, ncell, dtype=RT_DTYPE_F64, where="host", want=("kph", "gamma", "x_HI")):
+    ncell = _check_ncell(grid, ncell)
     outs = {k: _out(ncell, dtype, where) if k in want else None for k in ("kph", "gamma", "x_HI")}
     mk = RT_MEM_DEVICE if where == "device" else RT_MEM_HOST
     ptr = {k: (None if v is None else (v.data_ptr() if where == "device" else v.ctypes.data))
@@ -384,6 +394,7 @@ def rt_get_rates(grid, ncell, dtype=RT_DTYPE_F64, where="host", want=("kph", "ga
 
 
 def rt_get_ionised(grid, ncell, dtype=RT_DTYPE_F64, where="host"):
+    ncell = _check_ncell(grid, ncell)
     out = _out(ncell, dtype, where)
     p = out.data_ptr() if where == "device" else out.ctypes.data
     check(lib().rt_get_ionised(grid, p, int(dtype), RT_MEM_DEVICE if where == "device" else RT_MEM_HOST))

@@ -166,3 +166,10 @@ def test_noalloc_grid_arrays(fake):
         native.rt_trace_noalloc((4, 5, 6), 1.0, **arrays(kph=FakeCudaTensor(N - 1, **f32)), **src, params=params)
     with pytest.raises(ValueError):
         native.rt_trace_noalloc((4, 5, 6), 1.0, **arrays(), **dict(src, ndot=[1e48]), params=params)
+
+
+def test_read_backs_check_the_cell_count(fake):
+    for call in (lambda: native.rt_get_rates("g", N + 1), lambda: native.rt_get_ionised("g", N - 1),
+                 lambda: native.rt_get_rates_typed("g", 2 * N, 1)):
+        with pytest.raises(ValueError):
+            call()
