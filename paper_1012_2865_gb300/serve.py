@@ -70,6 +70,8 @@ class Server:
         self.active = {}
         self.done = []
         self.rejected = []
+        self.failed = []
+        self.cancelled = []
         self.steps = 0
         self.segments = 0
         self._mem_info = mem_info
@@ -117,11 +119,62 @@ class Server:
             n += 1
         return n
 
+    def _retire(self, slot: int, now: float, bucket: list, why: str = None):
+        req = self.active.pop(slot)
+        req.finished = now
+        if why is not None:
+            req.meta["error"] = why
+        self.batch.remove(slot)
+        req.handle.close()
+        req.handle = None
+        bucket.append(req)
+
+    def _trace_all(self, now_fn):
+        """The batch's trace.  When it fails, each request is traced alone to
+        find the ones that fail by themselves; they leave with the error and
+        the others are traced again together (a failed trace has not changed
+        any state: the update has not run).  If the batch still fails, the
+        error cannot be attributed and every active request fails with it."""
+        err = getattr(self.backend, "RtError", native.RtError)
+        try:
+            self.batch.trace(sync=True, **self.params)
+            return
+        except err as e:
+            first = str(e)
+        for slot, req in list(self.active.items()):
+            try:
+                req.handle.trace(**self.params)
+            except err as e:
+                self._retire(slot, now_fn(), self.failed, str(e))
+        if not self.active:
+            return
+        try:
+            self.batch.trace(sync=True, **self.params)
+        except err as e:
+            for slot in list(self.active):
+                self._retire(slot, now_fn(), self.failed, f"{e} (after: {first})")
+
+    def cancel(self, rid: int, now: float = 0.0) -> bool:
+        """Withdraw a request that is waiting or running (between steps)."""
+        for req in list(self.pending):
+            if req.rid == rid:
+                self.pending.remove(req)
+                req.finished = now
+                self.cancelled.append(req)
+                return True
+        for slot, req in list(self.active.items()):
+            if req.rid == rid:
+                self._retire(slot, now, self.cancelled)
+                return True
+        return False
+
     def step(self, now_fn) -> int:
         """One coupled step of every active request; returns requests finished."""
         if not self.active:
             return 0
-        self.batch.trace(sync=True, **self.params)
+        self._trace_all(now_fn)
+        if not self.active:
+            return 0
         self.batch.chem(self.dt_s, self.nsub, self.alpha_B)
         self.steps += 1
         finished = []
@@ -165,7 +218,8 @@ class Server:
 
     def report(self, wall_s: float) -> dict:
         lat = np.array([r.latency for r in self.done]) if self.done else np.array([np.nan])
-        return dict(completed=len(self.done), rejected=len(self.rejected), wall_s=wall_s, steps=self.steps,
+        return dict(completed=len(self.done), rejected=len(self.rejected), failed=len(self.failed),
+                    cancelled=len(self.cancelled), wall_s=wall_s, steps=self.steps,
                     segments=self.segments,
                     segments_per_s=self.segments / wall_s if wall_s > 0 else 0.0,
                     p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),

@@ -12,6 +12,10 @@ import numpy as np
 from paper_1012_2865_gb300 import serve
 
 
+class FakeRtError(RuntimeError):
+    pass
+
+
 class FakeGrid:
     live = []
     made = []
@@ -19,12 +23,18 @@ class FakeGrid:
     def __init__(self, ctx, g, precision):
         self.ncell = int(np.prod(g["dims"]))
         self.precision = precision
+        self.poison = g.get("poison", False)  # its trace fails, alone or in a batch
         self.created = time.perf_counter()
         FakeGrid.live.append(self)
         FakeGrid.made.append(self)
 
     def rates(self):
         return {"x_HI": np.zeros(self.ncell), "kph": np.ones(self.ncell)}
+
+    def trace(self, **kw):
+        if self.poison:
+            raise FakeRtError("device status 6")
+        return {"segments": self.ncell}
 
     def close(self):
         if self in FakeGrid.live:
@@ -47,6 +57,8 @@ class FakeBatch:
         del self.slots[slot]
 
     def trace(self, sync=True, **kw):
+        if any(gr.poison for gr in self.slots.values()):
+            raise FakeRtError("device status 6")
         self.sizes.append(len(self.slots))
         if FakeBatch.step_s:
             time.sleep(FakeBatch.step_s)
@@ -61,11 +73,11 @@ class FakeBatch:
         pass
 
 
-BACKEND = types.SimpleNamespace(Grid=FakeGrid, Batch=FakeBatch)
+BACKEND = types.SimpleNamespace(Grid=FakeGrid, Batch=FakeBatch, RtError=FakeRtError)
 
 
-def _request(rid, N, nsteps, arrival=0.0):
-    g = {"dims": (N, N, N)}
+def _request(rid, N, nsteps, arrival=0.0, poison=False):
+    g = {"dims": (N, N, N), "poison": poison}
     return serve.Request(rid=rid, grid=g, nsteps=nsteps, arrival=arrival)
 
 
@@ -148,3 +160,30 @@ def test_grid_bytes_counts_the_resident_fields():
     # n_H, x_HI, x_HII in FP64; n_HI, k_ph, Gamma in FP64 or (FP32 pair, FP32, FP32)
     assert serve.grid_bytes(1, "fp64") == 3 * 8 + 3 * 8
     assert serve.grid_bytes(1, "fp32_mixed") == 3 * 8 + 8 + 4 + 4
+
+
+def test_a_failing_request_leaves_and_the_others_finish():
+    FakeBatch.step_s = 0.0
+    reqs = [_request(0, 16, nsteps=3), _request(1, 12, nsteps=2, poison=True), _request(2, 20, nsteps=4)]
+    srv = _server(total_bytes=1 << 40, reserve=0, max_slots=8)
+    rep = srv.run(reqs)
+    assert rep["failed"] == 1 and srv.failed[0].rid == 1 and "status 6" in srv.failed[0].meta["error"]
+    assert rep["completed"] == 2 and sorted(r.rid for r in srv.done) == [0, 2]
+    assert all(r.steps_done == r.nsteps for r in srv.done)
+    assert not FakeGrid.live
+
+
+def test_cancel_waiting_and_running_requests():
+    FakeBatch.step_s = 0.0
+    one = serve.grid_bytes(16 ** 3, "fp32_mixed")
+    srv = _server(total_bytes=one, reserve=0, max_slots=4)  # room for one grid at a time
+    for i in range(3):
+        srv.submit(_request(i, 16, nsteps=5))
+    assert srv.admit(0.0) == 1
+    srv.step(lambda: 0.1)
+    assert srv.cancel(2, 0.2) and srv.cancel(0, 0.2)  # one waiting, one running
+    assert not srv.cancel(7)
+    assert [r.rid for r in srv.cancelled] == [2, 0]
+    rep = srv.run([])
+    assert rep["completed"] == 1 and srv.done[0].rid == 1 and rep["cancelled"] == 2
+    assert not FakeGrid.live
