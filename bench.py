@@ -598,12 +598,13 @@ def serving(args, ctx):
         free_at = start + sv
         lat.append(free_at - r.arrival)
     mixed_lat = {r.rid: r.latency for r in srv.done}
-    same = [mixed_lat[r.rid] for r in reqs[:len(service)]]
+    same = [mixed_lat[r.rid] for r in reqs[:len(service)] if r.rid in mixed_lat]
     return {"workload": f"first {len(reqs)} requests of a Poisson stream at 200 req/s (arrivals over "
                         f"{reqs[-1].arrival * 1e3:.0f} ms), 64^3-256^3 log-uniform cells, 1-500 sources, "
                         "1-20 coupled steps of 0.5 Myr from neutral",
             "value": rep["segments_per_s"], "unit": UNIT, "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"],
-            "completed": rep["completed"], "requests_per_s": rep["requests_per_s"], "wall_s": rep["wall_s"],
+            "completed": rep["completed"], "failed": rep.get("failed", 0), "rejected": rep.get("rejected", 0),
+            "requests_per_s": rep["requests_per_s"], "wall_s": rep["wall_s"],
             "segments": rep["segments"], "batch_steps": rep["steps"],
             "fp64_one_at_a_time": {"requests": len(service), "service_s_total": float(np.sum(service)),
                                    "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat else None,
