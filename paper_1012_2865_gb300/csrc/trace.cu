@@ -9,7 +9,7 @@
 // that split packages publish.  When a package splits (Step 3e) its lane
 // keeps child 0 and appends children 1-3 to the queue (one atomic per warp
 // reserves the slots); each record's tag word is stored last with release
-// semantics and read with acquire semantics.  An outstanding-package counter
+// semantics and polled with acquire loads.  An outstanding-package counter
 // (+3 per split, -1 per finished package) tells idle warps when the trace is
 // over.  Every wait is bounded: a warp that sees no change of the counter for
 // timeout_ns sets RT_ERR_TIMEOUT and leaves; a package that takes more steps
@@ -243,12 +243,11 @@ struct Walk64 {
     __stcg(&q->level, c.level);
     st_release_u32(&q->tag, epoch);
   }
-  // Poll with a relaxed load; only a successful poll pays for the fence that
-  // orders the payload reads after the tag.
+  // Poll with an acquire load of the tag: the payload reads that follow a
+  // successful poll are ordered after it without a fence.
   template <bool FSL>
   __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
-    if (ld_relaxed_u32(&q->tag) != epoch) return false;
-    __threadfence();
+    if (ld_acquire_u32(&q->tag) != epoch) return false;
     const double2 a = __ldcg(reinterpret_cast<const double2*>(&q->r));    // r, P
     const double2 b = __ldcg(reinterpret_cast<const double2*>(&q->tau));  // tau, (src, pix)
     const uint2 c = __ldcg(reinterpret_cast<const uint2*>(&q->level));    // level, tag
@@ -615,13 +614,12 @@ struct Walk32 {
     if (FSL) __stcg(&q->age, c.age);
     st_release_u32(&q->tag, (epoch << 4) | (c.tag & 15u));
   }
-  // Poll with a relaxed load; only a successful poll pays for the fence that
-  // orders the payload reads after the tag.
+  // Poll with an acquire load of the tag: the payload reads that follow a
+  // successful poll are ordered after it without a fence.
   template <bool FSL>
   __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
-    const uint32_t tg = ld_relaxed_u32(&q->tag);
+    const uint32_t tg = ld_acquire_u32(&q->tag);
     if ((tg >> 4) != (epoch & 0x0fffffffu)) return false;
-    __threadfence();
     const float4 a = __ldcg(reinterpret_cast<const float4*>(&q->r));
     const uint4 b = __ldcg(reinterpret_cast<const uint4*>(&q->tau_lo));
     o.r = a.x; o.r_lo = a.y; o.P = a.z; o.tau = a.w;
@@ -749,7 +747,8 @@ struct Walk32 {
     const float kap = kap2.hi;
     const float dtau = dtau2.hi;
     // transmitted fraction tr = e^-tau; phi = (1 - e^-tau)/tau from its Taylor
-    // series below tau = 1/4 (7 terms: truncation < 2e-13), else from tr.
+    // series below tau = 1/4 (7 terms: the first dropped term, tau^7 / 8!, is
+    // below 1.6e-9 there, under FP32 rounding), else from tr.
     // Both are computed and one is selected, so lanes do not diverge.
     const float tr = expf(-dtau);
     const float ser = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(dtau, 1.0f / 5040.0f, -1.0f / 720.0f), dtau, 1.0f / 120.0f), dtau,
@@ -1121,7 +1120,9 @@ __global__ void trace_init_kernel(unsigned long long* ctl, unsigned long long n_
                                   unsigned long long in_cap, int pass, int passes) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     if (first_pass) {
-      ctl[CTL_STATUS] = 0;
+      // a state rejected by an asynchronous upload stays reported until the
+      // host has read it
+      ctl[CTL_STATUS] = ctl[CTL_SET_ERR];
       ctl[CTL_PEAK] = 0;
       ctl[CTL_PUSHED] = 0;
       if (mode == FLIGHT_OFF) ctl[CTL_RESUME] = 0;
