@@ -256,6 +256,38 @@ int rt_set_state(rt_grid* grid, const double* n_H, const double* x_HI, const dou
 /* Copy k_ph (s^-1), Gamma (erg/s) and x_HI of every cell into caller buffers
  * (any may be NULL) of element type dtype in memory mem_kind.  Synchronous. */
 int rt_get_rates(rt_grid* grid, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind);
+
+/* The same two operations without waiting, for callers that overlap the
+ * host<->device copies of one step with the kernels of the next (the
+ * Sec. 2.2 state in, the Eqs. "kph", "gamma" rates out).  Not for grids in a
+ * batch (RT_ERR_STATE).  The first call of either on a grid allocates its
+ * staging area and streams (which synchronises the device).
+ *
+ * rt_set_state_async: as rt_set_state, but returns once the work is
+ * enqueued.  Host arrays (best pinned) are copied on a stream of the
+ * library's into a staging area, concurrently with the grid's kernels, and
+ * must stay unchanged until that copy is done (rt_synchronize, or any call
+ * that waits for the grid); device arrays are read in the grid's stream
+ * order.  The state is checked on the device as rt_set_state checks it; a
+ * state that fails leaves the grid unchanged and is reported as
+ * RT_ERR_INVALID_ARG, naming the first failing cell, by the next
+ * rt_synchronize, rt_get_budget or waiting rt_trace (every trace enqueued
+ * until the host has read the rejection carries that status).
+ *
+ * rt_get_rates_async: as rt_get_rates, but returns once the work is
+ * enqueued.  The fields are taken at this point of the grid's stream (a
+ * device-to-device snapshot into a staging area) and copied to host buffers
+ * (best pinned) on a stream of the library's, concurrently with the grid's
+ * later kernels; they are complete after rt_wait_rates or rt_synchronize.
+ * Device buffers are filled in the grid's stream order.  A later
+ * rt_get_rates_async waits on the device for this one's copies to leave the
+ * staging area. */
+int rt_set_state_async(rt_grid* grid, const double* n_H, const double* x_HI, const double* x_HII,
+                       int mem_kind);
+int rt_get_rates_async(rt_grid* grid, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind);
+/* Wait until the host copies of the last rt_get_rates_async are complete
+ * (and only for those: the grid's kernels may still run). */
+int rt_wait_rates(rt_grid* grid);
 /* Copy x_HII likewise. */
 int rt_get_ionised(rt_grid* grid, void* x_HII, int dtype, int mem_kind);
 
@@ -359,6 +391,20 @@ int rt_batch_autotune(rt_batch* batch, rt_trace_params* params);
  * assume (*bound may be NULL).  Synchronous. */
 int rt_selfcheck_directions(rt_ctx* ctx, int level, double* max_abs_err, double* bound);
 
+/* Measurement aid (no counterpart in the paper): the rate at which device
+ * `device` completes atomic reductions (RED) of 1 into an array of `words`
+ * elements (a power of two in [2^10, 2^30]) of element type dtype
+ * (RT_DTYPE_F32 or RT_DTYPE_F64), each to an element picked by a hash of
+ * (thread, iteration) -- the scattered pattern of lanes following diverging
+ * rays.  This is the roof of the trace's k_ph / Gamma deposits (Eqs. "kph",
+ * "gamma") while the rate arrays stay in L2.  *reds_per_s receives the best
+ * of five event-timed full-occupancy launches (after one warm-up).  The call
+ * allocates and frees its array and its own stream; it is synchronous.
+ * Errors: rt_probe_last_error() gives the message. */
+int rt_probe_red(int device, int dtype, uint64_t words, double* reds_per_s);
+/* Message for the last failed rt_probe_red on this host thread. */
+const char* rt_probe_last_error(void);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free trace.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- applications
@@ -404,7 +450,9 @@ int rt_trace_noalloc(const rt_noalloc_grid* grid, int nsrc, const double* pos_cm
 /* Message for the last failed rt_trace_noalloc on this host thread. */
 const char* rt_noalloc_last_error(void);
 
-/* Wait for all work enqueued on the grid's stream. */
+/* Wait for all work enqueued on the grid's stream (and for the copies of
+ * rt_set_state_async / rt_get_rates_async); RT_ERR_INVALID_ARG if a state
+ * uploaded by rt_set_state_async since the last report was rejected. */
 int rt_synchronize(rt_grid* grid);
 
 /* Number of kernels this library launched on the calling process so far. */

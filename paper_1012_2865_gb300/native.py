@@ -113,6 +113,9 @@ def lib():
             "rt_chem_update": ([vp, d, i, d], i),
             "rt_get_rates": ([vp, vp, vp, vp, i, i], i),
             "rt_set_state": ([vp, vp, vp, vp, i], i),
+            "rt_set_state_async": ([vp, vp, vp, vp, i], i),
+            "rt_get_rates_async": ([vp, vp, vp, vp, i, i], i),
+            "rt_wait_rates": ([vp], i),
             "rt_get_ionised": ([vp, vp, i, i], i),
             "rt_set_rates": ([vp, vp, vp, i, i], i),
             "rt_timestep": ([vp, d, d, d, d, d, d, ctypes.POINTER(d)], i),
@@ -140,6 +143,8 @@ def lib():
             "rt_trace_noalloc": ([ctypes.POINTER(rt_noalloc_grid), i, vp, vp, vp, vp,
                                   ctypes.POINTER(rt_trace_params), vp, ctypes.POINTER(rt_budget)], i),
             "rt_noalloc_last_error": ([], ctypes.c_char_p),
+            "rt_probe_red": ([i, i, ctypes.c_uint64, ctypes.POINTER(d)], i),
+            "rt_probe_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -293,6 +298,50 @@ def rt_set_state(grid, x_HI, x_HII=None, n_H=None):
     check(lib().rt_set_state(grid, pn, px, pz, kx))
 
 
+def _in_place(a, ptr) -> bool:
+    """True when the pointer handed to the library is the caller's own buffer
+    (not a converted copy that would be gone before a deferred copy runs)."""
+    if a is None:
+        return True
+    own = a.data_ptr() if type(a).__module__.startswith("torch") else np.asarray(a).ctypes.data
+    return own == ptr
+
+
+def rt_set_state_async(grid, x_HI, x_HII=None, n_H=None):
+    """Enqueue a new gas state (host arrays best pinned; they must stay unchanged
+    until rt_synchronize).  A rejected state is reported by a later call."""
+    n = _ncell(grid)
+    px, kx, kx_ = _buf(x_HI, n=n)
+    pz, kz, kz_ = _buf(x_HII, n=n)
+    pn, kn, kn_ = _buf(n_H, n=n)
+    if len({k for k, p in ((kn, pn), (kx, px), (kz, pz)) if p is not None}) > 1:
+        raise ValueError("n_H, x_HI, x_HII must all live on the host or all on the device")
+    if kx == RT_MEM_HOST and not all(_in_place(a, p) for a, p in ((x_HI, px), (x_HII, pz), (n_H, pn))):
+        raise ValueError("host arrays for rt_set_state_async must be contiguous float64 (they are read later)")
+    check(lib().rt_set_state_async(grid, pn, px, pz, kx))
+
+
+def rt_get_rates_async(grid, kph=None, gamma=None, x_HI=None, dtype=RT_DTYPE_F64):
+    """Enqueue copies of k_ph, Gamma and x_HI into caller buffers (all numpy
+    arrays, best pinned, or all CUDA tensors) of element type dtype; complete
+    after rt_wait_rates / rt_synchronize."""
+    n = _ncell(grid)
+    want = np.float64 if dtype == RT_DTYPE_F64 else np.float32
+    bufs = [(None, None, None) if a is None else _buf(a, dtype=want, n=n) for a in (kph, gamma, x_HI)]
+    kinds = {b[1] for b in bufs if b[0] is not None}
+    if len(kinds) > 1:
+        raise ValueError("the output buffers must all live on the host or all on the device")
+    for a, b in zip((kph, gamma, x_HI), bufs):
+        if b[1] == RT_MEM_HOST and not _in_place(a, b[0]):
+            raise ValueError("host output buffers for rt_get_rates_async must be contiguous arrays of the dtype")
+    kind = kinds.pop() if kinds else RT_MEM_HOST
+    check(lib().rt_get_rates_async(grid, bufs[0][0], bufs[1][0], bufs[2][0], int(dtype), kind))
+
+
+def rt_wait_rates(grid):
+    check(lib().rt_wait_rates(grid))
+
+
 def rt_set_source_offset(grid, first: int):
     check(lib().rt_set_source_offset(grid, int(first)))
 
@@ -410,6 +459,15 @@ def rt_selfcheck_directions(ctx, level: int):
 
 def rt_synchronize(grid):
     check(lib().rt_synchronize(grid))
+
+
+def rt_probe_red(device: int, dtype=RT_DTYPE_F32, words: int = 1 << 21) -> float:
+    """Atomic reductions per second into an array of `words` elements (measurement aid)."""
+    r = ctypes.c_double()
+    code = lib().rt_probe_red(int(device), int(dtype), int(words), ctypes.byref(r))
+    if code != RT_OK:
+        raise RtError(code, lib().rt_probe_last_error().decode(errors="replace"))
+    return r.value
 
 
 def rt_kernel_launches() -> int:
