@@ -14,6 +14,8 @@ contraction); this module only builds it and marshals numpy arrays:
 * ``trace`` -- Steps 1-5 of Sec. 3.1 for every source of a grid: k_ph and
   Gamma per cell (Eqs. "dtau", "flux", "kph", "gamma"), the photon budget,
   packages created per HEALPix level and a checksum of the created set.
+* ``trace_roots`` -- the same pass for a range of root packages (the
+  pass is their sum; used to share a trace among host threads).
 * ``chem`` -- backward-Euler update of Eq. "dndt" (hydrogen only).
 * ``trace(..., src_type=, n_he=)`` -- photon types (Sec. 3.2): H I, He I
   and He II ionising packages, each absorbed by its own species.
@@ -73,6 +75,8 @@ def _load():
             lib.orc_trace_mf.argtypes = [p, d, p, p, p, i, p, p, p, p, p, i, d, d, i, p, p, p, p, p, p, i, i,
                                          i, p, ctypes.c_size_t, p, ctypes.c_size_t, p, p]
             lib.orc_trace_mf.restype = i
+            lib.orc_trace_roots.argtypes = [p, d, p, p, i, p, p, p, p, i, d, d, i, p, p, p, p, p, p, u64, u64]
+            lib.orc_trace_roots.restype = i
             lib.orc_chem.argtypes = [ctypes.c_size_t, p, p, p, p, d, i, d]
             lib.orc_chem.restype = None
             _lib = lib
@@ -249,6 +253,40 @@ def trace(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, 
         flight.packages = out[:n_out.value].copy()
         res.update(resumed=float(budget[3]), halted=float(budget[4]), n_halted=int(n_out.value))
     return res
+
+
+def trace_roots(dims, box_len_cm: float, n_H, x_HI, pos_cm, ndot, e_ph_eV, sigma_cm2, root_first: int,
+                root_count: int, *, level0: int = 1, phi_c: float = 5.1, f_term: float = 1e-10,
+                max_level: int = MAX_LEVEL) -> dict:
+    """``trace`` restricted to the root packages src * 12 * 4^level0 + pixel in
+    [root_first, root_first + root_count) (H I photons, infinite speed of
+    light).  Disjoint ranges covering every root sum to the whole pass, so
+    host threads can share one trace (the C call releases the GIL)."""
+    lib = _load()
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    ncell = int(np.prod(dims.astype(np.int64)))
+    n_H = _f64(n_H).reshape(-1)
+    x_HI = _f64(x_HI).reshape(-1)
+    assert n_H.size == ncell and x_HI.size == ncell
+    pos = _f64(pos_cm).reshape(-1)
+    ndot = _f64(ndot).reshape(-1)
+    nsrc = ndot.size
+    e = _f64(e_ph_eV).reshape(-1)
+    sg = _f64(sigma_cm2).reshape(-1)
+    assert pos.size == 3 * nsrc and e.size == nsrc and sg.size == nsrc
+    kph = np.empty(ncell)
+    gamma = np.empty(ncell)
+    budget = np.empty(3)
+    counts = np.zeros(MAX_LEVEL + 1, dtype=np.uint64)
+    hashes = np.zeros(MAX_LEVEL + 1, dtype=np.uint64)
+    seg = np.zeros(1, dtype=np.uint64)
+    rc = lib.orc_trace_roots(_ptr(dims), float(box_len_cm), _ptr(n_H), _ptr(x_HI), int(nsrc), _ptr(pos), _ptr(ndot),
+                             _ptr(e), _ptr(sg), int(level0), float(phi_c), float(f_term), int(max_level), _ptr(kph),
+                             _ptr(gamma), _ptr(budget), _ptr(counts), _ptr(hashes), _ptr(seg), int(root_first),
+                             int(root_count))
+    if rc != 0:
+        raise ValueError("oracle trace rejected its arguments")
+    return dict(kph=kph, gamma=gamma, budget=budget, counts=counts, hashes=hashes, segments=int(seg[0]))
 
 
 def chem(n_H, x_HI, x_HII, kph, dt_s: float, nsub: int, alpha_B: float):

@@ -550,12 +550,13 @@ static int orc_walk(orc_run *R, orc_stack *st) {
  * returns 0; -1 on a bad argument or allocation failure; -2 when out_cap
  * was too small (*n_out then says how many are needed).
  */
-int orc_trace_mf(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, const double *n_he,
-                 int nsrc, const double *pos_cm, const double *ndot, const double *e_ph_eV, const double *sigma_cm2,
-                 const int *src_type, int level0, double phi_c, double f_term, int max_level, double *kph,
-                 double *gamma, double *budget, uint64_t *counts, uint64_t *hashes, uint64_t *segments, int fc,
-                 int src_offset, int n_ages, const double *rlim, size_t n_in, const orc_flight *in, size_t out_cap,
-                 orc_flight *out, size_t *n_out) {
+static int orc_trace_core(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI,
+                          const double *n_he, int nsrc, const double *pos_cm, const double *ndot,
+                          const double *e_ph_eV, const double *sigma_cm2, const int *src_type, int level0,
+                          double phi_c, double f_term, int max_level, double *kph, double *gamma, double *budget,
+                          uint64_t *counts, uint64_t *hashes, uint64_t *segments, int fc, int src_offset, int n_ages,
+                          const double *rlim, size_t n_in, const orc_flight *in, size_t out_cap, orc_flight *out,
+                          size_t *n_out, uint64_t root_lo, uint64_t root_hi) {
   if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0 || level0 < 0 || max_level > ORC_MAX_LEVEL ||
       level0 > max_level || !(phi_c > 0) || !(f_term > 0 && f_term < 1) || n_ages < 0 ||
       (n_ages == 0 && n_in > 0))
@@ -615,9 +616,13 @@ int orc_trace_mf(const int dims[3], double box_len_cm, const double *n_H, const 
   int rc = 0;
   const uint64_t npix0 = 12ULL << (2 * level0);
   for (int src = 0; src < nsrc && rc == 0; ++src) {
-    /* Step 1: N_pix packages on the initial level, luminosity spread equally */
+    /* Step 1: N_pix packages on the initial level, luminosity spread equally
+     * (root packages are numbered src * N_pix + pixel; only those in
+     * [root_lo, root_hi) are emitted) */
     const double P0 = ndot[src] / (double)npix0;
     for (uint64_t p = 0; p < npix0; ++p) {
+      const uint64_t root = (uint64_t)src * npix0 + (npix0 - 1 - p);
+      if (root < root_lo || root >= root_hi) continue;
       orc_pkg pk = {(uint32_t)src, (uint32_t)level0, npix0 - 1 - p, 0.0, P0, 0.0, 0, 0, {0, 0, 0}};
       if (orc_push(&st, pk)) { rc = -1; break; }
       orc_kadd(&emitted, P0);
@@ -648,6 +653,38 @@ int orc_trace_mf(const int dims[3], double box_len_cm, const double *n_H, const 
   *segments = R.nseg;
   *n_out = R.n_out;
   return R.n_out > out_cap ? -2 : 0;
+}
+
+int orc_trace_mf(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, const double *n_he,
+                 int nsrc, const double *pos_cm, const double *ndot, const double *e_ph_eV, const double *sigma_cm2,
+                 const int *src_type, int level0, double phi_c, double f_term, int max_level, double *kph,
+                 double *gamma, double *budget, uint64_t *counts, uint64_t *hashes, uint64_t *segments, int fc,
+                 int src_offset, int n_ages, const double *rlim, size_t n_in, const orc_flight *in, size_t out_cap,
+                 orc_flight *out, size_t *n_out) {
+  return orc_trace_core(dims, box_len_cm, n_H, x_HI, n_he, nsrc, pos_cm, ndot, e_ph_eV, sigma_cm2, src_type, level0,
+                        phi_c, f_term, max_level, kph, gamma, budget, counts, hashes, segments, fc, src_offset, n_ages,
+                        rlim, n_in, in, out_cap, out, n_out, 0, UINT64_MAX);
+}
+
+/* orc_trace_roots: the pass of orc_trace (H I photons, infinite speed of
+ * light) for the root packages src * 12 * 4^level0 + pixel in
+ * [root_first, root_first + root_count) only.  The trace is a sum over root
+ * packages, so the outputs of disjoint ranges covering every root add up to
+ * the whole pass (k_ph, Gamma, budget, counts, checksums, segments); emitted
+ * counts the range's roots only. */
+int orc_trace_roots(const int dims[3], double box_len_cm, const double *n_H, const double *x_HI, int nsrc,
+                    const double *pos_cm, const double *ndot, const double *e_ph_eV, const double *sigma_cm2,
+                    int level0, double phi_c, double f_term, int max_level, double *kph, double *gamma,
+                    double *budget, uint64_t *counts, uint64_t *hashes, uint64_t *segments, uint64_t root_first,
+                    uint64_t root_count) {
+  double b5[5];
+  size_t n_out = 0;
+  if (root_count > UINT64_MAX - root_first) return -1;
+  const int rc = orc_trace_core(dims, box_len_cm, n_H, x_HI, NULL, nsrc, pos_cm, ndot, e_ph_eV, sigma_cm2, NULL,
+                                level0, phi_c, f_term, max_level, kph, gamma, b5, counts, hashes, segments, 0, 0, 0,
+                                NULL, 0, NULL, 0, NULL, &n_out, root_first, root_first + root_count);
+  if (rc == 0) { budget[0] = b5[0]; budget[1] = b5[1]; budget[2] = b5[2]; }
+  return rc;
 }
 
 /* orc_trace_fsl: the same pass for H I photons only. */

@@ -197,7 +197,9 @@ def test_optically_thin_inverse_square():
         assert abs(np.mean(dev)) < 0.05, (pc, np.mean(dev))
         stds.append(np.std(dev))
     slope = np.polyfit(np.log(phis), np.log(stds), 1)[0]
-    assert -1.2 < slope < -0.3, (slope, stds)
+    # the paper's -0.6 is with its covering-factor correction on; without it
+    # the slope is measured near -0.7: the bound proposed for this pin
+    assert -0.9 < slope < -0.3, (slope, stds)
     assert stds[-1] < stds[0]
 
 
@@ -214,3 +216,27 @@ def test_stromgren_constants_golden():
     trec = 1.0 / (vals["alpha_B"] * vals["n_H"])
     assert abs(Rs / synth.KPC_CM - vals["R_s_kpc"]) < 0.05
     assert abs(trec / synth.MYR_S - vals["t_rec_Myr"]) < 0.1
+
+
+def test_root_ranges_sum_to_the_whole_trace():
+    """The trace is a sum over root packages: disjoint root ranges that cover
+    every root give, summed, the counts, checksums and segments of the whole
+    pass exactly and its k_ph, Gamma and budget up to summation order."""
+    g = synth.clumpy(16, 5)
+    args = (g["dims"], g["box_len_cm"], g["n_H"], g["x_HI"], g["pos_cm"], g["ndot"], g["e_ph_eV"], g["sigma_cm2"])
+    whole = oracle.trace(*args, **synth.DEFAULT_PARAMS)
+    nroots = 5 * 48
+    cuts = [0, 1, 47, 48, 130, 239, nroots]
+    parts = [oracle.trace_roots(*args, a, b - a, **synth.DEFAULT_PARAMS) for a, b in zip(cuts[:-1], cuts[1:])]
+    assert np.array_equal(sum(p["counts"] for p in parts), whole["counts"])
+    assert np.array_equal(sum(p["hashes"] for p in parts), whole["hashes"])
+    assert sum(p["segments"] for p in parts) == whole["segments"]
+    for key in ("kph", "gamma"):
+        tot = sum(p[key] for p in parts)
+        m = whole[key] > 0
+        assert np.array_equal(tot > 0, m)
+        assert np.max(np.abs(tot[m] - whole[key][m]) / whole[key][m]) < 1e-12
+    assert np.allclose(sum(p["budget"] for p in parts), whole["budget"], rtol=1e-12, atol=0)
+    # an empty range does nothing; a range past the last root is cut at it
+    empty = oracle.trace_roots(*args, nroots, 10, **synth.DEFAULT_PARAMS)
+    assert empty["segments"] == 0 and not np.any(empty["kph"]) and empty["budget"][0] == 0
