@@ -167,6 +167,41 @@ def _peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+# bytes of one queue record (written once, read once) per precision
+REC_BYTES = {"fp64": 48, "fp32_mixed": 48}
+
+
+def trace_roofline(precision, segments, pushed, kernel_ms, gamma, red_peak, peaks, peak_kind, traffic, red_words):
+    """Roofline figures of one trace launch.
+
+    HBM: algorithmic bytes per launch -- per segment the n_HI read (FP64, or
+    the FP32 pair: 8 bytes) and the k_ph reduction (8 / 4 bytes), plus the
+    Gamma reduction where photons carry energy above the threshold; per queue
+    record one write and one read -- over the kernel's event-timed duration,
+    against the measured copy bandwidth.
+    L2 reductions: one k_ph reduction per segment (and one Gamma reduction
+    where photons heat) over the same duration, against the reduction rate
+    the probe measured in this run into an array of the rate array's size
+    (the per-package residual deposits and the queue's atomics, a few per
+    cent, are left out, so the fraction is a lower bound)."""
+    red_b = 8 if precision == "fp64" else 4
+    nred = 2 if gamma else 1
+    alg = segments * (8 + red_b * nred) + pushed * 2 * REC_BYTES[precision]
+    s = kernel_ms / 1e3
+    achieved = alg / s / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+           "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes": alg, "kernel": "trace_kernel",
+           "kernel_ms": kernel_ms}
+    if red_peak:
+        reds = segments * nred
+        out["l2_red"] = {"reds_per_launch": reds, "achieved": reds / s / 1e9, "peak": red_peak / 1e9,
+                         "unit": "G RED/s", "frac": reds / s / red_peak,
+                         "peak_kind": f"measured in this run (rt_probe_red, {'f64' if red_b == 8 else 'f32'}, "
+                                      f"{red_words} words, scattered addresses)"}
+    return out
+
+
 def run_native(args, rank, world, local):
     import torch
     from paper_1012_2865_gb300 import build, native, synth
@@ -226,33 +261,50 @@ def run_native(args, rank, world, local):
                     pushed=pushed, launches=launches, clocks=clk.summary(), final=final)
 
     def e2e(precision):
+        """The step through the C ABI from host memory, pipelined as a caller
+        that streams states in and rates out would run it: each step uploads
+        its state from pinned host memory (rt_set_state_async, on the
+        library's upload stream, while the previous step's kernels run),
+        traces, updates, and reads k_ph (the path's precision) and x_HI (FP64)
+        back into pinned host buffers (rt_get_rates_async); before enqueueing
+        the read-back the host waits for the previous step's copies
+        (rt_wait_rates), so one step's results are on the host while the next
+        runs.  The timed region ends when the last step's results are on the
+        host."""
         grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
         b = grid.trace(**params)
         qp = dict(params, queue_capacity=max(1 << 20, int(b["queue_pushed"] * 1.5)))
         n = grid.ncell
         hx = torch.tensor(g["x_HI"], dtype=torch.float64).pin_memory()
         hz = torch.tensor(g["x_HII"], dtype=torch.float64).pin_memory()
-        # k_ph in the path's own precision (FP32 on the mixed path), x_HI in FP64
         kdt = native.RT_DTYPE_F64 if precision == "fp64" else native.RT_DTYPE_F32
-        hk = torch.empty(n, dtype=torch.float64 if precision == "fp64" else torch.float32).pin_memory()
-        hxo = torch.empty(n, dtype=torch.float64).pin_memory()
+        kt = torch.float64 if precision == "fp64" else torch.float32
+        hk = [torch.empty(n, dtype=kt).pin_memory() for _ in range(2)]
+        hxo = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(2)]
         lib = native.lib()
-        segs = 0
-        for i in range(max(3, args.warmup) + args.steps):
-            if i == max(3, args.warmup):
-                torch.cuda.synchronize()
+        warm = max(3, args.warmup)
+        t0 = None
+        for i in range(warm + args.steps):
+            if i == warm:
+                native.rt_synchronize(grid.h)
                 t0 = time.perf_counter()
-            native.check(lib.rt_set_state(grid.h, None, hx.data_ptr(), hz.data_ptr(), native.RT_MEM_HOST))
+            native.check(lib.rt_set_state_async(grid.h, None, hx.data_ptr(), hz.data_ptr(), native.RT_MEM_HOST))
             grid.trace(sync=False, **qp)
             grid.chem(DT_S, 10, synth.ALPHA_B)
-            native.check(lib.rt_get_rates(grid.h, hk.data_ptr(), None, None, kdt, native.RT_MEM_HOST))
-            native.check(lib.rt_get_rates(grid.h, None, None, hxo.data_ptr(), native.RT_DTYPE_F64,
-                                          native.RT_MEM_HOST))
-            if i >= max(3, args.warmup):
-                segs += native.rt_get_budget(grid.h)["segments"]
+            native.check(lib.rt_wait_rates(grid.h))
+            native.check(lib.rt_get_rates_async(grid.h, hk[i % 2].data_ptr(), None, None, kdt, native.RT_MEM_HOST))
+            native.check(lib.rt_get_rates_async(grid.h, None, None, hxo[i % 2].data_ptr(), native.RT_DTYPE_F64,
+                                                native.RT_MEM_HOST))
+        native.rt_synchronize(grid.h)
         dt = time.perf_counter() - t0
+        last = native.rt_get_budget(grid.h)
+        assert last["segments"] == b["segments"], (last["segments"], b["segments"])
+        # the last step's read-back is the one-step result of the snapshot
+        ref = grid.rates(dtype=kdt)
+        assert np.array_equal(hk[(warm + args.steps - 1) % 2].numpy(), np.asarray(ref["kph"]))
         grid.close()
-        return dict(value=segs / dt, h2d=2 * n * 8, d2h=n * (hk.element_size() + 8))
+        return dict(value=b["segments"] * args.steps / dt, h2d=2 * n * 8, d2h=n * (hk[0].element_size() + 8),
+                    ms_per_step=1e3 * dt / args.steps)
 
     res = {}
     for prec in args.precisions:
@@ -266,15 +318,11 @@ def run_native(args, rank, world, local):
     value = all_segments / total_s
     ee = e2e(head) if not args.no_e2e else dict(value=None, h2d=0, d2h=0)
     peaks, peak_kind = _peaks()
-    # algorithmic bytes per launch: per segment the n_HI read (FP64, or the FP32
-    # pair: 8 bytes) and the k_ph reduction (8 / 4 bytes), plus the Gamma
-    # reduction where photons carry energy above 13.6 eV; per queue record one
-    # write and one read of 48 bytes
-    red = (8 if head == "fp64" else 4) * (2 if np.any(np.asarray(g["e_ph_eV"]) > 13.6) else 1)
-    alg = r["seg_per_step"] * (8 + red) + r["pushed"] * 2 * 48
-    achieved = alg / (kern_s / args.steps) / 1e9
     wtag = "clumpy256" if args.workload == "clumpy" else f"stromgren{args.grid}"
     traffic = _profiled_traffic(head, wtag)
+    words = 1 << int(np.ceil(np.log2(int(np.prod(g["dims"])))))
+    red_peak = native.rt_probe_red(local, native.RT_DTYPE_F64 if head == "fp64" else native.RT_DTYPE_F32, words)
+    gamma = bool(np.any(np.asarray(g["e_ph_eV"]) > 13.6))
     if args.workload == "clumpy":
         wl = WORKLOAD_CLUMPY
     else:
@@ -288,12 +336,12 @@ def run_native(args, rank, world, local):
                    "precision": head, "segments_per_step": r["seg_per_step"],
                    "queue_records_per_step": r["pushed"], "l2": "flushed (512 MB write) between steps",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0),
-                     "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs", 6800.0),
-                     "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes": alg,
-                     "kernel": "trace_kernel", "kernel_ms": 1e3 * kern_s / args.steps},
+        "roofline": trace_roofline(head, r["seg_per_step"], r["pushed"], 1e3 * kern_s / args.steps, gamma,
+                                   red_peak, peaks, peak_kind, traffic, words),
         "e2e": {"value": ee["value"], "unit": UNIT, "h2d_bytes_per_step": ee["h2d"],
-                "d2h_bytes_per_step": ee["d2h"]},
+                "d2h_bytes_per_step": ee["d2h"], "ms_per_step": ee.get("ms_per_step"),
+                "how": "C ABI, pinned host buffers, rt_set_state_async / rt_get_rates_async pipelined "
+                       "one step deep"},
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
     }
@@ -325,6 +373,9 @@ def run_native(args, rank, world, local):
         # per cell: n_H, x_HI (FP64), k_ph read, the per-cell value written and read back
         out["timestep"] = {"ms": ms, "dt_s": dt_p, "cells": cells,
                            "gb_s": cells * (8 + 8 + (8 if head == "fp64" else 4) + 4 + 4) / (ms / 1e3) / 1e9}
+    # the clumpy multi-source configuration: 256^3, 1000 sources, one trace per step
+    if not args.no_clumpy and args.workload != "clumpy":
+        out["clumpy256"] = clumpy_leg(args, ctx, stream, flush, head, peaks, peak_kind, local)
     # photon types (Sec. 3.2): the clumpy configuration with H I, He I and He II sources
     if not args.no_types:
         out["photon_types"] = photon_types(args, ctx, stream, flush, head)
@@ -404,6 +455,51 @@ def precision_error(g, ref, final) -> dict:
         out[prec] = {"kph_max_rel": float(rk.max()), "kph_median_rel": float(np.median(rk)),
                      "x_HI_max_rel": float(rx.max()), "x_HI_median_rel": float(np.median(rx))}
     return out
+
+
+def clumpy_leg(args, ctx, stream, flush, precision, peaks, peak_kind, local) -> dict:
+    """The clumpy multi-source configuration (256^3 log-normal medium, 1000
+    sources, Ndot log-uniform in [1e48, 1e50], 13.6-29.6 eV; HEALPix level 1,
+    Phi_c 5.1, f_term 1e-10, FP32-mixed, FP32 rate grids): one rt_trace per
+    timed step, L2 flushed between steps, with the trace kernel's HBM and L2
+    reduction rooflines."""
+    import torch
+    from paper_1012_2865_gb300 import native, synth
+    g = synth.clumpy()
+    grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
+    params = dict(synth.DEFAULT_PARAMS)
+    b = grid.trace(**params)  # sizes the queue
+    qp = dict(params, queue_capacity=max(1 << 20, int(b["queue_pushed"] * 1.5)))
+    for _ in range(max(3, args.warmup)):
+        grid.trace(sync=False, **qp)
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 2)
+    step_ms, kern_ms, launches = [], [], 0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = native.rt_kernel_launches()
+        e0.record(stream)
+        grid.trace(sync=False, **qp)
+        e1.record(stream)
+        e1.synchronize()
+        launches += native.rt_kernel_launches() - l0
+        bb = native.rt_get_budget(grid.h)
+        assert bb["segments"] == b["segments"]
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(bb["kernel_ms"])
+    grid.close()
+    words = 1 << int(np.ceil(np.log2(int(np.prod(g["dims"])))))
+    red_peak = native.rt_probe_red(local, native.RT_DTYPE_F64 if precision == "fp64" else native.RT_DTYPE_F32, words)
+    t = sum(step_ms) / 1e3
+    km = sum(kern_ms) / steps
+    return {"workload": WORKLOAD_CLUMPY.replace(" + rt_chem_update (0.5 Myr, 10 substeps)", ""),
+            "value": b["segments"] * steps / t, "unit": UNIT, "ms_per_step": 1e3 * t / steps,
+            "segments_per_step": b["segments"], "queue_records_per_step": b["queue_pushed"],
+            "precision": precision, "gpu_launches": int(launches), "l2": "flushed (512 MB write) between steps",
+            "roofline": trace_roofline(precision, b["segments"], b["queue_pushed"], km, True, red_peak, peaks,
+                                       peak_kind, _profiled_traffic(precision, "clumpy256"), words)}
 
 
 def photon_types(args, ctx, stream, flush, precision) -> dict:
@@ -625,47 +721,112 @@ def oracle_step(g, x, z):
     return o["segments"], o["kph"], x1, o["budget"][0]
 
 
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_step_threads(g, x, z, threads: int):
+    """One step of the oracle shared by `threads` host threads: each takes root
+    packages one at a time from a shared counter and traces them
+    (oracle.trace_roots) into its own k_ph (thread-private), the partial fields
+    are summed at the end, and the update runs on equal cell ranges.  Returns
+    (segments, k_ph, x_HI after the update, emitted)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    from paper_1012_2865_gb300 import synth
+    p = synth.DEFAULT_PARAMS
+    nroots = len(g["ndot"]) * 12 * 4 ** p["level0"]
+    lock = threading.Lock()
+    nxt = [0]
+
+    def work(_):
+        acc, segs, emitted = None, 0, 0.0
+        while True:
+            with lock:
+                r = nxt[0]
+                nxt[0] += 1
+            if r >= nroots:
+                return acc, segs, emitted
+            o = oracle.trace_roots(g["dims"], g["box_len_cm"], g["n_H"], x, g["pos_cm"], g["ndot"], g["e_ph_eV"],
+                                   g["sigma_cm2"], r, 1, **p)
+            if acc is None:
+                acc = o["kph"]
+            else:
+                np.add(acc, o["kph"], out=acc)
+            segs += o["segments"]
+            emitted += float(o["budget"][0])
+
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(work, range(threads)))
+        kph = np.zeros(int(np.prod(g["dims"])))
+        for acc, _, _ in parts:
+            if acc is not None:
+                kph += acc
+        n = kph.size
+        cuts = [n * i // threads for i in range(threads + 1)]
+        upd = list(ex.map(lambda i: oracle.chem(g["n_H"][cuts[i]:cuts[i + 1]], x[cuts[i]:cuts[i + 1]],
+                                                z[cuts[i]:cuts[i + 1]], kph[cuts[i]:cuts[i + 1]], DT_S, 10,
+                                                synth.ALPHA_B)[0], range(threads)))
+    return sum(q[1] for q in parts), kph, np.concatenate(upd), sum(q[2] for q in parts)
+
+
 def cpu_baseline(seconds: float):
-    """The oracle timed on the benchmark step; also returns its first step's
-    (k_ph, x_HI, emitted) for the precision report."""
+    """The oracle timed on the benchmark step on the machine's host cores: shared by
+    one thread per core over the root packages (thread-private k_ph, summed),
+    and, beside it, on one thread.  Also returns the first step's (k_ph, x_HI,
+    emitted) for the precision report."""
     from paper_1012_2865_gb300 import synth
     g = synth.stromgren_snapshot(128)
-    segs, n, ref = 0, 0, None
-    t0 = time.perf_counter()
-    while True:
-        s, kph, x1, em = oracle_step(g, g["x_HI"], g["x_HII"])
-        segs += s
-        if ref is None:
-            ref = (kph, x1, em)
-        n += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
-    return ({"value": segs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-             "sample": f"{n} full steps of the bench workload (FP64 C oracle, 1 thread), {dt:.1f} s"}, ref)
+    threads = host_threads()
+
+    def timed(step, budget):
+        segs, n, first = 0, 0, None
+        t0 = time.perf_counter()
+        while True:
+            s, kph, x1, em = step()
+            segs += s
+            first = first or (kph, x1, em)
+            n += 1
+            if time.perf_counter() - t0 >= budget:
+                return segs / (time.perf_counter() - t0), n, time.perf_counter() - t0, first
+
+    v1, n1, t1, ref = timed(lambda: oracle_step(g, g["x_HI"], g["x_HII"]), seconds / 2)
+    vt, nt, tt, _ = timed(lambda: oracle_step_threads(g, g["x_HI"], g["x_HII"], threads), seconds / 2)
+    return ({"value": vt, "unit": UNIT, "cores": threads, "kind": "oracle",
+             "sample": f"{nt} full steps of the bench workload, FP64 C oracle shared by {threads} host threads "
+                       f"over the root packages (thread-private k_ph, summed), {tt:.1f} s",
+             "single_thread": {"value": v1, "cores": 1, "sample": f"{n1} full steps, {t1:.1f} s"}}, ref)
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the benchmark step, shared by one
+    thread per host core over the root packages."""
     if rank != 0:
         return None
     from paper_1012_2865_gb300 import synth
     import oracle
     oracle.build()
     g = synth.stromgren_snapshot(128)
+    threads = host_threads()
     for _ in range(args.warmup):
-        oracle_step(g, g["x_HI"], g["x_HII"])
+        oracle_step_threads(g, g["x_HI"], g["x_HII"], threads)
     segs = 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        segs += oracle_step(g, g["x_HI"], g["x_HII"])[0]
+        segs += oracle_step_threads(g, g["x_HI"], g["x_HII"], threads)[0]
     dt = time.perf_counter() - t0
     v = segs / dt
     return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": {"workload": WORKLOAD, "precision": "fp64 oracle"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full steps of the bench workload"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} full steps of the bench workload, shared by {threads} host "
+                                       "threads over the root packages"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -676,7 +837,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precisions", default="fp32_mixed,fp64")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -685,6 +846,7 @@ def main():
     ap.add_argument("--no-timestep", action="store_true", help="skip the adaptive-timestep (Sec. 3.4) leg")
     ap.add_argument("--no-fsl", action="store_true", help="skip the finite-speed-of-light (Application 5) leg")
     ap.add_argument("--no-types", action="store_true", help="skip the photon-types (Sec. 3.2) leg")
+    ap.add_argument("--no-clumpy", action="store_true", help="skip the clumpy 256^3, 1000-source leg")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the 500 Myr Strömgren evolution in each precision")
     ap.add_argument("--serve-requests", type=int, default=16)

@@ -33,6 +33,9 @@ cudaError_t launch_refresh(int precision, long long ncell, const double* nH, con
 cudaError_t launch_convert(long long n, const void* src, int src_dtype, void* dst, int dst_dtype,
                            cudaStream_t st, double scale = 1.0);
 cudaError_t launch_complement(long long n, const double* x, double* out, cudaStream_t st);
+cudaError_t launch_commit_state(int precision, long long n, unsigned long long* ctl, const double* sn,
+                               const double* sx, const double* sz, double* nH, double* xHI, double* xHII, void* nhi,
+                               cudaStream_t st);
 cudaError_t launch_timestep(long long n, int nx, int ny, int nz, const double* nH, const double* xHI, const void* K,
                             int fp64_rates, double sdx, double tau_front, float eps, float alpha, float dt_max,
                             float unit, float* dtc, unsigned int* out, cudaStream_t st);
@@ -215,7 +218,24 @@ struct rt_grid {
   rt_batch* batch = nullptr;                 // the batch holding the grid (at most one)
   int batch_slot = -1;
   cudaStream_t batch_stream = nullptr;       // set while the grid is in a batch
+  // Uploads and read-backs that do not wait (rt_set_state_async,
+  // rt_get_rates_async): host->device copies run on `up`, device->host copies
+  // on `dn`, through library-owned staging areas, ordered against the grid's
+  // stream by events; created on first use.
+  cudaStream_t up = nullptr, dn = nullptr;
+  cudaEvent_t ev_up = nullptr, ev_commit = nullptr, ev_snap = nullptr;
+  cudaEvent_t ev_dl[3] = {nullptr, nullptr, nullptr};  // last host copy of each staged field
+  double* up_stage = nullptr;                // 3 * ncell doubles: n_H, x_HI, x_HII
+  char* dn_stage = nullptr;                  // 3 * ncell * 8 bytes: k_ph, Gamma, x_HI
+  std::string set_err;                       // message of a rejected asynchronous state
   ~rt_grid() {
+    if (up) cudaStreamSynchronize(up);
+    if (dn) cudaStreamSynchronize(dn);
+    cudaFree(up_stage); cudaFree(dn_stage);
+    for (cudaEvent_t ev : {ev_up, ev_commit, ev_snap, ev_dl[0], ev_dl[1], ev_dl[2]})
+      if (ev) cudaEventDestroy(ev);
+    if (up) cudaStreamDestroy(up);
+    if (dn) cudaStreamDestroy(dn);
     cudaFree(nH); cudaFree(xHI); cudaFree(xHII); cudaFree(nhi); cudaFree(K); cudaFree(G);
     cudaFree(acc); cudaFree(cnt); cudaFree(inst_dev); cudaFree(src_dev);
     for (int t = 0; t < 2; ++t) {
@@ -825,6 +845,20 @@ static void commit_flight(rt_grid* g, bool fsl) {
   F.live = true;
 }
 
+// A state uploaded by rt_set_state_async failed its check on the device:
+// keep the message for the caller and clear the device's latch (the grid kept
+// its previous state).
+static void note_rejected_state(rt_grid* g, unsigned long long bad_n, unsigned long long bad_x) {
+  char buf[160];
+  if (bad_n != ~0ULL)
+    snprintf(buf, sizeof buf, "rt_set_state_async: n_H[%llu] is negative or not finite; the state was not changed",
+             bad_n);
+  else
+    snprintf(buf, sizeof buf, "rt_set_state_async: x_HI[%llu] lies outside [0, 1]; the state was not changed", bad_x);
+  g->set_err = buf;
+  cudaMemsetAsync(g->ts.ctl + CTL_SET_ERR, 0, sizeof(unsigned long long), g->stream);
+}
+
 static int read_budget(rt_grid* g, rt_budget* out) {
   double* hacc = (double*)g->host_rb;
   unsigned long long* hcnt = (unsigned long long*)((char*)g->host_rb + 64);
@@ -853,6 +887,10 @@ static int read_budget(rt_grid* g, rt_budget* out) {
   out->halted = hacc[4];
   out->n_resumed = hctl[CTL_RESUME];
   out->n_halted = hctl[CTL_HALTED];
+  if (hctl[CTL_SET_ERR]) {
+    note_rejected_state(g, hctl[CTL_SET_BADN], hctl[CTL_SET_BADX]);
+    out->status = RT_ERR_INVALID_ARG;
+  }
   if (g->fl.live) g->fl.last_halted = out->n_halted;
   unsigned long long pkgs = out->n_resumed;
   for (int l = 0; l < kLevels; ++l) pkgs += out->counts[l];
@@ -900,6 +938,8 @@ int rt_trace(rt_grid* g, const rt_trace_params* p, rt_budget* out) {
       }
       if (again) continue;
     }
+    if (out->status == RT_ERR_INVALID_ARG && !g->set_err.empty())
+      return fail(RT_ERR_INVALID_ARG, "rt_trace: %s", g->set_err.c_str());
     if (out->status != RT_OK)
       return fail(out->status, "rt_trace: device status %d (queue capacity %llu, largest pass %llu, passes %d)",
                   out->status, (unsigned long long)g->ts.cap, (unsigned long long)out->queue_peak, out->passes);
@@ -913,6 +953,8 @@ int rt_get_budget(rt_grid* g, rt_budget* out) {
   if (int rcw = wait_batch(g)) return rcw;
   int rc = read_budget(g, out);
   if (rc) return rc;
+  if (out->status == RT_ERR_INVALID_ARG && !g->set_err.empty())
+    return fail(RT_ERR_INVALID_ARG, "rt_get_budget: %s", g->set_err.c_str());
   if (out->status != RT_OK) return fail(out->status, "rt_get_budget: device status %d", out->status);
   return RT_OK;
 }
@@ -971,6 +1013,103 @@ int rt_set_state(rt_grid* g, const double* n_H, const double* x_HI, const double
 // The FP32-mixed grid keeps Gamma in eV/s (FP32 erg/s values of faint cells
 // fall below the FP32 normal range); this scale turns it into erg/s.
 static double gamma_scale(const rt_grid* g) { return g->precision == RT_FP64 ? 1.0 : kEvErg; }
+
+// Streams, events and (when `stage_up` / `stage_dn`) staging areas of the
+// calls that do not wait.  Allocating synchronises the device: the first
+// such call on a grid does it.
+static int ensure_async(rt_grid* g, bool stage_up, bool stage_dn) {
+  if (!g->up) CUDA_TRY(cudaStreamCreateWithFlags(&g->up, cudaStreamNonBlocking));
+  if (!g->dn) CUDA_TRY(cudaStreamCreateWithFlags(&g->dn, cudaStreamNonBlocking));
+  cudaEvent_t* evs[6] = {&g->ev_up, &g->ev_commit, &g->ev_snap, &g->ev_dl[0], &g->ev_dl[1], &g->ev_dl[2]};
+  for (cudaEvent_t* ev : evs)
+    if (!*ev) CUDA_TRY(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+  const size_t n8 = (size_t)g->ncell * 8;
+  if (stage_up && !g->up_stage) CUDA_TRY(cudaMalloc((void**)&g->up_stage, 3 * n8));
+  if (stage_dn && !g->dn_stage) CUDA_TRY(cudaMalloc((void**)&g->dn_stage, 3 * n8));
+  return RT_OK;
+}
+
+int rt_set_state_async(rt_grid* g, const double* n_H, const double* x_HI, const double* x_HII, int mem_kind) {
+  NvtxRange nr("rt_set_state_async");
+  if (!g || !x_HI) return fail(RT_ERR_INVALID_ARG, "rt_set_state_async: grid and x_HI are required");
+  if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE)
+    return fail(RT_ERR_INVALID_ARG, "rt_set_state_async: mem_kind %d", mem_kind);
+  if (g->batch) return fail(RT_ERR_STATE, "rt_set_state_async: the grid is in a batch (use rt_set_state)");
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  int rc = ensure_async(g, mem_kind == RT_MEM_HOST, false);
+  if (rc) return rc;
+  const long long n = g->ncell;
+  const size_t n8 = (size_t)n * 8;
+  cudaStream_t st = g->stream;
+  const double* sn = n_H;
+  const double* sx = x_HI;
+  const double* sz = x_HII;
+  if (mem_kind == RT_MEM_HOST) {
+    // the staging area is free once the previous commit has read it
+    CUDA_TRY(cudaStreamWaitEvent(g->up, g->ev_commit, 0));
+    double* d = g->up_stage;
+    if (n_H) CUDA_TRY(cudaMemcpyAsync(d, n_H, n8, cudaMemcpyHostToDevice, g->up));
+    CUDA_TRY(cudaMemcpyAsync(d + n, x_HI, n8, cudaMemcpyHostToDevice, g->up));
+    if (x_HII) CUDA_TRY(cudaMemcpyAsync(d + 2 * n, x_HII, n8, cudaMemcpyHostToDevice, g->up));
+    CUDA_TRY(cudaEventRecord(g->ev_up, g->up));
+    CUDA_TRY(cudaStreamWaitEvent(st, g->ev_up, 0));
+    sn = n_H ? d : nullptr;
+    sx = d + n;
+    sz = x_HII ? d + 2 * n : nullptr;
+  }
+  CUDA_TRY(cudaMemsetAsync(g->ts.ctl + CTL_CHECK_N, 0xff, 2 * sizeof(unsigned long long), st));
+  LAUNCH_TRY(launch_check_state(n, sn, sx, g->ts.ctl + CTL_CHECK_N, st));
+  LAUNCH_TRY(launch_commit_state(g->precision, n, g->ts.ctl, sn, sx, sz, g->nH, g->xHI, g->xHII, g->nhi, st));
+  CUDA_TRY(cudaEventRecord(g->ev_commit, st));
+  return RT_OK;
+}
+
+int rt_get_rates_async(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype, int mem_kind) {
+  NvtxRange nr("rt_get_rates_async");
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_get_rates_async: grid is NULL");
+  if (dtype != RT_DTYPE_F64 && dtype != RT_DTYPE_F32)
+    return fail(RT_ERR_INVALID_ARG, "rt_get_rates_async: dtype %d", dtype);
+  if (mem_kind != RT_MEM_HOST && mem_kind != RT_MEM_DEVICE)
+    return fail(RT_ERR_INVALID_ARG, "rt_get_rates_async: mem_kind %d", mem_kind);
+  if (g->batch) return fail(RT_ERR_STATE, "rt_get_rates_async: the grid is in a batch (use rt_get_rates)");
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  const int kd = g->precision == RT_FP64 ? RT_DTYPE_F64 : RT_DTYPE_F32;
+  const void* src[3] = {g->K, g->G, g->xHI};
+  const int sdt[3] = {kd, kd, RT_DTYPE_F64};
+  const double scale[3] = {1.0, gamma_scale(g), 1.0};
+  void* dst[3] = {kph, gamma, x_HI};
+  const long long n = g->ncell;
+  cudaStream_t st = g->stream;
+  if (mem_kind == RT_MEM_DEVICE) {
+    for (int f = 0; f < 3; ++f)
+      if (dst[f]) LAUNCH_TRY(launch_convert(n, src[f], sdt[f], dst[f], dtype, st, scale[f]));
+    return RT_OK;
+  }
+  int rc = ensure_async(g, false, true);
+  if (rc) return rc;
+  const size_t eb = dtype == RT_DTYPE_F64 ? 8 : 4, region = (size_t)n * 8;
+  // a field's staging region is free once its previous read-back has left it
+  for (int f = 0; f < 3; ++f) {
+    if (!dst[f]) continue;
+    CUDA_TRY(cudaStreamWaitEvent(st, g->ev_dl[f], 0));
+    LAUNCH_TRY(launch_convert(n, src[f], sdt[f], g->dn_stage + f * region, dtype, st, scale[f]));
+  }
+  CUDA_TRY(cudaEventRecord(g->ev_snap, st));
+  CUDA_TRY(cudaStreamWaitEvent(g->dn, g->ev_snap, 0));
+  for (int f = 0; f < 3; ++f) {
+    if (!dst[f]) continue;
+    CUDA_TRY(cudaMemcpyAsync(dst[f], g->dn_stage + f * region, (size_t)n * eb, cudaMemcpyDeviceToHost, g->dn));
+    CUDA_TRY(cudaEventRecord(g->ev_dl[f], g->dn));
+  }
+  return RT_OK;
+}
+
+int rt_wait_rates(rt_grid* g) {
+  if (!g) return fail(RT_ERR_INVALID_ARG, "rt_wait_rates: grid is NULL");
+  for (int f = 0; f < 3; ++f)
+    if (g->ev_dl[f]) CUDA_TRY(cudaEventSynchronize(g->ev_dl[f]));
+  return RT_OK;
+}
 
 static int copy_field(rt_grid* g, const void* src, int src_dtype, void* dst, int dtype, int mem_kind,
                       double scale = 1.0) {
@@ -1278,6 +1417,20 @@ int rt_synchronize(rt_grid* g) {
   if (!g) return fail(RT_ERR_INVALID_ARG, "rt_synchronize: grid is NULL");
   if (int rcw = wait_batch(g)) return rcw;
   CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (g->up) CUDA_TRY(cudaStreamSynchronize(g->up));
+  if (g->dn) CUDA_TRY(cudaStreamSynchronize(g->dn));
+  if (g->ev_commit) {
+    // a state uploaded by rt_set_state_async may have been rejected
+    unsigned long long* h = (unsigned long long*)((char*)g->host_rb + 3584);
+    CUDA_TRY(cudaMemcpyAsync(h, g->ts.ctl + CTL_SET_ERR, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (h[0]) {
+      note_rejected_state(g, h[1], h[2]);
+      CUDA_TRY(cudaStreamSynchronize(g->stream));
+      return fail(RT_ERR_INVALID_ARG, "rt_synchronize: %s", g->set_err.c_str());
+    }
+  }
   return RT_OK;
 }
 

@@ -185,6 +185,44 @@ __global__ void check_state_kernel(long long n, const double* __restrict__ nH, c
   }
 }
 
+// Commit of a gas state uploaded without waiting (rt_set_state_async), run
+// after check_state_kernel has left the first failing cells in
+// ctl[CTL_CHECK_N] and ctl[CTL_CHECK_X] (~0 = none).  When every cell passed,
+// the staged arrays replace the grid's -- n_H only when sn is given, x_HII
+// from sz or as 1 - x_HI -- and the absorber density n_HI = n_H x_HI is
+// refreshed (FP64, or the FP32 pair on the mixed path).  Otherwise nothing
+// changes and the rejection is latched in ctl[CTL_SET_ERR] (the first one
+// keeps its failing cells), where the next trace and rt_synchronize find it.
+template <bool PAIR>
+__global__ void commit_state_kernel(long long n, unsigned long long* __restrict__ ctl, const double* __restrict__ sn,
+                                    const double* __restrict__ sx, const double* __restrict__ sz,
+                                    double* __restrict__ nH, double* __restrict__ xHI, double* __restrict__ xHII,
+                                    void* __restrict__ nhi) {
+  const unsigned long long bn = ctl[CTL_CHECK_N], bx = ctl[CTL_CHECK_X];
+  if (bn != ~0ULL || bx != ~0ULL) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 &&
+        atomicCAS(&ctl[CTL_SET_ERR], 0ULL, (unsigned long long)RT_ERR_INVALID_ARG) == 0ULL) {
+      ctl[CTL_SET_BADN] = bn;
+      ctl[CTL_SET_BADX] = bx;
+    }
+    return;
+  }
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const double h = sn ? sn[c] : nH[c];
+    if (sn) nH[c] = h;
+    const double x = sx[c];
+    xHI[c] = x;
+    xHII[c] = sz ? sz[c] : __dsub_rn(1.0, x);
+    const double v = __dmul_rn(h, x);
+    if (PAIR) {
+      const F2 p = f2_from_double(v);
+      ((float2*)nhi)[c] = make_float2(p.hi, p.lo);
+    } else {
+      ((double*)nhi)[c] = v;
+    }
+  }
+}
+
 // Adaptive RT timestep (Sec. 3.4), step 1, Eq. "dtelec": per cell
 // eps / |k_ph + n_e alpha_B| (C_H = 0, n_e = n_H (1 - x_HI)) where the cell's
 // optical depth sdx n_HI exceeds tau_front, else dt_max; never above dt_max.
@@ -318,6 +356,17 @@ cudaError_t launch_check_state(long long n, const double* nH, const double* x, u
                                cudaStream_t st) {
   const int block = 256, grid = grid_for(n, block);
   check_state_kernel<<<grid, block, 0, st>>>(n, nH, x, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit_state(int precision, long long n, unsigned long long* ctl, const double* sn,
+                               const double* sx, const double* sz, double* nH, double* xHI, double* xHII, void* nhi,
+                               cudaStream_t st) {
+  const int block = 256, grid = grid_for(n, block);
+  if (precision == RT_FP64)
+    commit_state_kernel<false><<<grid, block, 0, st>>>(n, ctl, sn, sx, sz, nH, xHI, xHII, nhi);
+  else
+    commit_state_kernel<true><<<grid, block, 0, st>>>(n, ctl, sn, sx, sz, nH, xHI, xHII, nhi);
   return cudaGetLastError();
 }
 

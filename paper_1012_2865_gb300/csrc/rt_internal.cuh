@@ -31,6 +31,13 @@ enum CtlWord {
   CTL_RES_A = 53,        // this pass continues input records [RES_A, RES_B)
   CTL_RES_B = 54,
   CTL_HALTED = 56,       // packages halted so far in this trace (output store slots)
+  CTL_SET_ERR = 57,      // RT_ERR_INVALID_ARG once an asynchronously uploaded state was
+                         // rejected (until the host reports it); copied into STATUS
+                         // by every trace
+  CTL_SET_BADN = 58,     // first rejected cell of that state: n_H, x_HI (~0 = none)
+  CTL_SET_BADX = 59,
+  CTL_CHECK_N = 60,      // scratch of the state check: first bad n_H cell, x_HI cell
+  CTL_CHECK_X = 61,
   CTL_N = 64             // words (512 bytes)
 };
 

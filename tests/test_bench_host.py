@@ -54,3 +54,21 @@ def test_precision_report():
     assert rep["fp64"]["kph_max_rel"] == 0.0 and rep["fp64"]["x_HI_max_rel"] == 0.0
     np.testing.assert_allclose(rep["fp32_mixed"]["kph_max_rel"], 3e-6, rtol=1e-6)
     np.testing.assert_allclose(rep["fp32_mixed"]["x_HI_median_rel"], 1e-6, rtol=1e-6)
+
+
+def test_threaded_oracle_step_equals_the_oracle_step():
+    """The CPU baseline's threaded step (root packages shared by host threads,
+    thread-private k_ph summed, the update on cell ranges) gives the oracle's
+    step: the same segments and emitted photons, k_ph to summation order and
+    the same x_HI."""
+    import numpy as np
+    from paper_1012_2865_gb300 import synth
+    g = synth.stromgren_snapshot(32)
+    s1, k1, x1, e1 = bench.oracle_step(g, g["x_HI"], g["x_HII"])
+    s4, k4, x4, e4 = bench.oracle_step_threads(g, g["x_HI"], g["x_HII"], 4)
+    assert s1 == s4
+    assert abs(e1 - e4) <= 1e-12 * e1
+    m = k1 > 0
+    assert np.array_equal(k4 > 0, m)
+    assert np.max(np.abs(k4[m] - k1[m]) / k1[m]) < 1e-12
+    assert np.allclose(x4, x1, rtol=1e-12, atol=1e-15)
