@@ -487,7 +487,12 @@ class Grid:
         self.h = rt_create_grid(ctx, self.dims, g["box_len_cm"], g["n_H"], g["x_HI"],
                                 g.get("x_HII"), precision, stream)
         if len(g["ndot"]):
-            rt_add_sources(self.h, g["pos_cm"], g["ndot"], g["e_ph_eV"], g["sigma_cm2"])
+            try:
+                rt_add_sources(self.h, g["pos_cm"], g["ndot"], g["e_ph_eV"], g["sigma_cm2"])
+            except (RtError, ValueError):
+                rt_grid_destroy(self.h)  # a grid whose sources were refused is not kept
+                self.h = None
+                raise
 
     def trace(self, sync=True, **kw):
         return rt_trace(self.h, trace_params(**kw), sync=sync)

@@ -74,6 +74,7 @@ class Server:
         self.cancelled = []
         self.steps = 0
         self.segments = 0
+        self.oom_retries = 100  # admissions a request may retry after a failed allocation
         self._mem_info = mem_info
         self._mem_total = mem_total
 
@@ -112,8 +113,26 @@ class Server:
             if self.free_bytes() - need < self.reserve:
                 break
             self.pending.popleft()
-            req.handle = self.backend.Grid(self.ctx, req.grid, self.precision)
-            req.slot = self.batch.add(req.handle)
+            err = getattr(self.backend, "RtError", native.RtError)
+            try:
+                req.handle = self.backend.Grid(self.ctx, req.grid, self.precision)
+                req.slot = self.batch.add(req.handle)
+            except err as e:
+                if req.handle is not None:  # built, but the batch refused it
+                    req.handle.close()
+                    req.handle = None
+                req.slot = -1
+                tries = req.meta.get("oom_retries", 0)
+                if getattr(e, "code", None) == native.RT_ERR_OOM and tries < self.oom_retries:
+                    # memory taken by another user of the device since the
+                    # check: the request waits at the head of the queue
+                    req.meta["oom_retries"] = tries + 1
+                    self.pending.appendleft(req)
+                    break
+                req.finished = now
+                req.meta["error"] = f"admission: {e}"
+                self.failed.append(req)
+                continue
             req.admitted = now
             self.active[req.slot] = req
             n += 1
@@ -175,26 +194,42 @@ class Server:
         self._trace_all(now_fn)
         if not self.active:
             return 0
-        self.batch.chem(self.dt_s, self.nsub, self.alpha_B)
+        err = getattr(self.backend, "RtError", native.RtError)
+        try:
+            self.batch.chem(self.dt_s, self.nsub, self.alpha_B)
+        except err as e:
+            # one launch updates every grid: the error belongs to all of them
+            for slot in list(self.active):
+                self._retire(slot, now_fn(), self.failed, f"update: {e}")
+            return 0
         self.steps += 1
         finished = []
-        for slot, req in self.active.items():
-            b = self.batch.budget(slot)
+        for slot, req in list(self.active.items()):
+            try:
+                b = self.batch.budget(slot)
+            except err as e:
+                self._retire(slot, now_fn(), self.failed, f"budget: {e}")
+                continue
             req.segments += b["segments"]
             self.segments += b["segments"]
             req.steps_done += 1
             if req.steps_done >= req.nsteps:
                 finished.append(slot)
         for slot in finished:
-            req = self.active.pop(slot)
-            r = req.handle.rates()  # waits for the batch's update
+            req = self.active[slot]
+            try:
+                r = req.handle.rates()  # waits for the batch's update
+            except err as e:
+                self._retire(slot, now_fn(), self.failed, f"read-back: {e}")
+                continue
+            self.active.pop(slot)
             req.x_HI, req.kph = r["x_HI"], r["kph"]
             req.finished = now_fn()
             self.batch.remove(slot)
             req.handle.close()
             req.handle = None
             self.done.append(req)
-        return len(finished)
+        return sum(1 for slot in finished if slot not in self.active)
 
     def run(self, requests: list, time_limit_s: float = None) -> dict:
         """Serve a stream: request.arrival is in seconds from the start."""

@@ -13,14 +13,22 @@ from paper_1012_2865_gb300 import serve
 
 
 class FakeRtError(RuntimeError):
-    pass
+    def __init__(self, msg, code=3):
+        super().__init__(msg)
+        self.code = code
 
 
 class FakeGrid:
     live = []
     made = []
+    oom_left = 0  # the next constructions that fail as if the device's memory were gone
 
     def __init__(self, ctx, g, precision):
+        if g.get("invalid"):
+            raise FakeRtError("rt_add_sources: source 0 axis 0 outside the box", code=1)
+        if FakeGrid.oom_left > 0:
+            FakeGrid.oom_left -= 1
+            raise FakeRtError("rt_create_grid: cudaMalloc: out of memory", code=2)
         self.ncell = int(np.prod(g["dims"]))
         self.precision = precision
         self.poison = g.get("poison", False)  # its trace fails, alone or in a batch
@@ -76,8 +84,8 @@ class FakeBatch:
 BACKEND = types.SimpleNamespace(Grid=FakeGrid, Batch=FakeBatch, RtError=FakeRtError)
 
 
-def _request(rid, N, nsteps, arrival=0.0, poison=False):
-    g = {"dims": (N, N, N), "poison": poison}
+def _request(rid, N, nsteps, arrival=0.0, poison=False, invalid=False):
+    g = {"dims": (N, N, N), "poison": poison, "invalid": invalid}
     return serve.Request(rid=rid, grid=g, nsteps=nsteps, arrival=arrival)
 
 
@@ -186,4 +194,46 @@ def test_cancel_waiting_and_running_requests():
     assert [r.rid for r in srv.cancelled] == [2, 0]
     rep = srv.run([])
     assert rep["completed"] == 1 and srv.done[0].rid == 1 and rep["cancelled"] == 2
+    assert not FakeGrid.live
+
+
+def test_admission_failures_are_isolated():
+    """A request whose grid the library refuses leaves with the error instead
+    of ending the loop; one whose allocation fails (memory taken since the
+    check) waits at the head of the queue and is admitted later."""
+    FakeBatch.step_s = 0.0
+    FakeGrid.oom_left = 2
+    reqs = [_request(0, 16, nsteps=2), _request(1, 12, nsteps=1, invalid=True), _request(2, 20, nsteps=3)]
+    srv = _server(total_bytes=1 << 40, reserve=0, max_slots=8)
+    rep = srv.run(reqs)
+    assert FakeGrid.oom_left == 0
+    assert rep["failed"] == 1 and srv.failed[0].rid == 1 and "admission" in srv.failed[0].meta["error"]
+    assert rep["completed"] == 2 and sorted(r.rid for r in srv.done) == [0, 2]
+    assert srv.done[0].meta.get("oom_retries", 0) + srv.done[1].meta.get("oom_retries", 0) == 2
+    assert not FakeGrid.live
+
+
+def test_a_request_that_never_gets_its_memory_fails_after_its_retries():
+    FakeBatch.step_s = 0.0
+    FakeGrid.oom_left = 10 ** 6
+    srv = _server(total_bytes=1 << 40, reserve=0, max_slots=8)
+    srv.oom_retries = 5
+    rep = srv.run([_request(0, 16, nsteps=1)])
+    FakeGrid.oom_left = 0
+    assert rep["failed"] == 1 and srv.failed[0].meta["oom_retries"] == 5
+    assert "out of memory" in srv.failed[0].meta["error"]
+
+
+def test_a_failing_update_fails_every_active_request():
+    class BadChem(FakeBatch):
+        def chem(self, dt_s, nsub, alpha_B):
+            raise FakeRtError("rt_batch_chem: launch failed")
+    FakeBatch.step_s = 0.0
+    FakeGrid.live.clear()
+    srv = serve.Server(None, "fp32_mixed", max_slots=4, reserve_bytes=0, mem_info=lambda: 1 << 40,
+                       mem_total=lambda: 1 << 40,
+                       backend=types.SimpleNamespace(Grid=FakeGrid, Batch=BadChem, RtError=FakeRtError))
+    rep = srv.run([_request(0, 16, nsteps=2), _request(1, 16, nsteps=1)])
+    assert rep["failed"] == 2 and rep["completed"] == 0
+    assert all("update" in r.meta["error"] for r in srv.failed)
     assert not FakeGrid.live
