@@ -102,6 +102,15 @@ int na_setup(int dev, unsigned char** base, int* sms) {
 
 bool na_exact(double v) { return v == ldexp(floor(ldexp(v, 4)), -4) && fabs(v) <= 4096.0; }
 
+// The FP32 walker deposits Gamma in eV/s (an FP32 erg/s deposit of a faintly
+// lit cell would fall below the FP32 normal range); the caller's array is
+// turned into erg/s in place afterwards, the product taken in FP64 as
+// rt_get_rates takes it.
+__global__ void na_scale_kernel(float* a, long long n, double scale) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    a[c] = (float)((double)a[c] * scale);
+}
+
 }  // namespace
 
 extern "C" {
@@ -192,7 +201,7 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
         exact &= na_exact(S.s[a]) ? 1 : 0;
       }
       S.exact32 = exact && g->nx <= 4096 && g->ny <= 4096 && g->nz <= 4096;
-      S.k32 = make_float4((float)S.sdx, (float)S.w, (float)S.rw, (float)S.heat);
+      S.k32 = make_float4((float)S.sdx, (float)S.w, (float)S.rw, (float)(e_ph_eV[i] - kEHI));  // heat in eV
       S.s32 = make_float4(s32[0], s32[1], s32[2], S.exact32 ? 1.0f : 0.0f);
       S.slo32 = make_float4(slo[0], slo[1], slo[2], (float)(S.sdx - (double)(float)S.sdx));
       S.sabs32 = make_float4(sab[0], sab[1], sab[2], 0.0f);
@@ -244,6 +253,10 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
     if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
     if ((e = launch_trace(RT_FP32_MIXED, 0, A, per_sm * sms, 256, st)) != cudaSuccess)
       return na_fail(RT_ERR_CUDA, "trace launch", e);
+    long long blocks = ((long long)ncell + 255) / 256;
+    if (blocks > 8LL * sms) blocks = 8LL * sms;
+    na_scale_kernel<<<(int)blocks, 256, 0, st>>>(g->gamma, (long long)ncell, kEvErg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(RT_ERR_CUDA, "Gamma to erg/s", e);
   }
   // result: budget, counters and control words
   double hacc[4];

@@ -62,8 +62,31 @@ def test_noalloc_matches_regular_entry_point_twice(make):
         k = kph.double().cpu().numpy()
         gm = gamma.double().cpu().numpy()
         np.testing.assert_allclose(k[mask], ref_rates["kph"][mask], rtol=parity.TOL["fp32_mixed"])
-        np.testing.assert_allclose(gm[mask], ref_rates["gamma"][mask], rtol=parity.TOL["fp32_mixed"],
-                                   atol=1e-30)
+        if np.all(np.asarray(g["e_ph_eV"]) == 13.6):
+            # photons at the threshold heat nothing (Eq. "gamma")
+            assert not np.any(gm) and not np.any(ref_rates["gamma"])
+        else:
+            heated = mask & (ref_rates["gamma"] > 0)
+            assert heated.sum() > 0.9 * mask.sum()
+            np.testing.assert_allclose(gm[heated], ref_rates["gamma"][heated], rtol=parity.TOL["fp32_mixed"],
+                                       atol=0)
+            assert not np.any(gm[~mask & (ref_rates["gamma"] == 0)])
+
+
+def test_noalloc_matches_the_oracle():
+    """The allocation-free trace against the FP64 oracle on the same medium:
+    counts and checksums exact, k_ph and Gamma within the FP32-mixed tolerance
+    in every cell receiving more than 1e-8 of the emitted photons."""
+    g = _small_clumpy()
+    o = parity.run_oracle(g)
+    n_HI, n_H, x_HI, kph, gamma = _device_grid(g)
+    b = native.rt_trace_noalloc(g["dims"], g["box_len_cm"], n_HI, n_H, x_HI, kph, gamma, g["pos_cm"], g["ndot"],
+                                g["e_ph_eV"], g["sigma_cm2"], native.trace_params(checksums=True,
+                                                                                 **synth.DEFAULT_PARAMS))
+    torch.cuda.synchronize()
+    r = {"kph": kph.double().cpu().numpy(), "gamma": gamma.double().cpu().numpy()}
+    worst = parity.assert_trace_parity(g, b, r, o, "fp32_mixed")
+    assert worst["gamma"] <= parity.TOL["fp32_mixed"]
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits():
