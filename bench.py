@@ -398,6 +398,61 @@ def run_native(args, rank, world, local):
     return out
 
 
+def run_partition(args, rank, world, local):
+    """One large grid shared by the ranks by sources (the clumpy 256^3
+    configuration, 1000 sources): each rank holds the whole medium, traces its
+    contiguous share of the sources, the ranks sum k_ph, Gamma (FP32) and the
+    photon budget with one all-reduce per trace (NCCL), and every rank runs
+    the same update.  The timed step includes the exchange; the state is
+    restored (untimed) before each step.  Total work is fixed as ranks are
+    added (strong scaling)."""
+    import torch
+    from paper_1012_2865_gb300 import build, native, shard, synth
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = native.rt_ctx_create(local)
+    g = synth.clumpy()
+    prec = args.precisions[0]
+    sg = shard.ShardGrid(ctx, g, prec, rank, world)
+    x0 = torch.tensor(g["x_HI"], dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    params = dict(synth.DEFAULT_PARAMS)
+    sg.step(DT_S, 10, synth.ALPHA_B, **params)  # sizes the queue
+    for _ in range(max(3, args.warmup)):
+        native.rt_set_state(sg.grid.h, x0)
+        sg.step(DT_S, 10, synth.ALPHA_B, **params)
+    total_s, segs = 0.0, 0
+    torch.cuda.synchronize()
+    barrier()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            native.rt_set_state(sg.grid.h, x0)
+            flush.zero_()
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            b = sg.step(DT_S, 10, synth.ALPHA_B, **params)
+            torch.cuda.synchronize()
+            total_s += time.perf_counter() - t0
+            segs += b["segments"]
+    barrier()
+    # the slowest rank's time; every rank already holds the whole trace's segments
+    t_max, _ = reduce_over_ranks(total_s, 0)
+    sg.close()
+    return {"metric": METRIC, "value": segs / t_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_CLUMPY, "precision": prec, "segments_per_step": segs // args.steps,
+                       "parallelism": f"sources partitioned over {world} ranks; one all-reduce of k_ph, Gamma and "
+                                      "the photon budget per trace",
+                       "l2": "flushed (512 MB write) between steps"},
+            "e2e": {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                    "note": "device-resident mode; see the default run for the end-to-end figure"},
+            "clocks": clk.summary(), "gpu_launches": None}
+
+
 def stromgren_500myr(ctx, stream, precisions) -> dict:
     """Test 1 at 128^3 evolved over 500 Myr (1000 steps of trace + update, dt 0.5 Myr)
     in each precision: the volume-equivalent I-front radius against the closed form
@@ -847,6 +902,9 @@ def main():
     ap.add_argument("--no-fsl", action="store_true", help="skip the finite-speed-of-light (Application 5) leg")
     ap.add_argument("--no-types", action="store_true", help="skip the photon-types (Sec. 3.2) leg")
     ap.add_argument("--no-clumpy", action="store_true", help="skip the clumpy 256^3, 1000-source leg")
+    ap.add_argument("--partition", default="replicas", choices=["replicas", "sources"],
+                    help="replicas: one independent problem per rank (default); sources: the clumpy 256^3 grid "
+                         "shared by the ranks by sources, one all-reduce per trace")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the 500 Myr Strömgren evolution in each precision")
     ap.add_argument("--serve-requests", type=int, default=16)
@@ -868,7 +926,8 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
         dist.barrier()
-    out = run_native(args, rank, world, local)
+    out = run_partition(args, rank, world, local) if args.partition == "sources" else \
+        run_native(args, rank, world, local)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

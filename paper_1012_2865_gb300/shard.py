@@ -10,12 +10,15 @@ of the whole trace and runs the same ionisation update, so the ranks' states
 stay identical.  The exchange is the only communication per step.
 
 `shard_trace` runs one rank's share and returns its partial results;
-`install` writes the summed rates back into the grid.  The all-reduce itself
-is the caller's (`torch.distributed.all_reduce` between ranks).  With a
-finite speed of light the packages in flight belong to the sources that
-emitted them, so each rank keeps its own between steps: `ShardGrid` holds a
-rank's grid across steps, and the budget sums carry the photons resumed and
-halted.
+`allreduce` sums the partial rates (in place) and budgets over the ranks of a
+`torch.distributed` process group -- NCCL with the rates as CUDA tensors, or
+gloo with host tensors -- and `install` writes the sums back into the grid.
+`ShardGrid.step` is one coupled step of the whole grid on one rank: its share
+of the trace, the exchange, the installation and the (replicated) update.
+With a finite speed of light the packages in flight belong to the sources
+that emitted them, so each rank keeps its own between steps: `ShardGrid`
+holds a rank's grid across steps, and the budget sums carry the photons
+resumed and halted.
 """
 from __future__ import annotations
 
@@ -59,6 +62,22 @@ def budget_from_vector(f, i) -> dict:
     return out
 
 
+def allreduce(kph, gamma, budget: dict, group=None) -> dict:
+    """Sum k_ph and Gamma (torch tensors, summed in place) and the photon
+    budget over the ranks of `group` (one exchange per trace); returns the
+    whole trace's budget.  The budget travels on the rates' device."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return budget  # a single process holds the whole trace
+    f, i = budget_vector(budget)
+    ft = torch.from_numpy(f).to(kph.device)
+    it = torch.from_numpy(i).to(kph.device)
+    for t in (kph, gamma, ft, it):
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return budget_from_vector(ft.cpu().numpy(), it.cpu().numpy())
+
+
 def shard_trace(ctx, g: dict, precision: str, rank: int, world: int, where: str = "device", **params):
     """Trace this rank's sources on a grid holding the whole medium.
 
@@ -83,14 +102,18 @@ class ShardGrid:
     all-reduce, install() writes the sums into the grid and chem() advances
     the (identical on every rank) state."""
 
-    def __init__(self, ctx, g: dict, precision: str, rank: int, world: int):
+    def __init__(self, ctx, g: dict, precision: str, rank: int, world: int, backend=None):
+        # `backend` (the native module by default) may be replaced by a
+        # stand-in with the same calls, so the exchange can be exercised
+        # without a device
+        self.lib = backend if backend is not None else native
         sub, self.s0 = shard_of(g, rank, world)
         self.precision = precision
         self.nsrc = len(sub["ndot"])
-        self.grid = native.Grid(ctx, dict(sub, ndot=[]), precision)
-        native.rt_set_source_offset(self.grid.h, self.s0)
+        self.grid = self.lib.Grid(ctx, dict(sub, ndot=[]), precision)
+        self.lib.rt_set_source_offset(self.grid.h, self.s0)
         if self.nsrc:
-            native.rt_add_sources(self.grid.h, sub["pos_cm"], sub["ndot"], sub["e_ph_eV"], sub["sigma_cm2"])
+            self.lib.rt_add_sources(self.grid.h, sub["pos_cm"], sub["ndot"], sub["e_ph_eV"], sub["sigma_cm2"])
 
     def set_source_rates(self, ndot_all):
         """Rates of every source of the whole list; this rank takes its range."""
@@ -100,11 +123,27 @@ class ShardGrid:
     def trace(self, where: str = "device", **params):
         b = self.grid.trace(**params)
         dt = native.RT_DTYPE_F64 if self.precision == "fp64" else native.RT_DTYPE_F32
-        r = native.rt_get_rates(self.grid.h, self.grid.ncell, dt, where)
+        r = self.lib.rt_get_rates(self.grid.h, self.grid.ncell, dt, where)
         return b, r["kph"], r["gamma"]
 
     def install(self, kph, gamma):
-        install(self.grid, kph, gamma)
+        self.lib.rt_set_rates(self.grid.h, kph, gamma)
+
+    def step(self, dt_s: float, nsub: int, alpha_B: float, group=None, **params) -> dict:
+        """One coupled step of the whole grid on this rank: trace this rank's
+        sources, sum the rates and budgets over the ranks (NCCL: the rates stay
+        CUDA tensors; gloo: host tensors), install the sums, update.  Returns
+        the whole trace's budget."""
+        import torch
+        import torch.distributed as dist
+        on_device = not dist.is_initialized() or dist.get_backend(group) == "nccl"
+        b, kph, gamma = self.trace(where="device" if on_device else "host", **params)
+        if not on_device:
+            kph, gamma = torch.from_numpy(np.asarray(kph)), torch.from_numpy(np.asarray(gamma))
+        total = allreduce(kph, gamma, b, group)
+        self.install(kph if on_device else kph.numpy(), gamma if on_device else gamma.numpy())
+        self.chem(dt_s, nsub, alpha_B)
+        return total
 
     def chem(self, dt_s, nsub, alpha_B):
         self.grid.chem(dt_s, nsub, alpha_B)

@@ -176,3 +176,101 @@ def test_source_ranges_partition_the_list():
             assert got[0][0] == 0 and got[-1][1] == nsrc
             assert all(a[1] == b[0] for a, b in zip(got, got[1:]))
             assert max(b - a for a, b in got) - min(b - a for a, b in got) <= 1
+
+
+class _OracleGrid:
+    """Stands in for native.Grid on the host: the oracle traces the grid's
+    sources (with their global numbering) and updates its state."""
+
+    def __init__(self, ctx, g, precision):
+        import numpy as np
+        self.g = dict(g)
+        self.h = self
+        self.ncell = int(np.prod(g["dims"]))
+        self.x = np.asarray(g["x_HI"], dtype=np.float64).copy()
+        self.z = np.asarray(g.get("x_HII", 1.0 - self.x), dtype=np.float64).copy()
+        self.off = 0
+        self.kph = self.gamma = None
+
+    def add(self, pos, ndot, e, sg):
+        self.g.update(pos_cm=pos, ndot=ndot, e_ph_eV=e, sigma_cm2=sg)
+
+    def trace(self, **params):
+        import oracle
+        g = self.g
+        o = oracle.trace(g["dims"], g["box_len_cm"], g["n_H"], self.x, g["pos_cm"], g["ndot"], g["e_ph_eV"],
+                         g["sigma_cm2"], src_offset=self.off, **params)
+        self.kph, self.gamma = o["kph"], o["gamma"]
+        return dict(emitted=o["budget"][0], absorbed=o["budget"][1], escaped=o["budget"][2], counts=o["counts"],
+                    hashes=o["hashes"], segments=o["segments"])
+
+    def chem(self, dt_s, nsub, alpha_B):
+        import oracle
+        self.x, self.z = oracle.chem(self.g["n_H"], self.x, self.z, self.kph, dt_s, nsub, alpha_B)
+
+    def close(self):
+        pass
+
+
+def _oracle_backend():
+    import types
+    import numpy as np
+
+    def set_rates(h, k, g):
+        h.kph, h.gamma = np.asarray(k, dtype=np.float64), np.asarray(g, dtype=np.float64)
+    return types.SimpleNamespace(
+        Grid=_OracleGrid, rt_set_source_offset=lambda h, s0: setattr(h, "off", s0),
+        rt_add_sources=lambda h, pos, ndot, e, sg: h.add(pos, ndot, e, sg),
+        rt_get_rates=lambda h, n, dt, where: {"kph": h.kph.copy(), "gamma": h.gamma.copy()},
+        rt_set_rates=set_rates)
+
+
+def _shard_step_rank(rank, world, port, q):
+    """ShardGrid.step on gloo: each rank traces its share of the sources, the
+    rates and budgets are summed over the ranks, every rank installs the sums
+    and updates its (identical) state."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1012_2865_gb300 import shard, synth
+    g = synth.clumpy(N=16, nsrc=6, seed=41)
+    sg = shard.ShardGrid(None, g, "fp64", rank, world, backend=_oracle_backend())
+    out = []
+    for _ in range(2):
+        b = sg.step(0.5 * synth.MYR_S, 10, synth.ALPHA_B, **synth.DEFAULT_PARAMS)
+        out.append((b, sg.grid.kph.copy(), sg.grid.x.copy()))
+    q.put((rank, out))
+    dist.destroy_process_group()
+
+
+def test_shard_grid_step_exchanges_once_per_trace():
+    """Two coupled steps of a source-partitioned grid through ShardGrid.step
+    (the path a multi-GPU run takes, here on gloo with the oracle as each
+    rank's tracer) equal the same steps of the whole grid on one process."""
+    import numpy as np
+    import oracle
+    from paper_1012_2865_gb300 import synth
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_step_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=300) for _ in range(world)), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    g = synth.clumpy(N=16, nsrc=6, seed=41)
+    x, z = np.asarray(g["x_HI"], dtype=np.float64), np.asarray(g["x_HII"], dtype=np.float64)
+    for step in range(2):
+        full = oracle.trace(g["dims"], g["box_len_cm"], g["n_H"], x, g["pos_cm"], g["ndot"], g["e_ph_eV"],
+                            g["sigma_cm2"], **synth.DEFAULT_PARAMS)
+        x, z = oracle.chem(g["n_H"], x, z, full["kph"], 0.5 * synth.MYR_S, 10, synth.ALPHA_B)
+        for _, steps in out:
+            b, k, xr = steps[step]
+            np.testing.assert_array_equal(b["counts"], full["counts"])
+            np.testing.assert_array_equal(b["hashes"], full["hashes"])
+            assert b["segments"] == full["segments"]
+            for j, key in enumerate(("emitted", "absorbed", "escaped")):
+                assert abs(b[key] - full["budget"][j]) <= 1e-12 * full["budget"][0]
+            np.testing.assert_allclose(k, full["kph"], rtol=1e-12, atol=1e-300)
+            np.testing.assert_allclose(xr, x, rtol=1e-12, atol=1e-15)
