@@ -41,10 +41,16 @@ class Request:
     kph: np.ndarray = None
     segments: int = 0
     meta: dict = field(default_factory=dict)
+    factory: object = None    # builds `grid` at admission when it is None (a long stream)
+    cells_hint: int = 0       # cells of that grid, for admission before it exists
 
     @property
     def latency(self) -> float:
         return self.finished - self.arrival
+
+    @property
+    def cells(self) -> int:
+        return int(np.prod(self.grid["dims"])) if self.grid is not None else int(self.cells_hint)
 
 
 class Server:
@@ -102,7 +108,7 @@ class Server:
         n = 0
         while self.pending and len(self.active) < self.max_slots:
             req = self.pending[0]
-            need = grid_bytes(int(np.prod(req.grid["dims"])), self.precision)
+            need = grid_bytes(req.cells, self.precision)
             if need > self.total_bytes() - self.reserve:
                 self.pending.popleft()
                 req.finished = now
@@ -115,6 +121,8 @@ class Server:
             self.pending.popleft()
             err = getattr(self.backend, "RtError", native.RtError)
             try:
+                if req.grid is None and req.factory is not None:
+                    req.grid = req.factory()
                 req.handle = self.backend.Grid(self.ctx, req.grid, self.precision)
                 req.slot = self.batch.add(req.handle)
             except err as e:
@@ -146,6 +154,8 @@ class Server:
         self.batch.remove(slot)
         req.handle.close()
         req.handle = None
+        if req.factory is not None:
+            req.grid = None  # built on demand: let its medium go
         bucket.append(req)
 
     def _trace_all(self, now_fn):
@@ -228,11 +238,16 @@ class Server:
             self.batch.remove(slot)
             req.handle.close()
             req.handle = None
+            if req.factory is not None:
+                req.grid = None  # built on demand: let its medium go
             self.done.append(req)
         return sum(1 for slot in finished if slot not in self.active)
 
     def run(self, requests: list, time_limit_s: float = None) -> dict:
-        """Serve a stream: request.arrival is in seconds from the start."""
+        """Serve a stream: request.arrival is in seconds from the start.  With
+        `time_limit_s` the loop stops at the first step boundary after it; the
+        report then counts the requests that arrived and are still queued or
+        in progress."""
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
         todo = collections.deque(sorted(requests, key=lambda r: r.arrival))
@@ -249,12 +264,16 @@ class Server:
                 time.sleep(max(0.0, min(todo[0].arrival - now(), 0.01)))
             if time_limit_s is not None and now() > time_limit_s:
                 break
-        return self.report(now())
+        t = now()
+        while todo and todo[0].arrival <= t:
+            self.submit(todo.popleft())
+        return self.report(t, not_arrived=len(todo))
 
-    def report(self, wall_s: float) -> dict:
+    def report(self, wall_s: float, not_arrived: int = 0) -> dict:
         lat = np.array([r.latency for r in self.done]) if self.done else np.array([np.nan])
         return dict(completed=len(self.done), rejected=len(self.rejected), failed=len(self.failed),
-                    cancelled=len(self.cancelled), wall_s=wall_s, steps=self.steps,
+                    cancelled=len(self.cancelled), queued=len(self.pending), in_progress=len(self.active),
+                    not_arrived=not_arrived, wall_s=wall_s, steps=self.steps,
                     segments=self.segments,
                     segments_per_s=self.segments / wall_s if wall_s > 0 else 0.0,
                     p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
@@ -280,7 +299,13 @@ class MediumPool:
         self.side = side
         self.field = synth.lognormal_density(side, seed=seed).reshape(side, side, side)
 
-    def request(self, spec: dict, rid: int) -> Request:
+    def request(self, spec: dict, rid: int, lazy: bool = False) -> Request:
+        """The request of one stream entry; with `lazy` its medium is cut at
+        admission (a long stream then holds only the entries)."""
+        if lazy:
+            N = min(int(spec["N"]), self.side)
+            return Request(rid=rid, grid=None, nsteps=int(spec["nsteps"]), arrival=float(spec["arrival_s"]),
+                           factory=lambda: self.request(spec, rid).grid, cells_hint=N ** 3)
         rng = np.random.default_rng(spec["seed"])
         N = min(int(spec["N"]), self.side)
         o = rng.integers(0, self.side - N + 1, 3)
@@ -305,3 +330,28 @@ def run_alone(ctx, req: Request, precision: str, dt_s: float = 0.5 * synth.MYR_S
     r = grid.rates()
     grid.close()
     return r["x_HI"], r["kph"], segs
+
+
+def serve_one_at_a_time(ctx, requests: list, precision: str, time_limit_s: float = None, **kw) -> dict:
+    """The reference server, live: requests are served in arrival order, one at
+    a time, each on its own grid (run_alone, no batching); a request starts
+    when it has arrived and the previous one has finished, and its latency is
+    its finish time minus its arrival time.  Stops before starting a request
+    once `time_limit_s` has passed."""
+    t0 = time.perf_counter()
+    done = []
+    for r in sorted(requests, key=lambda q: q.arrival):
+        now = time.perf_counter() - t0
+        if time_limit_s is not None and now > time_limit_s:
+            break
+        if r.arrival > now:
+            time.sleep(r.arrival - now)
+        r.admitted = time.perf_counter() - t0
+        r.x_HI, r.kph, r.segments = run_alone(ctx, r, precision, **kw)
+        r.finished = time.perf_counter() - t0
+        done.append(r)
+    lat = np.array([r.latency for r in done]) if done else np.array([np.nan])
+    wall = time.perf_counter() - t0
+    return dict(completed=len(done), wall_s=wall, p50_ms=float(np.percentile(lat, 50) * 1e3),
+                p99_ms=float(np.percentile(lat, 99) * 1e3), service_s=[r.finished - r.admitted for r in done],
+                rids=[r.rid for r in done], latency_ms=[1e3 * r.latency for r in done])

@@ -237,3 +237,30 @@ def test_a_failing_update_fails_every_active_request():
     assert rep["failed"] == 2 and rep["completed"] == 0
     assert all("update" in r.meta["error"] for r in srv.failed)
     assert not FakeGrid.live
+
+
+def test_lazy_requests_and_a_time_limited_stream():
+    """A long stream holds only its entries: a request's grid is built at
+    admission and dropped when it leaves; a run cut at a time limit reports
+    what arrived and is still queued or in progress."""
+    FakeBatch.step_s = 0.003
+    built = []
+
+    def lazy(rid, N, nsteps, arrival):
+        def make():
+            built.append(rid)
+            return {"dims": (N, N, N), "poison": False}
+        return serve.Request(rid=rid, grid=None, nsteps=nsteps, arrival=arrival, factory=make, cells_hint=N ** 3)
+
+    one = serve.grid_bytes(16 ** 3, "fp32_mixed")
+    reqs = [lazy(i, 16, nsteps=4, arrival=0.002 * i) for i in range(40)] + [lazy(99, 16, 1, arrival=10.0)]
+    srv = _server(total_bytes=3 * one, reserve=0, max_slots=8)
+    rep = srv.run(reqs, time_limit_s=0.1)
+    FakeBatch.step_s = 0.0
+    assert rep["not_arrived"] == 1 and 99 not in built
+    assert rep["completed"] + rep["queued"] + rep["in_progress"] == 40
+    assert rep["completed"] > 0 and rep["queued"] > 0 and rep["in_progress"] <= 3
+    assert sorted(built) == sorted([r.rid for r in srv.done] + [r.rid for r in srv.active.values()])
+    assert all(r.grid is None for r in srv.done)
+    assert max(srv.batch.sizes) <= 3  # memory for three grids
+    srv.close()
