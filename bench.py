@@ -171,7 +171,20 @@ def _peaks():
 REC_BYTES = {"fp64": 48, "fp32_mixed": 48}
 
 
-def trace_roofline(precision, segments, pushed, kernel_ms, gamma, red_peak, peaks, peak_kind, traffic, red_words):
+def red_peak(native, device: int, precision: str, cells: int):
+    """Reductions per second the probe measures (rt_probe_red): into a 64 MB
+    array, which stays in L2 -- the roof of the deposits -- and, as context,
+    into an array of the workload's rate-array size (scattered addresses; the
+    deposits of a ray are spatially coherent, so they can exceed that one)."""
+    dt = native.RT_DTYPE_F64 if precision == "fp64" else native.RT_DTYPE_F32
+    esz = 8 if precision == "fp64" else 4
+    roof_words = (64 << 20) // esz
+    size_words = min(1 << 30, 1 << int(np.ceil(np.log2(max(cells, 1024)))))
+    return native.rt_probe_red(device, dt, roof_words), roof_words, native.rt_probe_red(device, dt, size_words), \
+        size_words
+
+
+def trace_roofline(precision, segments, pushed, kernel_ms, gamma, red, peaks, peak_kind, traffic):
     """Roofline figures of one trace launch.
 
     HBM: algorithmic bytes per launch -- per segment the n_HI read (FP64, or
@@ -180,10 +193,10 @@ def trace_roofline(precision, segments, pushed, kernel_ms, gamma, red_peak, peak
     record one write and one read -- over the kernel's event-timed duration,
     against the measured copy bandwidth.
     L2 reductions: one k_ph reduction per segment (and one Gamma reduction
-    where photons heat) over the same duration, against the reduction rate
-    the probe measured in this run into an array of the rate array's size
-    (the per-package residual deposits and the queue's atomics, a few per
-    cent, are left out, so the fraction is a lower bound)."""
+    where photons heat) over the same duration, against the L2-resident
+    reduction rate the probe measured in this run (`red`, from red_peak; the
+    per-package residual deposits and the queue's atomics, a few per cent,
+    are left out, so the fraction is a lower bound)."""
     red_b = 8 if precision == "fp64" else 4
     nred = 2 if gamma else 1
     alg = segments * (8 + red_b * nred) + pushed * 2 * REC_BYTES[precision]
@@ -193,12 +206,14 @@ def trace_roofline(precision, segments, pushed, kernel_ms, gamma, red_peak, peak
     out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
            "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes": alg, "kernel": "trace_kernel",
            "kernel_ms": kernel_ms}
-    if red_peak:
+    if red:
+        roof, roof_words, at_size, size_words = red
         reds = segments * nred
-        out["l2_red"] = {"reds_per_launch": reds, "achieved": reds / s / 1e9, "peak": red_peak / 1e9,
-                         "unit": "G RED/s", "frac": reds / s / red_peak,
+        out["l2_red"] = {"reds_per_launch": reds, "achieved": reds / s / 1e9, "peak": roof / 1e9,
+                         "unit": "G RED/s", "frac": reds / s / roof,
                          "peak_kind": f"measured in this run (rt_probe_red, {'f64' if red_b == 8 else 'f32'}, "
-                                      f"{red_words} words, scattered addresses)"}
+                                      f"{roof_words} words = 64 MB, L2-resident, scattered addresses)",
+                         "scattered_rate_at_array_size": {"words": size_words, "G_per_s": at_size / 1e9}}
     return out
 
 
@@ -320,8 +335,7 @@ def run_native(args, rank, world, local):
     peaks, peak_kind = _peaks()
     wtag = "clumpy256" if args.workload == "clumpy" else f"stromgren{args.grid}"
     traffic = _profiled_traffic(head, wtag)
-    words = 1 << int(np.ceil(np.log2(int(np.prod(g["dims"])))))
-    red_peak = native.rt_probe_red(local, native.RT_DTYPE_F64 if head == "fp64" else native.RT_DTYPE_F32, words)
+    red = red_peak(native, local, head, int(np.prod(g["dims"])))
     gamma = bool(np.any(np.asarray(g["e_ph_eV"]) > 13.6))
     if args.workload == "clumpy":
         wl = WORKLOAD_CLUMPY
@@ -337,7 +351,7 @@ def run_native(args, rank, world, local):
                    "queue_records_per_step": r["pushed"], "l2": "flushed (512 MB write) between steps",
                    "parallelism": f"replicas x{world}"},
         "roofline": trace_roofline(head, r["seg_per_step"], r["pushed"], 1e3 * kern_s / args.steps, gamma,
-                                   red_peak, peaks, peak_kind, traffic, words),
+                                   red, peaks, peak_kind, traffic),
         "e2e": {"value": ee["value"], "unit": UNIT, "h2d_bytes_per_step": ee["h2d"],
                 "d2h_bytes_per_step": ee["d2h"], "ms_per_step": ee.get("ms_per_step"),
                 "how": "C ABI, pinned host buffers, rt_set_state_async / rt_get_rates_async pipelined "
@@ -545,16 +559,15 @@ def clumpy_leg(args, ctx, stream, flush, precision, peaks, peak_kind, local) -> 
         step_ms.append(e0.elapsed_time(e1))
         kern_ms.append(bb["kernel_ms"])
     grid.close()
-    words = 1 << int(np.ceil(np.log2(int(np.prod(g["dims"])))))
-    red_peak = native.rt_probe_red(local, native.RT_DTYPE_F64 if precision == "fp64" else native.RT_DTYPE_F32, words)
+    red = red_peak(native, local, precision, int(np.prod(g["dims"])))
     t = sum(step_ms) / 1e3
     km = sum(kern_ms) / steps
     return {"workload": WORKLOAD_CLUMPY.replace(" + rt_chem_update (0.5 Myr, 10 substeps)", ""),
             "value": b["segments"] * steps / t, "unit": UNIT, "ms_per_step": 1e3 * t / steps,
             "segments_per_step": b["segments"], "queue_records_per_step": b["queue_pushed"],
             "precision": precision, "gpu_launches": int(launches), "l2": "flushed (512 MB write) between steps",
-            "roofline": trace_roofline(precision, b["segments"], b["queue_pushed"], km, True, red_peak, peaks,
-                                       peak_kind, _profiled_traffic(precision, "clumpy256"), words)}
+            "roofline": trace_roofline(precision, b["segments"], b["queue_pushed"], km, True, red, peaks,
+                                       peak_kind, _profiled_traffic(precision, "clumpy256"))}
 
 
 def photon_types(args, ctx, stream, flush, precision) -> dict:
@@ -668,12 +681,14 @@ def finite_light(args, ctx, stream, flush, precision) -> dict:
             "l2": "flushed (512 MB write) between steps"}
 
 
-def batched(args, ctx, stream, dev, world):
+def batched(args, ctx, stream, dev, world, n_grids=64, tune=True, warm=None):
     """Batched configuration: 64 grids (sides 32-192, 1-256 sources) per launch,
-    autotuned, one coupled step captured as a CUDA graph."""
+    autotuned, one coupled step captured as a CUDA graph.  (n_grids, tune and
+    warm shrink it for a profiler capture: the first n_grids grids of the same
+    draw, 8 segments per queue visit and 2 blocks per SM, `warm` warm-up steps.)"""
     import torch
     from paper_1012_2865_gb300 import native, synth
-    gs = synth.batch(64)
+    gs = synth.batch(64)[:n_grids]
     b = native.Batch(ctx, stream.cuda_stream)
     grids = [native.Grid(ctx, g, "fp32_mixed") for g in gs]
     slots = [b.add(gr) for gr in grids]
@@ -688,14 +703,17 @@ def batched(args, ctx, stream, dev, world):
             native.rt_set_state(gr.h, x)
         torch.cuda.synchronize()
 
-    p = native.rt_batch_autotune(b.h, native.trace_params(**synth.DEFAULT_PARAMS))
+    if tune:
+        p = native.rt_batch_autotune(b.h, native.trace_params(**synth.DEFAULT_PARAMS))
+    else:
+        p = native.trace_params(**dict(synth.DEFAULT_PARAMS, segs_per_iter=8, blocks_per_sm=2))
     tuned = dict(synth.DEFAULT_PARAMS, segs_per_iter=p.segs_per_iter, blocks_per_sm=p.blocks_per_sm)
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, args.warmup) if warm is None else warm):
         restore()
         b.step(1, DT_S, 10, synth.ALPHA_B, **tuned)  # the first call captures the graph
     torch.cuda.synchronize()
     steps = max(3, args.steps // 2)
-    ms, segs, launches = 0.0, 0, 0
+    ms, segs, launches, kms, pushed = 0.0, 0, 0, 0.0, 0
     for _ in range(steps):  # one graph replay per timed step, exact segments per step
         restore()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -707,18 +725,34 @@ def batched(args, ctx, stream, dev, world):
         e1.synchronize()
         launches += native.rt_kernel_launches() - l0
         ms += e0.elapsed_time(e1)
-        segs += sum(b.budget(s)["segments"] for s in slots)
+        buds = [b.budget(s) for s in slots]
+        segs += sum(bb["segments"] for bb in buds)
+        pushed += buds[0]["queue_pushed"]
+    # the trace launch's own duration for the roofline (a graph replay does not
+    # time its events): the same trace enqueued without the graph, after the
+    # timed steps
+    tms = []
+    for _ in range(3):
+        restore()
+        b.trace(sync=True, **tuned)
+        tms.append(b.budget(slots[0])["kernel_ms"])
+    kms = float(np.median(tms)) * steps
     cells = sum(int(np.prod(g["dims"])) for g in gs)
     b.close()
     for gr in grids:
         gr.close()
-    return {"workload": "64 grids, sides from {32,48,64,96,128,192}, 1-256 sources, log-normal medium, "
+    peaks, peak_kind = _peaks()
+    red = red_peak(native, dev.index or 0, "fp32_mixed", cells)
+    return {"workload": f"{n_grids} grids, sides from {{32,48,64,96,128,192}}, 1-256 sources, log-normal medium, "
                         "neutral; one CUDA-graph step = zero + emit + trace + update (0.5 Myr), the neutral "
                         "state restored (untimed) before each step",
             "value": segs * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "segments_per_step": segs // steps, "cells": cells, "gpu_launches": int(launches),
+            "queue_records_per_step": pushed // steps, "trace_ms": kms / steps,
             "autotuned": {"segs_per_iter": p.segs_per_iter, "blocks_per_sm": p.blocks_per_sm},
-            "l2": "inputs larger than L2 (no flush)"}
+            "l2": "inputs larger than L2 (no flush)",
+            "roofline": trace_roofline("fp32_mixed", segs // steps, pushed // steps, kms / steps, True, red,
+                                       peaks, peak_kind, _profiled_traffic("fp32_mixed", f"batch{n_grids}"))}
 
 
 def serving(args, ctx):
@@ -902,6 +936,9 @@ def main():
     ap.add_argument("--no-fsl", action="store_true", help="skip the finite-speed-of-light (Application 5) leg")
     ap.add_argument("--no-types", action="store_true", help="skip the photon-types (Sec. 3.2) leg")
     ap.add_argument("--no-clumpy", action="store_true", help="skip the clumpy 256^3, 1000-source leg")
+    ap.add_argument("--profile-batched", type=int, default=0, metavar="N",
+                    help="run only the batched leg on its first N grids (fixed tuning, one warm-up step), "
+                         "for a profiler capture")
     ap.add_argument("--partition", default="replicas", choices=["replicas", "sources"],
                     help="replicas: one independent problem per rank (default); sources: the clumpy 256^3 grid "
                          "shared by the ranks by sources, one all-reduce per trace")
@@ -917,6 +954,19 @@ def main():
     args = ap.parse_args()
     args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
     rank, world, local = _dist()
+    if args.profile_batched:
+        # a profiler's capture of the batched trace on a smaller batch: the
+        # trace launches are the sizing trace, one warm-up replay, then the
+        # timed replays
+        import torch
+        from paper_1012_2865_gb300 import build, native
+        build.build()
+        torch.cuda.set_device(local)
+        ctx = native.rt_ctx_create(local)
+        stream = torch.cuda.current_stream()
+        print(json.dumps(batched(args, ctx, stream, torch.device("cuda", local), 1, n_grids=args.profile_batched,
+                                 tune=False, warm=1)), flush=True)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:
