@@ -167,8 +167,10 @@ def _peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-# bytes of one queue record (written once, read once) per precision
-REC_BYTES = {"fp64": 48, "fp32_mixed": 48}
+# bytes of one queue record (written once, read once) per precision, for
+# traces without a finite speed of light (FP32-mixed records of FSL traces,
+# which carry the package's age, take 48)
+REC_BYTES = {"fp64": 48, "fp32_mixed": 32}
 
 
 def red_peak(native, device: int, precision: str, cells: int):

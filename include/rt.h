@@ -415,7 +415,7 @@ const char* rt_probe_last_error(void);
  * It runs the same FP32-mixed trace as rt_trace on a grid the caller holds in
  * device memory, and keeps all scratch (package queue, control words, budget
  * sums, source records, a table of pixel directions) in one static device
- * array of about 15 MiB that every device loading the library holds until the
+ * array of about 10 MiB that every device loading the library holds until the
  * process exits.  It calls no cudaMalloc, cudaFree or other allocating
  * routine.  Limits: at most RT_NOALLOC_MAX_SOURCES sources and
  * RT_NOALLOC_MAX_RECORDS queue records per call (a larger trace returns

@@ -19,8 +19,9 @@
 #include "rt_internal.cuh"
 
 namespace rtg {
-cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass, int mode,
-                              unsigned long long in_cap, int pass, int passes, cudaStream_t st);
+cudaError_t launch_trace_init(unsigned long long* ctl, void* queue, size_t queue_bytes, unsigned long long n_roots,
+                              int first_pass, int mode, unsigned long long in_cap, int pass, int passes,
+                              cudaStream_t st);
 cudaError_t trace_occupancy(int precision, int fsl, int block, int* blocks_per_sm);
 cudaError_t launch_trace(int precision, int fsl, const TraceArgs& A, int grid, int block, cudaStream_t st);
 cudaError_t launch_flight_table(const double* old, double* neu, float2* neu32, int n_new, double c_dt,
@@ -596,8 +597,9 @@ static int check_params(const rt_trace_params* p) {
   return RT_OK;
 }
 
-static int ensure_queue(rt_grid* g, unsigned long long cap) {
-  const size_t rec = g->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+// Queue of `cap` records of `rec` bytes (the layout of the next trace: a
+// change of layout reallocates, which clears the tags).
+static int ensure_queue(rt_grid* g, unsigned long long cap, size_t rec) {
   if (g->ts.queue && g->ts.cap >= cap && g->ts.rec_bytes == rec) return RT_OK;
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   if (g->ts.queue) cudaFree(g->ts.queue);
@@ -640,16 +642,18 @@ static void fill_common_args(TraceArgs& A, const rt_trace_params* p) {
 // caller; A.src, A.nsrc, A.src_first and A.n_roots are set here per pass.  Packages in
 // flight (fsl) are shared out over the passes on the device; `mode` and
 // `in_cap` say what the first pass takes over from the previous trace.
-static int launch_passes(TraceArgs A, const SourceDev* src, int nsrc, int passes, int precision, int fsl,
-                         int mode, unsigned long long in_cap, int blocks, cudaEvent_t ev0, cudaEvent_t ev1,
+static int launch_passes(TraceArgs A, size_t queue_bytes, const SourceDev* src, int nsrc, int passes, int precision,
+                         int fsl, int mode, unsigned long long in_cap, int blocks, cudaEvent_t ev0, cudaEvent_t ev1,
                          cudaStream_t st, bool stall = false) {
+  if ((unsigned long long)nsrc >= kMaxQueueSources)
+    return fail(RT_ERR_INVALID_ARG, "trace: %d sources in one launch (at most %u)", nsrc, kMaxQueueSources - 1u);
   if (passes > nsrc) passes = nsrc;
   if (passes < 1) passes = 1;
   for (int i = 0; i < passes; ++i) {
     const int s0 = (int)((long long)nsrc * i / passes);
     const int s1 = (int)((long long)nsrc * (i + 1) / passes);
     const unsigned long long n = (unsigned long long)A.npix0 * (unsigned long long)(s1 - s0);
-    LAUNCH_TRY(launch_trace_init(A.ctl, n, i == 0, mode, in_cap, i, passes, st));
+    LAUNCH_TRY(launch_trace_init(A.ctl, A.queue, queue_bytes, n, i == 0, mode, in_cap, i, passes, st));
     // self-test: one package that never exists keeps the trace from ending,
     // so its bounded waits must run out (RT_TRACE_SELFTEST_STALL)
     if (i == 0 && stall) LAUNCH_TRY(launch_add_word(A.ctl + CTL_OUTSTANDING, 1ULL, st));
@@ -778,7 +782,7 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool 
   CUDA_TRY(cudaMemsetAsync(g->cnt, 0, kCntWords * sizeof(unsigned long long), st));
   const int nsrc = (int)g->src.size();
   if (nsrc == 0) {
-    LAUNCH_TRY(launch_trace_init(g->ts.ctl, 0, 1, FLIGHT_OFF, 0, 0, 1, st));
+    LAUNCH_TRY(launch_trace_init(g->ts.ctl, g->ts.queue, g->ts.cap * g->ts.rec_bytes, 0, 1, FLIGHT_OFF, 0, 0, 1, st));
     drop_flight(g);
     g->traced = false;
     g->ts.passes_run = 0;
@@ -818,8 +822,8 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool 
   CUDA_TRY(trace_occupancy(g->precision, fsl ? 1 : 0, block, &per_sm));
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
-  if ((rc = launch_passes(A, g->src_dev, nsrc, passes, g->precision, fsl ? 1 : 0, mode, in_cap,
-                          per_sm * g->ctx->num_sms, g->ev0, g->ev1, st, (p->flags & RT_TRACE_SELFTEST_STALL) != 0)))
+  if ((rc = launch_passes(A, g->ts.cap * g->ts.rec_bytes, g->src_dev, nsrc, passes, g->precision, fsl ? 1 : 0, mode,
+                          in_cap, per_sm * g->ctx->num_sms, g->ev0, g->ev1, st, (p->flags & RT_TRACE_SELFTEST_STALL) != 0)))
     return rc;
   commit_flight(g, fsl);
   g->traced = true;
@@ -918,13 +922,13 @@ int rt_trace(rt_grid* g, const rt_trace_params* p, rt_budget* out) {
       if (cap > (1ULL << 26)) cap = 1ULL << 26;
     }
   }
-  const size_t rec = g->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+  const bool fsl = p->light_cm > 0;
+  const size_t rec = queue_rec_bytes(g->precision == RT_FP64, fsl);
   const int p_min = p->passes > 1 ? p->passes : 1;
   int passes = automatic && g->ts.passes > p_min ? g->ts.passes : p_min;
   const int nsrc = (int)g->src.size();
-  const bool fsl = p->light_cm > 0;
   for (int attempt = 0;; ++attempt) {
-    if ((rc = ensure_queue(g, cap))) return rc;
+    if ((rc = ensure_queue(g, cap, rec))) return rc;
     if ((rc = enqueue_trace(g, p, passes, attempt > 0))) return rc;
     if (!out) return RT_OK;
     if ((rc = read_budget(g, out))) return rc;
@@ -1544,7 +1548,7 @@ static int batch_enqueue(rt_batch* b, const rt_trace_params* p, int passes) {
   cudaStream_t st = b->stream;
   LAUNCH_TRY(launch_batch_zero(b->inst_dev, ninst, b->precision, b->max_cells, st));  // Step 2
   if (b->nsrc == 0) {
-    LAUNCH_TRY(launch_trace_init(b->ts.ctl, 0, 1, FLIGHT_OFF, 0, 0, 1, st));
+    LAUNCH_TRY(launch_trace_init(b->ts.ctl, b->ts.queue, b->ts.cap * b->ts.rec_bytes, 0, 1, FLIGHT_OFF, 0, 0, 1, st));
     b->traced = false;
     b->ts.passes_run = 0;
     return RT_OK;
@@ -1572,7 +1576,8 @@ static int batch_enqueue(rt_batch* b, const rt_trace_params* p, int passes) {
   CUDA_TRY(trace_occupancy(b->precision, 0, 256, &per_sm));
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
-  if ((rc = launch_passes(A, b->src_dev, b->nsrc, passes, b->precision, 0, FLIGHT_OFF, 0, per_sm * b->ctx->num_sms,
+  if ((rc = launch_passes(A, b->ts.cap * b->ts.rec_bytes, b->src_dev, b->nsrc, passes, b->precision, 0, FLIGHT_OFF, 0,
+                          per_sm * b->ctx->num_sms,
                           b->ev0, b->ev1, st)))
     return rc;
   b->traced = true;
@@ -1581,7 +1586,7 @@ static int batch_enqueue(rt_batch* b, const rt_trace_params* p, int passes) {
 }
 
 static int batch_ensure_queue(rt_batch* b, unsigned long long cap) {
-  const size_t rec = b->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+  const size_t rec = queue_rec_bytes(b->precision == RT_FP64, false);
   if (b->ts.queue && b->ts.cap >= cap && b->ts.rec_bytes == rec) return RT_OK;
   CUDA_TRY(cudaStreamSynchronize(b->stream));
   if (b->ts.queue) cudaFree(b->ts.queue);
@@ -1753,7 +1758,7 @@ int rt_batch_trace(rt_batch* b, const rt_trace_params* p, int sync) {
       if (cap > (1ULL << 26)) cap = 1ULL << 26;
     }
   }
-  const size_t rec = b->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+  const size_t rec = queue_rec_bytes(b->precision == RT_FP64, false);
   const int p_min = p->passes > 1 ? p->passes : 1;
   int passes = automatic && b->ts.passes > p_min ? b->ts.passes : p_min;
   for (int attempt = 0;; ++attempt) {
@@ -1818,7 +1823,7 @@ int rt_batch_step(rt_batch* b, const rt_trace_params* p, double dt_s, int nsub, 
       BatchStatus bs;
       if ((rc = batch_status(b, &bs))) return rc;
       // headroom: the media evolve between replays, and traces grow as they ionise
-      const size_t rec = b->precision == RT_FP64 ? sizeof(Rec64) : sizeof(Rec32);
+      const size_t rec = queue_rec_bytes(b->precision == RT_FP64, false);
       const unsigned long long limit = queue_cap_limit(rec, (size_t)b->ts.cap * b->ts.rec_bytes);
       unsigned long long need = 4 * bs.peak + (1ULL << 20);
       if (need > limit) need = limit;

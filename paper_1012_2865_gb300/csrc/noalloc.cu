@@ -30,8 +30,9 @@
 #include "rt_internal.cuh"
 
 namespace rtg {
-cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass, int mode,
-                              unsigned long long in_cap, int pass, int passes, cudaStream_t st);
+cudaError_t launch_trace_init(unsigned long long* ctl, void* queue, size_t queue_bytes, unsigned long long n_roots,
+                              int first_pass, int mode, unsigned long long in_cap, int pass, int passes,
+                              cudaStream_t st);
 cudaError_t trace_occupancy(int precision, int fsl, int block, int* blocks_per_sm);
 cudaError_t launch_trace(int precision, int fsl, const TraceArgs& A, int grid, int block, cudaStream_t st);
 cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st);
@@ -53,7 +54,8 @@ constexpr size_t kNaInstOff = 1024; // one InstDev
 constexpr size_t kNaSrcOff = 2048;  // RT_NOALLOC_MAX_SOURCES SourceDev
 constexpr size_t kNaTabOff = na_align(kNaSrcOff + (size_t)RT_NOALLOC_MAX_SOURCES * sizeof(SourceDev));
 constexpr size_t kNaQueueOff = na_align(kNaTabOff + kNaTableEntries * 2 * sizeof(float4));
-constexpr size_t kNaBytes = kNaQueueOff + (size_t)RT_NOALLOC_MAX_RECORDS * sizeof(Rec32);
+constexpr size_t kNaQueueBytes = (size_t)RT_NOALLOC_MAX_RECORDS * sizeof(QRec32);
+constexpr size_t kNaBytes = kNaQueueOff + kNaQueueBytes;
 static_assert(CTL_N * 8 <= kNaAccOff && kNaAccOff + kNaAccWords * 8 <= kNaCntOff && kNaCntOff + kCntWords * 8 <= kNaInstOff &&
                   sizeof(InstDev) <= kNaSrcOff - kNaInstOff,
               "scratch layout");
@@ -212,7 +214,8 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
   }
 
   const unsigned long long n_roots = (unsigned long long)npix0 * (unsigned long long)nsrc;
-  if ((e = launch_trace_init(ctl, n_roots, 1, FLIGHT_OFF, 0, 0, 1, st)) != cudaSuccess)
+  if ((e = launch_trace_init(ctl, base + kNaQueueOff, kNaQueueBytes, n_roots, 1, FLIGHT_OFF, 0, 0, 1, st)) !=
+      cudaSuccess)
     return na_fail(RT_ERR_CUDA, "trace init", e);
   if (n_roots > 0) {
     TraceArgs A;

@@ -38,6 +38,7 @@ enum CtlWord {
   CTL_SET_BADX = 59,
   CTL_CHECK_N = 60,      // scratch of the state check: first bad n_H cell, x_HI cell
   CTL_CHECK_X = 61,
+  CTL_INIT_DONE = 62,    // blocks of the queue reset that have finished (reset to 0 by the last)
   CTL_N = 64             // words (512 bytes)
 };
 
@@ -122,8 +123,31 @@ struct __align__(16) Rec32 {
   uint32_t cell;  // in flight: the cell index
   uint32_t pad;
 };
+// Queue record of the FP32-mixed walker when packages do not outlive the
+// trace (no finite speed of light): one 32-byte sector.  The level rides in
+// the top 4 bits of the source index, and the tag word holds the low 16 bits
+// of the trace epoch above the error bound tau_err rounded up to bf16 (a
+// wider bound only sends more decisions to FP64).  Epochs whose low 16 bits
+// are 0 are never used, and the queue is cleared before the epoch that would
+// repeat them (trace_init_kernel), so zeroed or stale slots never match.
+struct __align__(32) QRec32 {
+  float r, r_lo, P, tau;
+  float tau_lo;
+  uint32_t src_lv;  // src | level << 28
+  uint32_t pix;
+  uint32_t tag;     // (epoch & 0xffff) << 16 | bf16(tau_err)
+};
+constexpr unsigned long long kEpochMask = 0xffffULL;
+constexpr uint32_t kMaxQueueSources = 1u << 28;  // source indices of QRec32
 static_assert(sizeof(Rec64) == 48, "record layout");
 static_assert(sizeof(Rec32) == 48, "record layout");
+static_assert(sizeof(QRec32) == 32, "record layout");
+static_assert(RT_MAX_LEVEL < 16, "the level takes 4 bits of a queue record");
+
+// Bytes of one queue record of a trace.
+inline size_t queue_rec_bytes(int fp64, bool fsl) {
+  return fp64 ? sizeof(Rec64) : fsl ? sizeof(Rec32) : sizeof(QRec32);
+}
 
 struct TraceArgs {
   const InstDev* inst;

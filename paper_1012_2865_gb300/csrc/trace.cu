@@ -28,6 +28,7 @@
 // test comes first, and the package is appended to an output store with its
 // cell.  The next trace's tickets n_roots .. n_roots + n_res - 1 name the
 // stored packages, which continue from their cells.
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -146,6 +147,7 @@ __device__ __forceinline__ double next_t64(int c, double s, double n) {
 
 struct Walk64 {
   using Rec = Rec64;
+  template <bool FSL> using Q = Rec64;  // queue record
   uint32_t src, level, pix;
   uint32_t age;   // traces since emission (finite speed of light)
   double r, P, tau, Pstart;
@@ -457,7 +459,8 @@ __device__ __noinline__ int decide64(const TraceArgs& A, uint32_t src, int level
 }
 
 struct Walk32 {
-  using Rec = Rec32;
+  using Rec = Rec32;  // packages in flight between traces; records of FSL traces
+  template <bool FSL> using Q = typename std::conditional<FSL, Rec32, QRec32>::type;  // queue record
   uint32_t src, pix;
   uint32_t age;         // traces since emission (finite speed of light)
   F2 rlim;              // halting radius of this age
@@ -604,27 +607,48 @@ struct Walk32 {
         make_uint4(__float_as_uint(tau_lo), __float_as_uint(tau_err), src, pix);
     reinterpret_cast<uint4*>(&q->tag)[0] = make_uint4((uint32_t)lvl(), age + 1, (uint32_t)cell_index(), 0u);
   }
-  // Publish a record in the global queue: payload first, then the tag
-  // ((epoch << 4) | level) with release semantics.
+  // Publish a record in the global queue: payload first, then the tag with
+  // release semantics.  FSL records (48 B) carry the age and the tag
+  // ((epoch << 4) | level); the others (32 B) the level beside the source
+  // index and the tag ((epoch & 0xffff) << 16 | tau_err as bf16 rounded up).
   template <bool FSL>
-  __device__ __forceinline__ static void publish(Rec* q, const Rec& c, uint32_t epoch) {
+  __device__ __forceinline__ static void publish(Q<FSL>* q, const Rec& c, uint32_t epoch) {
     __stcg(reinterpret_cast<float4*>(&q->r), make_float4(c.r, c.r_lo, c.P, c.tau));
-    __stcg(reinterpret_cast<uint4*>(&q->tau_lo),
-           make_uint4(__float_as_uint(c.tau_lo), __float_as_uint(c.tau_err), c.src, c.pix));
-    if (FSL) __stcg(&q->age, c.age);
-    st_release_u32(&q->tag, (epoch << 4) | (c.tag & 15u));
+    if constexpr (FSL) {
+      __stcg(reinterpret_cast<uint4*>(&q->tau_lo),
+             make_uint4(__float_as_uint(c.tau_lo), __float_as_uint(c.tau_err), c.src, c.pix));
+      __stcg(&q->age, c.age);
+      st_release_u32(&q->tag, (epoch << 4) | (c.tag & 15u));
+    } else {
+      // tau_err >= 0: adding 0xffff before the shift rounds the magnitude up
+      const uint32_t e16 = (__float_as_uint(c.tau_err) + 0xffffu) >> 16;
+      __stcg(reinterpret_cast<uint2*>(&q->tau_lo), make_uint2(__float_as_uint(c.tau_lo), c.src | ((c.tag & 15u) << 28)));
+      __stcg(&q->pix, c.pix);
+      st_release_u32(&q->tag, (epoch << 16) | e16);
+    }
   }
   // Poll with an acquire load of the tag: the payload reads that follow a
   // successful poll are ordered after it without a fence.
   template <bool FSL>
-  __device__ __forceinline__ static bool poll(const Rec* q, uint32_t epoch, Rec& o) {
+  __device__ __forceinline__ static bool poll(const Q<FSL>* q, uint32_t epoch, Rec& o) {
     const uint32_t tg = ld_acquire_u32(&q->tag);
-    if ((tg >> 4) != (epoch & 0x0fffffffu)) return false;
+    if constexpr (FSL) {
+      if ((tg >> 4) != (epoch & 0x0fffffffu)) return false;
+    } else {
+      if ((tg >> 16) != (epoch & (uint32_t)kEpochMask)) return false;
+    }
     const float4 a = __ldcg(reinterpret_cast<const float4*>(&q->r));
     const uint4 b = __ldcg(reinterpret_cast<const uint4*>(&q->tau_lo));
     o.r = a.x; o.r_lo = a.y; o.P = a.z; o.tau = a.w;
-    o.tau_lo = __uint_as_float(b.x); o.tau_err = __uint_as_float(b.y); o.src = b.z; o.pix = b.w; o.tag = tg;
-    o.age = FSL ? __ldcg(&q->age) : 0u;
+    o.tau_lo = __uint_as_float(b.x);
+    if constexpr (FSL) {
+      o.tau_err = __uint_as_float(b.y); o.src = b.z; o.pix = b.w; o.tag = tg;
+      o.age = __ldcg(&q->age);
+    } else {
+      o.src = b.y & (kMaxQueueSources - 1u); o.tag = b.y >> 28; o.pix = b.z;
+      o.tau_err = __uint_as_float(tg << 16);
+      o.age = 0u;
+    }
     return true;
   }
   __device__ __forceinline__ static Rec root_rec(uint32_t gsrc, uint32_t l, uint32_t p) {
@@ -879,7 +903,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const uint32_t epoch = (uint32_t)A.ctl[CTL_EPOCH];
-  Rec* queue = (Rec*)A.queue;
+  using QR = typename W::template Q<FSL>;
+  QR* queue = (QR*)A.queue;
   // tickets: roots [0, n_roots), packages in flight [n_roots, qbase), queue slots after
   unsigned long long res_a = 0, n_res = 0;
   if (FSL) {
@@ -1109,6 +1134,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   }
 }
 
+constexpr int kInitBlocks = 128;  // blocks of trace_init_kernel (they clear the queue at an epoch wrap)
+
 // Resets the queue for pass `pass` of `passes`.  A trace may run as several
 // passes over ranges of its sources; the status of earlier passes stays (the
 // first error wins) and their queue use is folded into CTL_PEAK / CTL_PUSHED.
@@ -1116,39 +1143,72 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
 // FLIGHT_ADVANCE takes what the previous trace halted (at most in_cap
 // records were stored) as this trace's input; every pass continues an equal
 // share of them.
-__global__ void trace_init_kernel(unsigned long long* ctl, unsigned long long n_roots, int first_pass, int mode,
-                                  unsigned long long in_cap, int pass, int passes) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    if (first_pass) {
-      // a state rejected by an asynchronous upload stays reported until the
-      // host has read it
-      ctl[CTL_STATUS] = ctl[CTL_SET_ERR];
-      ctl[CTL_PEAK] = 0;
-      ctl[CTL_PUSHED] = 0;
-      if (mode == FLIGHT_OFF) ctl[CTL_RESUME] = 0;
-      else if (mode == FLIGHT_ADVANCE) ctl[CTL_RESUME] = ctl[CTL_HALTED] < in_cap ? ctl[CTL_HALTED] : in_cap;
-      ctl[CTL_HALTED] = 0;
-    } else {
-      const unsigned long long t = ctl[CTL_TAIL];
-      if (t > ctl[CTL_PEAK]) ctl[CTL_PEAK] = t;
-      ctl[CTL_PUSHED] += t;
-    }
-    const unsigned long long nr = ctl[CTL_RESUME];
-    const unsigned long long a = nr * (unsigned long long)pass / (unsigned long long)passes;
-    const unsigned long long b = nr * (unsigned long long)(pass + 1) / (unsigned long long)passes;
-    ctl[CTL_RES_A] = a;
-    ctl[CTL_RES_B] = b;
-    ctl[CTL_HEAD] = 0;
-    ctl[CTL_TAIL] = 0;
-    ctl[CTL_OUTSTANDING] = n_roots + (b - a);
-    ctl[CTL_EPOCH] = ctl[CTL_EPOCH] + 1;
+//
+// Every pass takes the next epoch, and queue records carry its low 16 bits
+// (QRec32).  Before an epoch whose low 16 bits would be 0 the launch clears
+// the queue (all blocks, grid-stride) and takes the epoch after it: a record
+// left in a slot that no trace has written for 2^16 - 1 epochs cannot then
+// pass for a current one, and zeroed memory never does.  Every block reads
+// the old epoch before it counts itself done in CTL_INIT_DONE; the block that
+// counts last writes the control words (no block waits on another).
+__global__ void trace_init_kernel(unsigned long long* ctl, uint4* queue, unsigned long long queue_u4,
+                                  unsigned long long n_roots, int first_pass, int mode, unsigned long long in_cap,
+                                  int pass, int passes) {
+  __shared__ unsigned long long s_epoch;
+  __shared__ int s_last;
+  if (threadIdx.x == 0) s_epoch = *(volatile unsigned long long*)&ctl[CTL_EPOCH];
+  __syncthreads();
+  const unsigned long long old = s_epoch;
+  const bool wrap = ((old + 1) & kEpochMask) == 0;
+  if (wrap && queue) {
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < queue_u4;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+      queue[i] = z;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctl[CTL_INIT_DONE], 1ULL) == (unsigned long long)gridDim.x - 1ULL;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0 || !s_last) return;
+  __threadfence();
+  ctl[CTL_INIT_DONE] = 0;
+  if (first_pass) {
+    // a state rejected by an asynchronous upload stays reported until the
+    // host has read it
+    ctl[CTL_STATUS] = ctl[CTL_SET_ERR];
+    ctl[CTL_PEAK] = 0;
+    ctl[CTL_PUSHED] = 0;
+    if (mode == FLIGHT_OFF) ctl[CTL_RESUME] = 0;
+    else if (mode == FLIGHT_ADVANCE) ctl[CTL_RESUME] = ctl[CTL_HALTED] < in_cap ? ctl[CTL_HALTED] : in_cap;
+    ctl[CTL_HALTED] = 0;
+  } else {
+    const unsigned long long t = ctl[CTL_TAIL];
+    if (t > ctl[CTL_PEAK]) ctl[CTL_PEAK] = t;
+    ctl[CTL_PUSHED] += t;
+  }
+  const unsigned long long nr = ctl[CTL_RESUME];
+  const unsigned long long a = nr * (unsigned long long)pass / (unsigned long long)passes;
+  const unsigned long long b = nr * (unsigned long long)(pass + 1) / (unsigned long long)passes;
+  ctl[CTL_RES_A] = a;
+  ctl[CTL_RES_B] = b;
+  ctl[CTL_HEAD] = 0;
+  ctl[CTL_TAIL] = 0;
+  ctl[CTL_OUTSTANDING] = n_roots + (b - a);
+  ctl[CTL_EPOCH] = old + (wrap ? 2ULL : 1ULL);
 }
 
-// Host-side launch helpers (called from api.cu).
-cudaError_t launch_trace_init(unsigned long long* ctl, unsigned long long n_roots, int first_pass, int mode,
-                              unsigned long long in_cap, int pass, int passes, cudaStream_t st) {
-  trace_init_kernel<<<1, 32, 0, st>>>(ctl, n_roots, first_pass, mode, in_cap, pass, passes);
+// Host-side launch helpers (called from api.cu).  `queue` / `queue_bytes`:
+// the whole queue allocation (a multiple of 16 bytes), cleared when the epoch
+// wraps.
+cudaError_t launch_trace_init(unsigned long long* ctl, void* queue, size_t queue_bytes, unsigned long long n_roots,
+                              int first_pass, int mode, unsigned long long in_cap, int pass, int passes,
+                              cudaStream_t st) {
+  if (queue_bytes % 16 != 0 || ((uintptr_t)queue & 15u) != 0) return cudaErrorInvalidValue;
+  trace_init_kernel<<<kInitBlocks, 256, 0, st>>>(ctl, (uint4*)queue, queue_bytes / 16, n_roots, first_pass, mode,
+                                                in_cap, pass, passes);
   return cudaGetLastError();
 }
 
