@@ -32,39 +32,60 @@ __device__ __forceinline__ bool is_neutral(double x, double z) {
 
 // One cell, FP32-mixed path: FP32 solution + one double-float Newton
 // correction per substep (see chem_mixed_kernel).  x, z and n arrive and
-// leave in FP64; in between they are carried as double-float pairs.  ha and
-// h2 are h alpha_B and h as pairs.  Returns n_HI = n_H x_HI as a pair.
+// leave in FP64 (converted through their bit fields, off the FP64 pipe); in
+// between, the smaller of the two fractions is carried as a double-float
+// pair s and the larger only as its FP32 complement until a substep needs it
+// as a pair.  ha and h2 are h alpha_B and h as pairs.  Returns
+// n_HI = n_H x_HI as a pair.
 __device__ __forceinline__ F2 chem_cell_mixed(double& x, double& z, double n, float kc, F2 ha, F2 h2, int nsub) {
-  const F2 n2 = f2_from_double(n);
+  const F2 n2 = f2_from_double_bits(n);
   const F2 a = f2_mul(ha, n2);
   const F2 hk = f2_mul_f(h2, kc);
   const F2 one = {1.0f, 0.0f};
   const F2 b = f2_add(one, hk);
   const F2 two_a_b = f2_add(F2{2.0f * a.hi, 2.0f * a.lo}, b);
   const float af = a.hi, bf = b.hi, hkf = hk.hi;
-  F2 xp = f2_from_double(x), zp = f2_from_double(z);
+  const F2 x0 = f2_from_double_bits(x), z0 = f2_from_double_bits(z);
+  float xf = x0.hi, zf = z0.hi;
+  bool sx = xf < 0.5f;  // s holds x_HI (else x_HII)
+  F2 s = sx ? x0 : z0;
   for (int i = 0; i < nsub; ++i) {
-    const float xf = xp.hi, zf = zp.hi;
     const float wf = zf + hkf;
-    const float sq = sqrtf(fmaf(4.0f * af, wf, bf * bf));
+    // the FP32 guess needs only ~1e-7: approximate square root and quotient
+    // (D >= 1 and both denominators >= 2); the correction's quotient is exact
+    const float D = fmaf(4.0f * af, wf, bf * bf);
+    const float sq = D * rsqrtf(D);
     if (xf < 0.5f) {
-      const float xg = 2.0f * (af + xf) / (2.0f * af + bf + sq);
+      if (!sx) {
+        s = f2_sub(one, s);
+        sx = true;
+      }
+      const float xg = __fdividef(2.0f * (af + xf), 2.0f * af + bf + sq);
       const F2 t = f2_mul_f(f2_sub(f2_mul_f(a, xg), two_a_b), xg);
-      const float g = f2_to_float(f2_add(t, f2_add(a, xp)));
+      const float g = f2_sum_float(t, f2_add(a, s));
       const float gp = fmaf(2.0f * af, xg, -(2.0f * af + bf));
-      xp = two_sum(xg, -__fdiv_rn(g, gp));
-      zp = f2_sub(one, xp);
+      s = two_sum(xg, -__fdiv_rn(g, gp));
+      xf = s.hi;
+      zf = 1.0f - xf;
     } else {
-      const float zg = 2.0f * wf / (bf + sq);
+      if (sx) {
+        s = f2_sub(one, s);
+        sx = false;
+      }
+      const float zg = __fdividef(2.0f * wf, bf + sq);
       const F2 t = f2_mul_f(f2_add(f2_mul_f(a, zg), b), zg);
-      const float f = f2_to_float(f2_sub(t, f2_add(zp, hk)));
+      const F2 c = f2_add(s, hk);
+      const float f = f2_sum_float(t, F2{-c.hi, -c.lo});
       const float fp = fmaf(2.0f * af, zg, bf);
-      zp = two_sum(zg, -__fdiv_rn(f, fp));
-      xp = f2_sub(one, zp);
+      s = two_sum(zg, -__fdiv_rn(f, fp));
+      zf = s.hi;
+      xf = 1.0f - zf;
     }
   }
-  x = f2_to_double(xp);
-  z = f2_to_double(zp);
+  const F2 xp = sx ? s : f2_sub(one, s);
+  const F2 zp = sx ? f2_sub(one, s) : s;
+  x = f2_to_double_bits(xp);
+  z = f2_to_double_bits(zp);
   return f2_mul(n2, xp);
 }
 
@@ -103,8 +124,11 @@ __global__ void chem_kernel(long long ncell, const double* __restrict__ nH, doub
 //   z-form: f(z') = a z'^2 + b z' - (z + hk),         f' = 2a z' + b.
 // From a ~1e-7 relative guess one Newton step leaves ~1e-14 (the residual's
 // double-float rounding, ~2^-48 of its largest term), so the carried state
-// stays within ~1e-14 of the FP64 recursion while the substeps run on the
-// FP32 pipe; FP64 is used only to load and store the state.
+// stays within ~1e-13 of the FP64 recursion while the substeps run on the
+// FP32 pipe.  FP64 arithmetic is left only in one addition per stored
+// fraction: the state's conversions to and from pairs move bit fields
+// (f2.cuh), since the FP64 pipe, a small fraction of the FP32 one, otherwise
+// bounds the kernel.
 __global__ void chem_mixed_kernel(long long ncell, const double* __restrict__ nH, double* __restrict__ xHI,
                                   double* __restrict__ xHII, const float* __restrict__ K,
                                   float2* __restrict__ nhi, float4 hh, int nsub) {

@@ -65,6 +65,59 @@ __device__ __forceinline__ F2 f2_from_double(double v) {
   return {hi, __double2float_rn(__dsub_rn(v, (double)hi))};
 }
 __device__ __forceinline__ double f2_to_double(F2 a) { return __dadd_rn((double)a.hi, (double)a.lo); }
+
+// The same two conversions with the format changes done in integer
+// arithmetic (IEEE-754 binary64 / binary32 fields), for kernels where the
+// FP64 pipe, a small fraction of the FP32 one, would otherwise bound them.
+//
+// Nearest pair to v: hi = v rounded to 24 bits (ties to even) by adding the
+// rounding bias to the binary64 pattern (a carry moves into the exponent as
+// it should); v - hi is then the difference of the two patterns, an integer
+// of at most 2^28 units of v's last place, and lo its FP32 rounding.  Equal
+// to f2_from_double for zeros and 2^-74 <= |v| < 2^125, which it handles
+// this way (hi and lo stay normal FP32 numbers); other values take
+// f2_from_double.
+// The rare operands of these conversions go through functions that are
+// never inlined, so the compiler cannot predicate their FP64 instructions
+// into the common path.
+static __device__ __noinline__ F2 f2_from_double_call(double v) { return f2_from_double(v); }
+static __device__ __noinline__ double f32_widen_call(float f) { return (double)f; }
+__device__ __forceinline__ F2 f2_from_double_bits(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned uh = (unsigned)(u >> 32);
+  const unsigned long long mag = u & 0x7fffffffffffffffULL;
+  if (mag == 0ULL) return {__uint_as_float(uh & 0x80000000u), 0.0f};  // signed zero
+  const int e = (int)((uh >> 20) & 0x7ffu);  // biased binary64 exponent
+  if (e < 949 || e > 1147) return f2_from_double_call(v);
+  const unsigned long long r = (mag + 0x0fffffffULL + ((mag >> 29) & 1ULL)) & ~0x1fffffffULL;
+  const long long d = (long long)(mag - r);  // |v| - |hi|, units of 2^(e - 1075)
+  const unsigned rh = (unsigned)(r >> 32), rl = (unsigned)r;
+  const unsigned sign = uh & 0x80000000u;
+  const unsigned hb = sign | ((((rh >> 20) & 0x7ffu) - 896u) << 23) | ((rh & 0xfffffu) << 3) | (rl >> 29);
+  const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
+  const float lo = __fmul_rn(__int2float_rn((int)d), scale);  // |d| <= 2^28
+  return {__uint_as_float(hb), sign ? -lo : lo};
+}
+// An FP32 number widened to binary64 exactly by moving its fields (normal
+// numbers and zeros; others take the conversion instruction).
+__device__ __forceinline__ double f32_widen_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ex = (b >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) {
+    if ((b << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)b << 32));
+    return f32_widen_call(f);
+  }
+  const unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+// hi + lo rounded to binary64 with one FP64 addition.
+__device__ __forceinline__ double f2_to_double_bits(F2 a) { return __dadd_rn(f32_widen_bits(a.hi), f32_widen_bits(a.lo)); }
 __device__ __forceinline__ float f2_to_float(F2 a) { return __fadd_rn(a.hi, a.lo); }
+// a + b rounded to FP32: f2_to_float(f2_add(a, b)) without the final
+// renormalisation (the same value)
+__device__ __forceinline__ float f2_sum_float(F2 a, F2 b) {
+  const F2 s = two_sum(a.hi, b.hi);
+  return __fadd_rn(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
 
 }  // namespace rtg
