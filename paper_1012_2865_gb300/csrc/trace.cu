@@ -57,7 +57,11 @@ struct LaneAcc {
   unsigned long long segments;
   unsigned int fallbacks, fallbacks_tau;
   int inst;
+  // 72 bytes = 18 banks: the 8-byte accesses of a half-warp to one field
+  // fall on 16 different bank pairs (a 64-byte stride puts them on two)
+  unsigned int pad[3];
 };
+static_assert(sizeof(LaneAcc) == 72, "conflict-free stride of the per-lane sums");
 
 // A block's budget sums per grid, in shared memory, for the first kShInst
 // grids of the launch: a lane that moves to a package of another grid adds
