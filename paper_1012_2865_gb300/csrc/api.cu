@@ -229,6 +229,7 @@ struct rt_grid {
   double* up_stage = nullptr;                // 3 * ncell doubles: n_H, x_HI, x_HII
   char* dn_stage = nullptr;                  // 3 * ncell * 8 bytes: k_ph, Gamma, x_HI
   std::string set_err;                       // message of a rejected asynchronous state
+  bool check_words_set = false;              // CTL_CHECK_N/X hold ~0 (then kept so by each commit)
   ~rt_grid() {
     if (up) cudaStreamSynchronize(up);
     if (dn) cudaStreamSynchronize(dn);
@@ -1030,6 +1031,11 @@ static int ensure_async(rt_grid* g, bool stage_up, bool stage_dn) {
   const size_t n8 = (size_t)g->ncell * 8;
   if (stage_up && !g->up_stage) CUDA_TRY(cudaMalloc((void**)&g->up_stage, 3 * n8));
   if (stage_dn && !g->dn_stage) CUDA_TRY(cudaMalloc((void**)&g->dn_stage, 3 * n8));
+  if (!g->check_words_set) {
+    // ~0 = no failing cell; every commit leaves them so for the next upload
+    CUDA_TRY(cudaMemsetAsync(g->ts.ctl + CTL_CHECK_N, 0xff, 2 * sizeof(unsigned long long), g->stream));
+    g->check_words_set = true;
+  }
   return RT_OK;
 }
 
@@ -1061,10 +1067,21 @@ int rt_set_state_async(rt_grid* g, const double* n_H, const double* x_HI, const 
     sx = d + n;
     sz = x_HII ? d + 2 * n : nullptr;
   }
-  CUDA_TRY(cudaMemsetAsync(g->ts.ctl + CTL_CHECK_N, 0xff, 2 * sizeof(unsigned long long), st));
   LAUNCH_TRY(launch_check_state(n, sn, sx, g->ts.ctl + CTL_CHECK_N, st));
   LAUNCH_TRY(launch_commit_state(g->precision, n, g->ts.ctl, sn, sx, sz, g->nH, g->xHI, g->xHII, g->nhi, st));
   CUDA_TRY(cudaEventRecord(g->ev_commit, st));
+  return RT_OK;
+}
+
+// One field into a snapshot or a caller's device buffer: a device-to-device
+// copy when neither the element type nor the scale changes, else the
+// conversion kernel.
+static int copy_or_convert(long long n, const void* src, int sdt, void* dst, int ddt, double scale, cudaStream_t st) {
+  if (sdt == ddt && scale == 1.0) {
+    CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)n * (sdt == RT_DTYPE_F64 ? 8 : 4), cudaMemcpyDeviceToDevice, st));
+    return RT_OK;
+  }
+  LAUNCH_TRY(launch_convert(n, src, sdt, dst, ddt, st, scale));
   return RT_OK;
 }
 
@@ -1086,7 +1103,10 @@ int rt_get_rates_async(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype
   cudaStream_t st = g->stream;
   if (mem_kind == RT_MEM_DEVICE) {
     for (int f = 0; f < 3; ++f)
-      if (dst[f]) LAUNCH_TRY(launch_convert(n, src[f], sdt[f], dst[f], dtype, st, scale[f]));
+      if (dst[f]) {
+        int rc = copy_or_convert(n, src[f], sdt[f], dst[f], dtype, scale[f], st);
+        if (rc) return rc;
+      }
     return RT_OK;
   }
   int rc = ensure_async(g, false, true);
@@ -1096,7 +1116,7 @@ int rt_get_rates_async(rt_grid* g, void* kph, void* gamma, void* x_HI, int dtype
   for (int f = 0; f < 3; ++f) {
     if (!dst[f]) continue;
     CUDA_TRY(cudaStreamWaitEvent(st, g->ev_dl[f], 0));
-    LAUNCH_TRY(launch_convert(n, src[f], sdt[f], g->dn_stage + f * region, dtype, st, scale[f]));
+    if ((rc = copy_or_convert(n, src[f], sdt[f], g->dn_stage + f * region, dtype, scale[f], st))) return rc;
   }
   CUDA_TRY(cudaEventRecord(g->ev_snap, st));
   CUDA_TRY(cudaStreamWaitEvent(g->dn, g->ev_snap, 0));

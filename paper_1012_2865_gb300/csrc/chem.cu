@@ -209,6 +209,22 @@ __global__ void check_state_kernel(long long n, const double* __restrict__ nH, c
   }
 }
 
+// The same check two cells at a time (16-byte loads, twice the bytes in
+// flight per thread), for 16-byte aligned arrays of an even length.
+__global__ void check_state2_kernel(long long n2, const double2* __restrict__ nH, const double2* __restrict__ x,
+                                    unsigned long long* __restrict__ bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    if (nH) {
+      const double2 v = nH[i];
+      if (!(v.x >= 0.0) || isinf(v.x)) atomicMin(&bad[0], (unsigned long long)(2 * i));
+      if (!(v.y >= 0.0) || isinf(v.y)) atomicMin(&bad[0], (unsigned long long)(2 * i + 1));
+    }
+    const double2 xv = x[i];
+    if (!(xv.x >= 0.0 && xv.x <= 1.0)) atomicMin(&bad[1], (unsigned long long)(2 * i));
+    if (!(xv.y >= 0.0 && xv.y <= 1.0)) atomicMin(&bad[1], (unsigned long long)(2 * i + 1));
+  }
+}
+
 // Commit of a gas state uploaded without waiting (rt_set_state_async), run
 // after check_state_kernel has left the first failing cells in
 // ctl[CTL_CHECK_N] and ctl[CTL_CHECK_X] (~0 = none).  When every cell passed,
@@ -217,21 +233,40 @@ __global__ void check_state_kernel(long long n, const double* __restrict__ nH, c
 // refreshed (FP64, or the FP32 pair on the mixed path).  Otherwise nothing
 // changes and the rejection is latched in ctl[CTL_SET_ERR] (the first one
 // keeps its failing cells), where the next trace and rt_synchronize find it.
+// The block that finishes last (CTL_COMMIT_DONE) sets the check words back
+// to ~0 for the next upload, after every block has read them.
+__device__ __forceinline__ bool commit_verdict(unsigned long long* ctl) {
+  const unsigned long long bn = ctl[CTL_CHECK_N], bx = ctl[CTL_CHECK_X];
+  if (bn == ~0ULL && bx == ~0ULL) return true;
+  if (blockIdx.x == 0 && threadIdx.x == 0 &&
+      atomicCAS(&ctl[CTL_SET_ERR], 0ULL, (unsigned long long)RT_ERR_INVALID_ARG) == 0ULL) {
+    ctl[CTL_SET_BADN] = bn;
+    ctl[CTL_SET_BADX] = bx;
+  }
+  return false;
+}
+__device__ __forceinline__ void commit_finish(unsigned long long* ctl) {
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&ctl[CTL_COMMIT_DONE], 1ULL) == (unsigned long long)gridDim.x - 1ULL;
+    if (last) {
+      __threadfence();
+      ctl[CTL_CHECK_N] = ~0ULL;
+      ctl[CTL_CHECK_X] = ~0ULL;
+      ctl[CTL_COMMIT_DONE] = 0ULL;
+    }
+  }
+}
 template <bool PAIR>
 __global__ void commit_state_kernel(long long n, unsigned long long* __restrict__ ctl, const double* __restrict__ sn,
                                     const double* __restrict__ sx, const double* __restrict__ sz,
                                     double* __restrict__ nH, double* __restrict__ xHI, double* __restrict__ xHII,
                                     void* __restrict__ nhi) {
-  const unsigned long long bn = ctl[CTL_CHECK_N], bx = ctl[CTL_CHECK_X];
-  if (bn != ~0ULL || bx != ~0ULL) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 &&
-        atomicCAS(&ctl[CTL_SET_ERR], 0ULL, (unsigned long long)RT_ERR_INVALID_ARG) == 0ULL) {
-      ctl[CTL_SET_BADN] = bn;
-      ctl[CTL_SET_BADX] = bx;
-    }
-    return;
-  }
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+  const bool ok = commit_verdict(ctl);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; ok && c < n;
+       c += (long long)gridDim.x * blockDim.x) {
     const double h = sn ? sn[c] : nH[c];
     if (sn) nH[c] = h;
     const double x = sx[c];
@@ -245,6 +280,33 @@ __global__ void commit_state_kernel(long long n, unsigned long long* __restrict_
       ((double*)nhi)[c] = v;
     }
   }
+  commit_finish(ctl);
+}
+
+// The same commit two cells at a time (16-byte accesses), for 16-byte
+// aligned arrays of an even length.
+template <bool PAIR>
+__global__ void commit_state2_kernel(long long n2, unsigned long long* __restrict__ ctl, const double2* __restrict__ sn,
+                                     const double2* __restrict__ sx, const double2* __restrict__ sz,
+                                     double2* __restrict__ nH, double2* __restrict__ xHI, double2* __restrict__ xHII,
+                                     void* __restrict__ nhi) {
+  const bool ok = commit_verdict(ctl);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; ok && i < n2;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 h = sn ? sn[i] : nH[i];
+    if (sn) nH[i] = h;
+    const double2 x = sx[i];
+    xHI[i] = x;
+    xHII[i] = sz ? sz[i] : make_double2(__dsub_rn(1.0, x.x), __dsub_rn(1.0, x.y));
+    const double v0 = __dmul_rn(h.x, x.x), v1 = __dmul_rn(h.y, x.y);
+    if (PAIR) {
+      const F2 p0 = f2_from_double(v0), p1 = f2_from_double(v1);
+      ((float4*)nhi)[i] = make_float4(p0.hi, p0.lo, p1.hi, p1.lo);
+    } else {
+      ((double2*)nhi)[i] = make_double2(v0, v1);
+    }
+  }
+  commit_finish(ctl);
 }
 
 // Adaptive RT timestep (Sec. 3.4), step 1, Eq. "dtelec": per cell
@@ -376,17 +438,37 @@ cudaError_t launch_add_word(unsigned long long* w, unsigned long long delta, cud
   return cudaGetLastError();
 }
 
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 cudaError_t launch_check_state(long long n, const double* nH, const double* x, unsigned long long* bad,
                                cudaStream_t st) {
-  const int block = 256, grid = grid_for(n, block);
-  check_state_kernel<<<grid, block, 0, st>>>(n, nH, x, bad);
+  const int block = 256;
+  if (n % 2 == 0 && aligned16(nH) && aligned16(x))
+    check_state2_kernel<<<grid_for(n / 2, block), block, 0, st>>>(n / 2, (const double2*)nH, (const double2*)x, bad);
+  else
+    check_state_kernel<<<grid_for(n, block), block, 0, st>>>(n, nH, x, bad);
   return cudaGetLastError();
 }
 
 cudaError_t launch_commit_state(int precision, long long n, unsigned long long* ctl, const double* sn,
                                const double* sx, const double* sz, double* nH, double* xHI, double* xHII, void* nhi,
                                cudaStream_t st) {
-  const int block = 256, grid = grid_for(n, block);
+  const int block = 256;
+  if (n % 2 == 0 && aligned16(sn) && aligned16(sx) && aligned16(sz) && aligned16(nH) && aligned16(xHI) &&
+      aligned16(xHII) && aligned16(nhi)) {
+    const long long n2 = n / 2;
+    const int grid = grid_for(n2, block);
+    if (precision == RT_FP64)
+      commit_state2_kernel<false><<<grid, block, 0, st>>>(n2, ctl, (const double2*)sn, (const double2*)sx,
+                                                          (const double2*)sz, (double2*)nH, (double2*)xHI,
+                                                          (double2*)xHII, nhi);
+    else
+      commit_state2_kernel<true><<<grid, block, 0, st>>>(n2, ctl, (const double2*)sn, (const double2*)sx,
+                                                         (const double2*)sz, (double2*)nH, (double2*)xHI,
+                                                         (double2*)xHII, nhi);
+    return cudaGetLastError();
+  }
+  const int grid = grid_for(n, block);
   if (precision == RT_FP64)
     commit_state_kernel<false><<<grid, block, 0, st>>>(n, ctl, sn, sx, sz, nH, xHI, xHII, nhi);
   else

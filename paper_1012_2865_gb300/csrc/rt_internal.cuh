@@ -39,6 +39,7 @@ enum CtlWord {
   CTL_CHECK_N = 60,      // scratch of the state check: first bad n_H cell, x_HI cell
   CTL_CHECK_X = 61,
   CTL_INIT_DONE = 62,    // blocks of the queue reset that have finished (reset to 0 by the last)
+  CTL_COMMIT_DONE = 63,  // blocks of a state commit that have finished (reset to 0 by the last)
   CTL_N = 64             // words (512 bytes)
 };
 

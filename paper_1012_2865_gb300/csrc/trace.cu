@@ -1138,7 +1138,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   }
 }
 
-constexpr int kInitBlocks = 128;  // blocks of trace_init_kernel (they clear the queue at an epoch wrap)
+constexpr int kInitBlocks = 16;  // blocks of trace_init_kernel (they clear the queue at an epoch wrap)
 
 // Resets the queue for pass `pass` of `passes`.  A trace may run as several
 // passes over ranges of its sources; the status of earlier passes stays (the
