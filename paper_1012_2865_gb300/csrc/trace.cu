@@ -52,6 +52,25 @@ constexpr int kAcc = 5;  // budget sums per grid: emitted, absorbed, escaped, re
 
 // Photon budget of one lane for the grid it is working on; lives in shared
 // memory (one slot per thread) and is touched only at package events.
+// Position of the set bit of rank n (0 = lowest) in m; m holds more than n
+// set bits.  A binary search on the population counts of the low halves.
+__device__ __forceinline__ int nth_set_bit(unsigned m, unsigned n) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const unsigned low = m & ((1u << w) - 1u);
+    const unsigned c = (unsigned)__popc(low);
+    if (c <= n) {
+      n -= c;
+      m >>= w;
+      pos += w;
+    } else {
+      m = low;
+    }
+  }
+  return pos;
+}
+
 struct LaneAcc {
   double emitted, absorbed, escaped, resumed, halted;
   unsigned long long segments;
@@ -263,6 +282,15 @@ struct Walk64 {
     o.pix = (uint32_t)(sp >> 32);
     o.level = c.x;
     return true;
+  }
+  // Every lane takes the record that lane `from` holds (all lanes call it).
+  __device__ __forceinline__ static void shfl_rec(Rec& c, int from) {
+    c.r = __shfl_sync(0xffffffffu, c.r, from);
+    c.P = __shfl_sync(0xffffffffu, c.P, from);
+    c.tau = __shfl_sync(0xffffffffu, c.tau, from);
+    c.src = __shfl_sync(0xffffffffu, c.src, from);
+    c.pix = __shfl_sync(0xffffffffu, c.pix, from);
+    c.level = __shfl_sync(0xffffffffu, c.level, from);
   }
   __device__ __forceinline__ static Rec root_rec(uint32_t gsrc, uint32_t lvl0, uint32_t p) {
     Rec c;
@@ -655,6 +683,19 @@ struct Walk32 {
     }
     return true;
   }
+  // Every lane takes the record that lane `from` holds (all lanes call it).
+  __device__ __forceinline__ static void shfl_rec(Rec& c, int from) {
+    c.r = __shfl_sync(0xffffffffu, c.r, from);
+    c.r_lo = __shfl_sync(0xffffffffu, c.r_lo, from);
+    c.P = __shfl_sync(0xffffffffu, c.P, from);
+    c.tau = __shfl_sync(0xffffffffu, c.tau, from);
+    c.tau_lo = __shfl_sync(0xffffffffu, c.tau_lo, from);
+    c.tau_err = __shfl_sync(0xffffffffu, c.tau_err, from);
+    c.src = __shfl_sync(0xffffffffu, c.src, from);
+    c.pix = __shfl_sync(0xffffffffu, c.pix, from);
+    c.tag = __shfl_sync(0xffffffffu, c.tag, from);
+    c.age = __shfl_sync(0xffffffffu, c.age, from);
+  }
   __device__ __forceinline__ static Rec root_rec(uint32_t gsrc, uint32_t l, uint32_t p) {
     Rec c;
     c.r = 0.0f; c.r_lo = 0.0f; c.P = 1.0f; c.tau = 0.0f; c.tau_lo = 0.0f; c.tau_err = 0.0f; c.src = gsrc; c.pix = p;
@@ -1029,15 +1070,25 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         }
       }
     }
-    // (5) splits reserve 3 slots per splitting lane, publish children 1-3 and
-    //     keep child 0; finished packages leave the outstanding count.  One
-    //     atomic per warp carries both: +3 per split, -1 per finished package.
+    // (5) a split keeps child 0 and hands children 1-3 first to lanes of this
+    //     warp that are free (no package and no ticket: in practice the
+    //     lanes whose package ended in this round; a lane holding a ticket
+    //     must stay free to take up the record that the ticket names), the
+    //     rest to the queue (slots reserved together); finished packages
+    //     leave the outstanding count.
+    //     One atomic per warp carries both: +3 per split, -1 per finished
+    //     package.  Child j = 3 i + k - 1 of the i-th splitting lane goes to
+    //     the j-th free lane when there is one, else to slot base + j - nin.
     const bool split = (ev == EV_SPLIT);
     const unsigned sm = __ballot_sync(kFull, split);
     const unsigned dm = __ballot_sync(kFull, ev == EV_DONE);
     if (sm | dm) {
       const int leader = __ffs(sm | dm) - 1;
       const unsigned nsp = __popc(sm);
+      const unsigned fm = __ballot_sync(kFull, !split && (!active || ev == EV_DONE) && ticket < 0);
+      const unsigned nfree = __popc(fm);
+      const unsigned nin = nfree < 3u * nsp ? nfree : 3u * nsp;  // children placed in this warp
+      const unsigned nq = 3u * nsp - nin;                         // children through the queue
       unsigned long long base = 0;
       if (lane == leader) {
         // The count must include the children before any child is published,
@@ -1046,8 +1097,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         const long long delta = 3LL * nsp - (long long)__popc(dm);
         const unsigned long long o = atomicAdd(&A.ctl[CTL_OUTSTANDING], (unsigned long long)delta);
         asm volatile("" ::"l"(o) : "memory");
-        if (nsp) {
-          base = atomicAdd(&A.ctl[CTL_TAIL], 3ULL * nsp);
+        if (nq) {
+          base = atomicAdd(&A.ctl[CTL_TAIL], (unsigned long long)nq);
           __threadfence();
         }
       }
@@ -1056,15 +1107,32 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         active = false;
         ev = EV_NONE;
       }
+      bool fresh = false;  // a package starts in this lane now
+      if (nin) {
+        const unsigned q = __popc(fm & lt_mask);
+        const bool recv = ((fm >> lane) & 1u) && q < nin;
+        Rec c = w.make_child(4u * w.pix);  // in splitting lanes: child 0's record, children differ in pix
+        W::shfl_rec(c, recv ? nth_set_bit(sm, q / 3u) : lane);
+        if (recv) {
+          c.pix += q % 3u + 1u;
+          w.load(c);
+          active = true;
+          fresh = true;
+          acc_switch(acc, w.nseg, w.inst(A), A, BB);
+          if (FSL) w.set_rlim(A);
+        }
+      }
       if (split) {
         w.on_split(A, acc);
-        const unsigned long long my = base + 3ULL * __popc(sm & lt_mask);
+        const unsigned i = __popc(sm & lt_mask);
         const SourceDev& S = A.src[w.src];
         const int cl = w.lvl() + 1;
         LC.add(A, S.inst, S.local, cl, 4u * w.pix, 4);
         unsigned dropped = 0;
         for (uint32_t k = 1; k < 4; ++k) {
-          const unsigned long long slot = my + (k - 1);
+          const unsigned j = 3u * i + (k - 1u);
+          if (j < nin) continue;  // placed in a free lane of this warp
+          const unsigned long long slot = base + (j - nin);
           if (slot < A.cap) W::template publish<FSL>(&queue[slot], w.make_child(4u * w.pix + k), epoch);
           else ++dropped;
         }
@@ -1073,6 +1141,9 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
           atomicAdd(&A.ctl[CTL_OUTSTANDING], (unsigned long long)(-(long long)dropped));
         }
         w.become_child0();
+        fresh = true;
+      }
+      if (fresh) {
         if (w.start(A)) ev = EV_NONE;
         else {
           w.on_start_outside(A, acc);

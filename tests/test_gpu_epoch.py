@@ -49,7 +49,10 @@ def test_epoch_wrap_leaves_no_stale_record():
 
     grid = native.Grid(ctx, a, "fp32_mixed")
     first = grid.trace(**q)
-    assert first["status"] == 0 and first["queue_pushed"] == big["queue_pushed"]
+    # (how many children pass through the queue depends on scheduling: those
+    # placed in a free lane of the splitting warp do not)
+    assert first["status"] == 0 and first["passes"] == 1 and first["queue_pushed"] > 0
+    np.testing.assert_array_equal(first["counts"], big["counts"])
     n = grid.ncell
     native.rt_set_state(grid.h, np.ones(n), np.zeros(n))  # neutral: packages stop within a few cells
     small = dict(q, checksums=False)

@@ -49,7 +49,9 @@ def test_passes_equal_one_launch_and_the_oracle(precision):
     for passes in (3, 12, 50):  # 50 > sources: one pass per source
         b = grid.trace(checksums=True, passes=passes, **synth.DEFAULT_PARAMS)
         assert b["passes"] == min(passes, 12)
-        assert b["queue_pushed"] == b1["queue_pushed"]  # the same packages
+        # the same packages (how many of them pass through the queue depends
+        # on scheduling: children placed in a free lane of the warp do not)
+        np.testing.assert_array_equal(b["counts"], b1["counts"])
         assert b["queue_peak"] < b1["queue_peak"]
         _same(b, grid.rates(), b1, r1, SUM_ORDER_TOL[precision])
     b = grid.trace(checksums=True, passes=3, **synth.DEFAULT_PARAMS)
@@ -62,8 +64,10 @@ def test_a_queue_for_one_pass_suffices():
     grid, b1, r1 = parity.run_gpu(g, "fp32_mixed")
     b4 = grid.trace(checksums=True, passes=4, **synth.DEFAULT_PARAMS)
     grid.close()
-    cap = b4["queue_peak"] + 64
-    assert cap < b1["queue_peak"]
+    # queue use varies a little from run to run (children placed in a free
+    # lane of the splitting warp skip the queue): keep a margin both ways
+    cap = b4["queue_peak"] * 3 // 2 + 64
+    assert cap < b1["queue_peak"] * 3 // 4
     fresh = native.Grid(parity.ctx(), g, "fp32_mixed")  # its queue is allocated at `cap`
     with pytest.raises(native.RtError) as e:  # one launch overflows this queue ...
         fresh.trace(checksums=True, queue_capacity=cap, **synth.DEFAULT_PARAMS)
