@@ -167,6 +167,14 @@ def _peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+def queue_capacity_for(b, level0=1):
+    """Queue records that a repeat of trace `b` can need: every child other
+    than child 0 of every split (how many of them a free lane of the splitting
+    warp takes instead of the queue depends on scheduling), with a margin."""
+    kids = sum(int(c) for c in np.asarray(b["counts"])[level0 + 1:])
+    return max(1 << 20, kids // 4 * 3 * 9 // 8 + 1024)
+
+
 # bytes of one queue record (written once, read once) per precision, for
 # traces without a finite speed of light (FP32-mixed records of FSL traces,
 # which carry the package's age, take 48)
@@ -238,7 +246,7 @@ def run_native(args, rank, world, local):
     def measure(precision, **extra):
         grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
         b = grid.trace(**params, **extra)  # sizes the queue
-        cap = max(1 << 20, int(b["queue_pushed"] * 1.5))
+        cap = queue_capacity_for(b, params["level0"])
         qp = dict(params, queue_capacity=cap, **extra)
         seg_per_step = b["segments"]
         pushed = b["queue_pushed"]
@@ -290,7 +298,7 @@ def run_native(args, rank, world, local):
         host."""
         grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
         b = grid.trace(**params)
-        qp = dict(params, queue_capacity=max(1 << 20, int(b["queue_pushed"] * 1.5)))
+        qp = dict(params, queue_capacity=queue_capacity_for(b, params["level0"]))
         n = grid.ncell
         hx = torch.tensor(g["x_HI"], dtype=torch.float64).pin_memory()
         hz = torch.tensor(g["x_HII"], dtype=torch.float64).pin_memory()
@@ -540,7 +548,7 @@ def clumpy_leg(args, ctx, stream, flush, precision, peaks, peak_kind, local) -> 
     grid = native.Grid(ctx, g, precision, stream=stream.cuda_stream)
     params = dict(synth.DEFAULT_PARAMS)
     b = grid.trace(**params)  # sizes the queue
-    qp = dict(params, queue_capacity=max(1 << 20, int(b["queue_pushed"] * 1.5)))
+    qp = dict(params, queue_capacity=queue_capacity_for(b, params["level0"]))
     for _ in range(max(3, args.warmup)):
         grid.trace(sync=False, **qp)
     torch.cuda.synchronize()
@@ -587,7 +595,7 @@ def photon_types(args, ctx, stream, flush, precision) -> dict:
     grid.set_source_types(g["types"])
     params = dict(synth.DEFAULT_PARAMS)
     b = grid.trace(**params)  # sizes the queue
-    qp = dict(params, queue_capacity=max(1 << 20, int(b["queue_pushed"] * 1.5)))
+    qp = dict(params, queue_capacity=queue_capacity_for(b, params["level0"]))
     x0 = torch.tensor(g["x_HI"], dtype=torch.float64, device=stream.device)
     for _ in range(max(3, args.warmup)):
         native.rt_set_state(grid.h, x0)

@@ -948,7 +948,20 @@ int rt_trace(rt_grid* g, const rt_trace_params* p, rt_budget* out) {
     if (out->status != RT_OK)
       return fail(out->status, "rt_trace: device status %d (queue capacity %llu, largest pass %llu, passes %d)",
                   out->status, (unsigned long long)g->ts.cap, (unsigned long long)out->queue_peak, out->passes);
-    if (automatic) g->ts.passes = passes > p_min && 4 * out->queue_peak < g->ts.cap ? passes / 2 : passes;
+    if (automatic) {
+      g->ts.passes = passes > p_min && 4 * out->queue_peak < g->ts.cap ? passes / 2 : passes;
+      // a repeat of this trace may send every child that is not child 0
+      // through the queue (which of them a free lane of the splitting warp
+      // takes depends on scheduling): keep room for that
+      if (out->passes <= 1) {
+        const unsigned long long need = queue_worst_case(out->counts, p->level0, kLevels);
+        if (need > g->ts.cap) {
+          const unsigned long long limit = queue_cap_limit(rec, (size_t)g->ts.cap * g->ts.rec_bytes);
+          const unsigned long long want = need + need / 8 + 1024;
+          if (want <= limit && (rc = ensure_queue(g, want, rec))) return rc;
+        }
+      }
+    }
     return RT_OK;
   }
 }

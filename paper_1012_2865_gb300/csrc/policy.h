@@ -26,6 +26,18 @@ inline bool grow_after_overflow(unsigned long long peak, unsigned long long limi
   return true;
 }
 
+// Queue records a repeat of a trace can need at most: the three children of
+// every split that went to other lanes (a split keeps child 0; which of the
+// other three a free lane of the splitting warp takes instead of the queue
+// depends on scheduling).  counts[l] = packages created at level l, four per
+// split above level0.
+template <class Count>
+inline unsigned long long queue_worst_case(const Count* counts, int level0, int levels) {
+  unsigned long long kids = 0;
+  for (int l = level0 + 1; l < levels; ++l) kids += (unsigned long long)counts[l];
+  return kids / 4 * 3;
+}
+
 // Segments a lane traces between visits to the queue, from the packages'
 // mean length in the grid's last trace: long rays (optically thin media)
 // gain from fewer warp-wide queue visits, short ones (dense media) from

@@ -1085,7 +1085,9 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
     if (sm | dm) {
       const int leader = __ffs(sm | dm) - 1;
       const unsigned nsp = __popc(sm);
-      const unsigned fm = __ballot_sync(kFull, !split && (!active || ev == EV_DONE) && ticket < 0);
+      // (not in the finite-speed-of-light kernel, which spills at the
+      // register cap already: there the hand-off code cost more than it saved)
+      const unsigned fm = FSL ? 0u : __ballot_sync(kFull, !split && (!active || ev == EV_DONE) && ticket < 0);
       const unsigned nfree = __popc(fm);
       const unsigned nin = nfree < 3u * nsp ? nfree : 3u * nsp;  // children placed in this warp
       const unsigned nq = 3u * nsp - nin;                         // children through the queue
@@ -1108,7 +1110,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
         ev = EV_NONE;
       }
       bool fresh = false;  // a package starts in this lane now
-      if (nin) {
+      if (!FSL && nin) {
         const unsigned q = __popc(fm & lt_mask);
         const bool recv = ((fm >> lane) & 1u) && q < nin;
         Rec c = w.make_child(4u * w.pix);  // in splitting lanes: child 0's record, children differ in pix

@@ -25,6 +25,8 @@ int main() {
     const bool ok = grow_after_overflow(3000000ULL, 1ULL << 26, 5, &cap, &passes);
     printf("grow %d %llu %d\n", ok ? 1 : 0, cap, passes);
   }
+  const unsigned long long counts[5] = {0, 48, 192, 768, 3072};  // level0 1: 48 roots, 3 levels of splits
+  printf("worst %llu %llu\n", queue_worst_case(counts, 1, 5), queue_worst_case(counts, 3, 5));
   std::vector<double> r, n;
   const double cdt[] = {3.5, 3.5, 2.25, 4.0, 3.5, 3.5, 3.5, 3.5, 3.5, 3.5, 3.5, 3.5};
   for (double c : cdt) {
@@ -62,6 +64,13 @@ def test_queue_grows_then_passes_double(output):
     passes = [p for _, _, p in rows]
     assert passes[:3] == [1, 1, 1] and passes[3] == 2 and passes[4] == 4 and max(passes) == 5
     assert rows[-1][0] == 0  # five sources cannot be split further
+
+
+def test_worst_case_queue_counts_three_children_per_split(output):
+    # the children at levels 2-4 (4 per split of 48 + 192 + 768 parents) -> 3 per split
+    # through the queue at most; from level 3 on only the level-4 packages
+    row = [l for l in output if l.startswith("worst")][0].split()
+    assert int(row[1]) == (192 + 768 + 3072) // 4 * 3 and int(row[2]) == 3072 // 4 * 3
 
 
 def test_halting_radii_equal_the_oracle(output):
