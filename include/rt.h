@@ -147,7 +147,9 @@ typedef struct {
   uint64_t segments;                   /* cell segments with length > 0 */
   uint64_t fallbacks;                  /* FP32 crossing/split decisions re-taken in FP64 */
   uint64_t fallbacks_tau;              /* FP32 termination decisions re-taken in FP64 */
-  uint64_t queue_pushed;               /* records written to the queue, all passes */
+  uint64_t queue_pushed;               /* records written to the queue, all passes
+                                          (children taken by a free lane of the
+                                          splitting warp are not queued) */
   int status;                          /* RT_OK or the device-side error */
   float kernel_ms;                     /* duration of the trace launches themselves
                                           (CUDA events on the grid's stream) */
@@ -232,7 +234,12 @@ int rt_get_in_flight(rt_grid* grid, rt_flight* out, uint64_t cap, uint64_t* n);
  * device memory, and beyond that as several launches ("passes") over equal
  * ranges of the sources, which add into the same k_ph, Gamma and budget.  The
  * pass count is kept as the start for the grid's next trace.  A single source
- * whose packages do not fit returns RT_ERR_QUEUE_OVERFLOW. */
+ * whose packages do not fit returns RT_ERR_QUEUE_OVERFLOW.  A split hands
+ * children 1-3 to free lanes of the same warp where it can and queues the
+ * rest, so the records a trace queues vary a little from run to run; after a
+ * successful one-pass trace with queue_capacity 0 the queue is grown to hold
+ * every child of that trace's splits but child 0 (3/4 of the packages created
+ * above level0), so that repeating it cannot overflow. */
 int rt_trace(rt_grid* grid, const rt_trace_params* params, rt_budget* out);
 /* Result of the last trace (synchronises the grid's stream). */
 int rt_get_budget(rt_grid* grid, rt_budget* out);
