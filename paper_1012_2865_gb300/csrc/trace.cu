@@ -92,27 +92,37 @@ struct BlockBudget {
   unsigned int* fb;         // [kShInst][2]: fallbacks, fallbacks_tau
 };
 
+// Grids beyond the block's shared table (rare: batches of more than
+// kShInst grids) flush to global memory, out of line.
+__device__ __noinline__ void acc_flush_global(const LaneAcc& a, const TraceArgs& A) {
+  const InstDev& I = A.inst[a.inst];
+  if (a.emitted != 0.0) atomicAdd(&I.acc[0], a.emitted);
+  if (a.absorbed != 0.0) atomicAdd(&I.acc[1], a.absorbed);
+  if (a.escaped != 0.0) atomicAdd(&I.acc[2], a.escaped);
+  if (a.resumed != 0.0) atomicAdd(&I.acc[3], a.resumed);
+  if (a.halted != 0.0) atomicAdd(&I.acc[4], a.halted);
+  if (a.segments) atomicAdd(&I.cnt[kCntSegments], a.segments);
+  if (a.fallbacks) atomicAdd(&I.cnt[kCntFallbacks], (unsigned long long)a.fallbacks);
+  if (a.fallbacks_tau) atomicAdd(&I.cnt[kCntFallbacksTau], (unsigned long long)a.fallbacks_tau);
+}
 __device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A, const BlockBudget& bb) {
   if (a.inst >= 0 && a.inst < kShInst) {
+    // straight-line shared atomics (adding zeros costs less than branching)
     double* t = bb.sums + kAcc * a.inst;
-    if (a.emitted != 0.0) atomicAdd(&t[0], a.emitted);
-    if (a.absorbed != 0.0) atomicAdd(&t[1], a.absorbed);
-    if (a.escaped != 0.0) atomicAdd(&t[2], a.escaped);
-    if (a.resumed != 0.0) atomicAdd(&t[3], a.resumed);
-    if (a.halted != 0.0) atomicAdd(&t[4], a.halted);
-    if (a.segments) atomicAdd(&bb.segs[a.inst], a.segments);
-    if (a.fallbacks) atomicAdd(&bb.fb[2 * a.inst], a.fallbacks);
-    if (a.fallbacks_tau) atomicAdd(&bb.fb[2 * a.inst + 1], a.fallbacks_tau);
+    atomicAdd(&t[0], a.emitted);
+    atomicAdd(&t[1], a.absorbed);
+    atomicAdd(&t[2], a.escaped);
+    if (a.resumed != 0.0 || a.halted != 0.0) {
+      atomicAdd(&t[3], a.resumed);
+      atomicAdd(&t[4], a.halted);
+    }
+    atomicAdd(&bb.segs[a.inst], a.segments);
+    if (a.fallbacks | a.fallbacks_tau) {
+      atomicAdd(&bb.fb[2 * a.inst], a.fallbacks);
+      atomicAdd(&bb.fb[2 * a.inst + 1], a.fallbacks_tau);
+    }
   } else if (a.inst >= 0) {
-    const InstDev& I = A.inst[a.inst];
-    if (a.emitted != 0.0) atomicAdd(&I.acc[0], a.emitted);
-    if (a.absorbed != 0.0) atomicAdd(&I.acc[1], a.absorbed);
-    if (a.escaped != 0.0) atomicAdd(&I.acc[2], a.escaped);
-    if (a.resumed != 0.0) atomicAdd(&I.acc[3], a.resumed);
-    if (a.halted != 0.0) atomicAdd(&I.acc[4], a.halted);
-    if (a.segments) atomicAdd(&I.cnt[kCntSegments], a.segments);
-    if (a.fallbacks) atomicAdd(&I.cnt[kCntFallbacks], (unsigned long long)a.fallbacks);
-    if (a.fallbacks_tau) atomicAdd(&I.cnt[kCntFallbacksTau], (unsigned long long)a.fallbacks_tau);
+    acc_flush_global(a, A);
   }
   a.emitted = a.absorbed = a.escaped = a.resumed = a.halted = 0.0;
   a.segments = 0;
