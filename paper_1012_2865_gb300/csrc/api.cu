@@ -44,6 +44,8 @@ cudaError_t launch_check_state(long long n, const double* nH, const double* x, u
                                cudaStream_t st);
 cudaError_t launch_check_density(long long n, const double* a, unsigned long long* bad, cudaStream_t st);
 cudaError_t launch_add_word(unsigned long long* w, unsigned long long delta, cudaStream_t st);
+cudaError_t launch_zero_fields(void* a, void* b, size_t nbytes, void* acc, int nacc, void* cnt, int ncnt,
+                               cudaStream_t st);
 cudaError_t launch_pair(long long n, const double* src, void* dst, cudaStream_t st);
 cudaError_t launch_direction_check(int level, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st);
@@ -773,14 +775,12 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool 
   if (rc) return rc;
   cudaStream_t st = g->stream;
   const size_t ne = (size_t)g->ncell * elem_bytes(g->precision);
-  CUDA_TRY(cudaMemsetAsync(g->K, 0, ne, st));  // Step 2
-  CUDA_TRY(cudaMemsetAsync(g->G, 0, ne, st));
+  // Step 2: k_ph, Gamma and the budget words in one launch
+  LAUNCH_TRY(launch_zero_fields(g->K, g->G, ne, g->acc, kAccWords, g->cnt, kCntWords, st));
   for (int t = 0; t < 2 && g->he; ++t) {
     CUDA_TRY(cudaMemsetAsync(g->Khe[t], 0, ne, st));
     CUDA_TRY(cudaMemsetAsync(g->Ghe[t], 0, ne, st));
   }
-  CUDA_TRY(cudaMemsetAsync(g->acc, 0, kAccWords * sizeof(double), st));
-  CUDA_TRY(cudaMemsetAsync(g->cnt, 0, kCntWords * sizeof(unsigned long long), st));
   const int nsrc = (int)g->src.size();
   if (nsrc == 0) {
     LAUNCH_TRY(launch_trace_init(g->ts.ctl, g->ts.queue, g->ts.cap * g->ts.rec_bytes, 0, 1, FLIGHT_OFF, 0, 0, 1, st));

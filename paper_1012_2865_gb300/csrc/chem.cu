@@ -429,6 +429,38 @@ cudaError_t launch_check_density(long long n, const double* a, unsigned long lon
 }
 
 // Adds delta to one device word (the trace self-test's phantom package).
+// Step 2 of a trace in one launch: k_ph and Gamma (two arrays of nbytes
+// each, 16-byte aligned) and the budget words (acc, cnt) to zero.
+__global__ void zero_fields_kernel(uint4* __restrict__ a, uint4* __restrict__ b, size_t n16, size_t nbytes,
+                                   unsigned long long* __restrict__ acc, int nacc, unsigned long long* __restrict__ cnt,
+                                   int ncnt) {
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x) {
+    a[i] = z;
+    b[i] = z;
+  }
+  if (blockIdx.x == 0) {
+    for (size_t t = 16 * n16 + threadIdx.x; t < nbytes; t += blockDim.x) {
+      ((unsigned char*)a)[t] = 0;
+      ((unsigned char*)b)[t] = 0;
+    }
+    for (int t = threadIdx.x; t < nacc; t += blockDim.x) acc[t] = 0ULL;
+    for (int t = threadIdx.x; t < ncnt; t += blockDim.x) cnt[t] = 0ULL;
+  }
+}
+
+cudaError_t launch_zero_fields(void* a, void* b, size_t nbytes, void* acc, int nacc, void* cnt, int ncnt,
+                               cudaStream_t st) {
+  if (((uintptr_t)a & 15u) || ((uintptr_t)b & 15u)) return cudaErrorInvalidValue;
+  const size_t n16 = nbytes / 16;
+  long long blocks = (long long)((n16 + 255) / 256);
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  if (blocks < 1) blocks = 1;
+  zero_fields_kernel<<<(int)blocks, 256, 0, st>>>((uint4*)a, (uint4*)b, n16, nbytes, (unsigned long long*)acc, nacc,
+                                                  (unsigned long long*)cnt, ncnt);
+  return cudaGetLastError();
+}
+
 __global__ void add_word_kernel(unsigned long long* w, unsigned long long delta) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *w += delta;
 }
