@@ -810,7 +810,7 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool 
   A.cap = g->ts.cap;
   A.ctl = g->ts.ctl;
   A.max_steps = 2 * (g->nx + g->ny + g->nz) + 16;
-  if (p->segs_per_iter == 0) A.segs_per_iter = tuned_segs_per_iter(g->seg_per_pkg);
+  if (p->segs_per_iter == 0) A.segs_per_iter = tuned_segs_per_iter(g->seg_per_pkg, !fsl);
   int mode = FLIGHT_OFF;
   unsigned long long in_cap = 0;
   if (fsl) {

@@ -40,12 +40,15 @@ inline unsigned long long queue_worst_case(const Count* counts, int level0, int 
 
 // Segments a lane traces between visits to the queue, from the packages'
 // mean length in the grid's last trace: long rays (optically thin media)
-// gain from fewer warp-wide queue visits, short ones (dense media) from
-// lanes that finish being refilled sooner.  Half the mean, as a power of two
-// in [8, 64]; 16 before any trace was read back.
-inline int tuned_segs_per_iter(double seg_per_pkg) {
+// gain from fewer warp-wide queue visits; without the in-warp hand-off of
+// children (the finite-speed-of-light kernel) short ones gain from lanes
+// that finish being refilled sooner.  Half the mean, as a power of two in
+// [32, 64] with the hand-off (a lane whose package ends mostly takes a child
+// that a split in its warp hands over, so short packages do not want short
+// visits) and in [8, 64] without it; 16 before any trace was read back.
+inline int tuned_segs_per_iter(double seg_per_pkg, bool handoff = true) {
   if (!(seg_per_pkg > 0)) return 16;
-  int s = 8;
+  int s = handoff ? 32 : 8;
   while (s < 64 && s < 0.5 * seg_per_pkg) s *= 2;
   return s;
 }

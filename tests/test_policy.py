@@ -19,7 +19,7 @@ PROGRAM = r"""
 using namespace rtg;
 int main() {
   const double spp[] = {0.0, -1.0, 3.0, 10.0, 16.1, 49.0, 64.0, 100.0, 1e9};
-  for (double v : spp) printf("spi %.17g %d\n", v, tuned_segs_per_iter(v));
+  for (double v : spp) printf("spi %.17g %d %d\n", v, tuned_segs_per_iter(v), tuned_segs_per_iter(v, false));
   unsigned long long cap = 1ULL << 20; int passes = 1;
   for (int k = 0; k < 8; ++k) {
     const bool ok = grow_after_overflow(3000000ULL, 1ULL << 26, 5, &cap, &passes);
@@ -53,7 +53,9 @@ def output(tmp_path_factory):
 
 def test_segments_per_queue_visit(output):
     got = [int(l.split()[2]) for l in output if l.startswith("spi")]
-    assert got == [16, 16, 8, 8, 16, 32, 32, 64, 64]
+    assert got == [16, 16, 32, 32, 32, 32, 32, 64, 64]  # with the in-warp hand-off of children
+    got = [int(l.split()[3]) for l in output if l.startswith("spi")]
+    assert got == [16, 16, 8, 8, 16, 32, 32, 64, 64]  # without (finite speed of light)
 
 
 def test_queue_grows_then_passes_double(output):
