@@ -1,4 +1,5 @@
 // api.cu -- host implementation of the C ABI declared in rt.h.
+#include <utility>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -46,6 +47,9 @@ cudaError_t launch_check_density(long long n, const double* a, unsigned long lon
 cudaError_t launch_add_word(unsigned long long* w, unsigned long long delta, cudaStream_t st);
 cudaError_t launch_zero_fields(void* a, void* b, size_t nbytes, void* acc, int nacc, void* cnt, int ncnt,
                                cudaStream_t st);
+cudaError_t launch_check_refresh(int precision, long long n, unsigned long long* ctl, const double* nH, double* x,
+                                 double* z, int z_given, const double* x_old, const double* z_old, void* nhi,
+                                 InstDev* inst, cudaStream_t st);
 cudaError_t launch_pair(long long n, const double* src, void* dst, cudaStream_t st);
 cudaError_t launch_direction_check(int level, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_direction_table(int level, float4* tab, cudaStream_t st);
@@ -229,13 +233,15 @@ struct rt_grid {
   cudaEvent_t ev_up = nullptr, ev_commit = nullptr, ev_snap = nullptr;
   cudaEvent_t ev_dl[3] = {nullptr, nullptr, nullptr};  // last host copy of each staged field
   double* up_stage = nullptr;                // 3 * ncell doubles: n_H, x_HI, x_HII
+  double* xHI_alt = nullptr;                 // alternate state buffers: an upload without n_H goes
+  double* xHII_alt = nullptr;                // into them and they swap with xHI, xHII on commit
   char* dn_stage = nullptr;                  // 3 * ncell * 8 bytes: k_ph, Gamma, x_HI
   std::string set_err;                       // message of a rejected asynchronous state
   bool check_words_set = false;              // CTL_CHECK_N/X hold ~0 (then kept so by each commit)
   ~rt_grid() {
     if (up) cudaStreamSynchronize(up);
     if (dn) cudaStreamSynchronize(dn);
-    cudaFree(up_stage); cudaFree(dn_stage);
+    cudaFree(up_stage); cudaFree(dn_stage); cudaFree(xHI_alt); cudaFree(xHII_alt);
     for (cudaEvent_t ev : {ev_up, ev_commit, ev_snap, ev_dl[0], ev_dl[1], ev_dl[2]})
       if (ev) cudaEventDestroy(ev);
     if (up) cudaStreamDestroy(up);
@@ -1042,7 +1048,7 @@ static int ensure_async(rt_grid* g, bool stage_up, bool stage_dn) {
   for (cudaEvent_t* ev : evs)
     if (!*ev) CUDA_TRY(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
   const size_t n8 = (size_t)g->ncell * 8;
-  if (stage_up && !g->up_stage) CUDA_TRY(cudaMalloc((void**)&g->up_stage, 3 * n8));
+  if (stage_up && !g->up_stage) CUDA_TRY(cudaMalloc((void**)&g->up_stage, 3 * n8));  // uploads with n_H
   if (stage_dn && !g->dn_stage) CUDA_TRY(cudaMalloc((void**)&g->dn_stage, 3 * n8));
   if (!g->check_words_set) {
     // ~0 = no failing cell; every commit leaves them so for the next upload
@@ -1059,7 +1065,7 @@ int rt_set_state_async(rt_grid* g, const double* n_H, const double* x_HI, const 
     return fail(RT_ERR_INVALID_ARG, "rt_set_state_async: mem_kind %d", mem_kind);
   if (g->batch) return fail(RT_ERR_STATE, "rt_set_state_async: the grid is in a batch (use rt_set_state)");
   CUDA_TRY(cudaSetDevice(g->ctx->device));
-  int rc = ensure_async(g, mem_kind == RT_MEM_HOST, false);
+  int rc = ensure_async(g, mem_kind == RT_MEM_HOST && n_H != nullptr, false);
   if (rc) return rc;
   const long long n = g->ncell;
   const size_t n8 = (size_t)n * 8;
@@ -1067,6 +1073,24 @@ int rt_set_state_async(rt_grid* g, const double* n_H, const double* x_HI, const 
   const double* sn = n_H;
   const double* sx = x_HI;
   const double* sz = x_HII;
+  if (mem_kind == RT_MEM_HOST && !n_H) {
+    // Straight into the alternate buffers, which the grid's kernels last
+    // used before the previous commit; one kernel checks the new state and
+    // refreshes n_HI (undoing it if rejected), and the buffers swap.
+    if (!g->xHI_alt) CUDA_TRY(cudaMalloc((void**)&g->xHI_alt, n8));
+    if (!g->xHII_alt) CUDA_TRY(cudaMalloc((void**)&g->xHII_alt, n8));
+    CUDA_TRY(cudaStreamWaitEvent(g->up, g->ev_commit, 0));
+    CUDA_TRY(cudaMemcpyAsync(g->xHI_alt, x_HI, n8, cudaMemcpyHostToDevice, g->up));
+    if (x_HII) CUDA_TRY(cudaMemcpyAsync(g->xHII_alt, x_HII, n8, cudaMemcpyHostToDevice, g->up));
+    CUDA_TRY(cudaEventRecord(g->ev_up, g->up));
+    CUDA_TRY(cudaStreamWaitEvent(st, g->ev_up, 0));
+    LAUNCH_TRY(launch_check_refresh(g->precision, n, g->ts.ctl, g->nH, g->xHI_alt, g->xHII_alt, x_HII != nullptr,
+                                    g->xHI, g->xHII, g->nhi, g->inst_dev, st));
+    CUDA_TRY(cudaEventRecord(g->ev_commit, st));
+    std::swap(g->xHI, g->xHI_alt);
+    std::swap(g->xHII, g->xHII_alt);
+    return RT_OK;
+  }
   if (mem_kind == RT_MEM_HOST) {
     // the staging area is free once the previous commit has read it
     CUDA_TRY(cudaStreamWaitEvent(g->up, g->ev_commit, 0));

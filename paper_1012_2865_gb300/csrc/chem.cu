@@ -309,6 +309,71 @@ __global__ void commit_state2_kernel(long long n2, unsigned long long* __restric
   commit_finish(ctl);
 }
 
+// Commit of a state uploaded straight into the grid's alternate buffers
+// (rt_set_state_async from host memory without n_H; the host has already
+// made x and z the grid's arrays).  Every block checks its cells' x_HI and
+// writes their n_HI = n_H x_HI (and x_HII = 1 - x_HI when none was uploaded)
+// as if the state passed; the block that finishes last (CTL_COMMIT_DONE)
+// takes the verdict.  A rejected state is undone by that block -- the
+// previous state copied into x and z and n_HI recomputed from it, so the
+// grid ends as it was -- and latched in ctl[CTL_SET_ERR].  Either way it
+// points the grid's device descriptor at x and z and sets the check words
+// back to ~0.
+template <bool PAIR>
+__global__ void check_refresh_kernel(long long n, unsigned long long* __restrict__ ctl, const double* __restrict__ nH,
+                                     double* __restrict__ x, double* __restrict__ z, int z_given,
+                                     const double* __restrict__ x_old, const double* __restrict__ z_old,
+                                     void* __restrict__ nhi, InstDev* __restrict__ inst) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const double xv = x[c];
+    if (!(xv >= 0.0 && xv <= 1.0)) atomicMin(&ctl[CTL_CHECK_X], (unsigned long long)c);
+    if (!z_given) z[c] = __dsub_rn(1.0, xv);
+    const double v = __dmul_rn(nH[c], xv);
+    if (PAIR) {
+      const F2 p = f2_from_double(v);
+      ((float2*)nhi)[c] = make_float2(p.hi, p.lo);
+    } else {
+      ((double*)nhi)[c] = v;
+    }
+  }
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&ctl[CTL_COMMIT_DONE], 1ULL) == (unsigned long long)gridDim.x - 1ULL;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const unsigned long long bx = ctl[CTL_CHECK_X];
+  if (bx != ~0ULL) {
+    if (threadIdx.x == 0 && atomicCAS(&ctl[CTL_SET_ERR], 0ULL, (unsigned long long)RT_ERR_INVALID_ARG) == 0ULL) {
+      ctl[CTL_SET_BADN] = ~0ULL;
+      ctl[CTL_SET_BADX] = bx;
+    }
+    for (long long c = threadIdx.x; c < n; c += blockDim.x) {
+      const double xv = x_old[c];
+      x[c] = xv;
+      z[c] = z_old[c];
+      const double v = __dmul_rn(nH[c], xv);
+      if (PAIR) {
+        const F2 p = f2_from_double(v);
+        ((float2*)nhi)[c] = make_float2(p.hi, p.lo);
+      } else {
+        ((double*)nhi)[c] = v;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    inst->xHI = x;
+    inst->xHII = z;
+    ctl[CTL_CHECK_N] = ~0ULL;
+    ctl[CTL_CHECK_X] = ~0ULL;
+    ctl[CTL_COMMIT_DONE] = 0ULL;
+  }
+}
+
 // Adaptive RT timestep (Sec. 3.4), step 1, Eq. "dtelec": per cell
 // eps / |k_ph + n_e alpha_B| (C_H = 0, n_e = n_H (1 - x_HI)) where the cell's
 // optical depth sdx n_HI exceeds tau_front, else dt_max; never above dt_max.
@@ -505,6 +570,17 @@ cudaError_t launch_commit_state(int precision, long long n, unsigned long long* 
     commit_state_kernel<false><<<grid, block, 0, st>>>(n, ctl, sn, sx, sz, nH, xHI, xHII, nhi);
   else
     commit_state_kernel<true><<<grid, block, 0, st>>>(n, ctl, sn, sx, sz, nH, xHI, xHII, nhi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_refresh(int precision, long long n, unsigned long long* ctl, const double* nH, double* x,
+                                 double* z, int z_given, const double* x_old, const double* z_old, void* nhi,
+                                 InstDev* inst, cudaStream_t st) {
+  const int block = 256, grid = grid_for(n, block);
+  if (precision == RT_FP64)
+    check_refresh_kernel<false><<<grid, block, 0, st>>>(n, ctl, nH, x, z, z_given, x_old, z_old, nhi, inst);
+  else
+    check_refresh_kernel<true><<<grid, block, 0, st>>>(n, ctl, nH, x, z, z_given, x_old, z_old, nhi, inst);
   return cudaGetLastError();
 }
 
