@@ -272,10 +272,12 @@ int rt_get_rates(rt_grid* grid, void* kph, void* gamma, void* x_HI, int dtype, i
  *
  * rt_set_state_async: as rt_set_state, but returns once the work is
  * enqueued.  Host arrays (best pinned) are copied on a stream of the
- * library's into a staging area, concurrently with the grid's kernels, and
- * must stay unchanged until that copy is done (rt_synchronize, or any call
- * that waits for the grid); device arrays are read in the grid's stream
- * order.  The state is checked on the device as rt_set_state checks it; a
+ * library's, concurrently with the grid's kernels -- x_HI and x_HII straight
+ * into a second pair of state arrays that the grid swaps for its own once
+ * the state is checked (the grid holds two copies of its state from the first
+ * such call), n_H when given into a staging area -- and must stay unchanged
+ * until that copy is done (rt_synchronize, or any call that waits for the
+ * grid); device arrays are read in the grid's stream order.  The state is checked on the device as rt_set_state checks it; a
  * state that fails leaves the grid unchanged and is reported as
  * RT_ERR_INVALID_ARG, naming the first failing cell, by the next
  * rt_synchronize, rt_get_budget or waiting rt_trace (every trace enqueued
