@@ -63,6 +63,9 @@ def test_rejected_async_state_changes_nothing_and_is_reported_once(ctx):
     grid = native.Grid(ctx, g, "fp32_mixed")
     good = np.full(grid.ncell, 0.25)
     native.rt_set_state_async(grid.h, _pinned(good))
+    p = dict(synth.DEFAULT_PARAMS, checksums=True)
+    before = grid.trace(**p)
+    z_before = grid.x_HII()
     bad = good.copy()
     bad[1234] = 1.5
     native.rt_set_state_async(grid.h, _pinned(bad))
@@ -70,7 +73,12 @@ def test_rejected_async_state_changes_nothing_and_is_reported_once(ctx):
         native.rt_synchronize(grid.h)
     assert ei.value.code == native.RT_ERR_INVALID_ARG and "x_HI[1234]" in str(ei.value)
     assert np.array_equal(grid.rates()["x_HI"], good)
+    assert np.array_equal(grid.x_HII(), z_before)
     native.rt_synchronize(grid.h)  # reported once
+    # the absorber density was restored too: the same trace as before the rejected upload
+    after = grid.trace(**p)
+    assert after["segments"] == before["segments"]
+    assert np.array_equal(after["counts"], before["counts"]) and np.array_equal(after["hashes"], before["hashes"])
     # a rejection is also the status of the next trace, which still runs on the kept state
     bad_n = np.full(grid.ncell, 1e-3)
     bad_n[7] = -1.0
