@@ -7,9 +7,11 @@
 // source = ticket / N_pix, pixel = ticket % N_pix, P = 1 in units of the
 // source's Ndot / N_pix) and need no memory; higher tickets name queue slots
 // that split packages publish.  When a package splits (Step 3e) its lane
-// keeps child 0 and appends children 1-3 to the queue (one atomic per warp
-// reserves the slots); each record's tag word is stored last with release
-// semantics and polled with acquire loads.  An outstanding-package counter
+// keeps child 0 and hands children 1-3 to lanes of its warp whose package
+// ended in the same round (no package, no ticket), by warp shuffles; the
+// rest go to the queue (one atomic per warp reserves the slots), where each
+// 32-byte record's tag word is stored last with release semantics and
+// polled with acquire loads.  An outstanding-package counter
 // (+3 per split, -1 per finished package) tells idle warps when the trace is
 // over.  Every wait is bounded: a warp that sees no change of the counter for
 // timeout_ns sets RT_ERR_TIMEOUT and leaves; a package that takes more steps
@@ -27,7 +29,8 @@
 // radius would pass rlim[a]; the cut segment is deposited, the termination
 // test comes first, and the package is appended to an output store with its
 // cell.  The next trace's tickets n_roots .. n_roots + n_res - 1 name the
-// stored packages, which continue from their cells.
+// stored packages, which continue from their cells.  This instantiation
+// queues every child 1-3, in 48-byte records that carry the age.
 #include <type_traits>
 #include <cuda_runtime.h>
 #include <math.h>
