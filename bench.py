@@ -277,7 +277,7 @@ def run_native(args, rank, world, local):
                 step_ms.append(e0.elapsed_time(e1))
                 kern_ms.append(bb["kernel_ms"])
                 segs += bb["segments"]
-                assert bb["segments"] == seg_per_step
+                assert bb["segments"] == seg_per_step, (bb["status"], bb["segments"], seg_per_step)
         torch.cuda.synchronize()
         barrier()
         final = grid.rates()  # one step from the snapshot: k_ph of the trace, x_HI after the update
