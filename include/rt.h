@@ -233,7 +233,8 @@ int rt_get_in_flight(rt_grid* grid, rt_flight* out, uint64_t cap, uint64_t* n);
  * queue is redone with a larger queue, up to 2^31 records or half the free
  * device memory, and beyond that as several launches ("passes") over equal
  * ranges of the sources, which add into the same k_ph, Gamma and budget.  The
- * pass count is kept as the start for the grid's next trace.  A single source
+ * passes the sizing added (not params->passes) are kept as the start for the
+ * grid's next trace.  A single source
  * whose packages do not fit returns RT_ERR_QUEUE_OVERFLOW.  A split hands
  * children 1-3 to free lanes of the same warp where it can and queues the
  * rest, so the records a trace queues vary a little from run to run; after a

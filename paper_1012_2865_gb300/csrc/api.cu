@@ -955,7 +955,9 @@ int rt_trace(rt_grid* g, const rt_trace_params* p, rt_budget* out) {
       return fail(out->status, "rt_trace: device status %d (queue capacity %llu, largest pass %llu, passes %d)",
                   out->status, (unsigned long long)g->ts.cap, (unsigned long long)out->queue_peak, out->passes);
     if (automatic) {
-      g->ts.passes = passes > p_min && 4 * out->queue_peak < g->ts.cap ? passes / 2 : passes;
+      // remember the passes the sizing added (halved while the queue is
+      // under a quarter full), not the caller's minimum
+      if (passes > p_min) g->ts.passes = 4 * out->queue_peak < g->ts.cap ? passes / 2 : passes;
       // a repeat of this trace may send every child that is not child 0
       // through the queue (which of them a free lane of the splitting warp
       // takes depends on scheduling): keep room for that
@@ -1831,7 +1833,7 @@ int rt_batch_trace(rt_batch* b, const rt_trace_params* p, int sync) {
     if (bs.status != RT_OK)
       return fail(bs.status, "rt_batch_trace: device status %d (queue capacity %llu, largest pass %llu, passes %d)",
                   bs.status, (unsigned long long)b->ts.cap, bs.peak, b->ts.passes_run);
-    if (automatic) b->ts.passes = passes > p_min && 4 * bs.peak < b->ts.cap ? passes / 2 : passes;
+    if (automatic && passes > p_min) b->ts.passes = 4 * bs.peak < b->ts.cap ? passes / 2 : passes;
     return RT_OK;
   }
 }

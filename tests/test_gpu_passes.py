@@ -56,6 +56,8 @@ def test_passes_equal_one_launch_and_the_oracle(precision):
         _same(b, grid.rates(), b1, r1, SUM_ORDER_TOL[precision])
     b = grid.trace(checksums=True, passes=3, **synth.DEFAULT_PARAMS)
     parity.assert_trace_parity(g, b, grid.rates(), parity.run_oracle(g), precision)
+    # a caller's minimum holds for its own call only
+    assert grid.trace(**synth.DEFAULT_PARAMS)["passes"] == 1
     grid.close()
 
 
@@ -95,6 +97,8 @@ def test_batch_passes_and_graph_steps():
         b = batch.budget(s)
         assert b["passes"] == 5
         _same(b, gr.rates(), b_ref, r_ref, SUM_ORDER_TOL["fp32_mixed"])
+    batch.trace(**synth.DEFAULT_PARAMS)
+    assert batch.budget(slots[0])["passes"] == 1
     # graph steps with passes equal graph steps without
     ref = []
     for g in gs:
