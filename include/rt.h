@@ -424,7 +424,8 @@ const char* rt_probe_last_error(void);
  *
  * It runs the same FP32-mixed trace as rt_trace on a grid the caller holds in
  * device memory, and keeps all scratch (package queue, control words, budget
- * sums, source records, a table of pixel directions) in one static device
+ * sums and per-block budget rows, source records, a table of pixel
+ * directions) in one static device
  * array of about 10 MiB that every device loading the library holds until the
  * process exits.  It calls no cudaMalloc, cudaFree or other allocating
  * routine.  Limits: at most RT_NOALLOC_MAX_SOURCES sources and

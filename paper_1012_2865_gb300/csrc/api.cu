@@ -146,11 +146,24 @@ struct TraceState {
   unsigned long long cap = 0;  // records
   size_t rec_bytes = 0;
   unsigned long long* ctl = nullptr;
+  double* blk = nullptr;  // per-block budget rows (allocated with the grid or batch)
+  int blk_blocks = 0;     // blocks the rows are allocated for
+  int blk_rows = 0;       // grids per block
   int passes = 1;       // source ranges the last automatically sized trace used
   int passes_run = 1;   // passes of the last trace launched
   ~TraceState() {
     if (queue) cudaFree(queue);
     if (ctl) cudaFree(ctl);
+    if (blk) cudaFree(blk);
+  }
+  // Rows for `blocks` blocks of a launch over `ninst` grids.
+  int bind_rows(TraceArgs& A, int blocks, int ninst) const {
+    if (blocks > blk_blocks)
+      return fail(RT_ERR_INVALID_ARG, "trace launch of %d blocks exceeds the %d blocks of its budget rows", blocks,
+                  blk_blocks);
+    A.blk = blk;
+    A.blk_rows = ninst < blk_rows ? ninst : blk_rows;
+    return RT_OK;
   }
 };
 
@@ -383,6 +396,9 @@ int rt_create_grid(rt_ctx* ctx, const rt_grid_desc* d, void* stream, rt_grid** o
   ALLOC(g->cnt, kCntWords * sizeof(unsigned long long));
   ALLOC(g->inst_dev, sizeof(InstDev));
   ALLOC(g->ts.ctl, CTL_N * sizeof(unsigned long long));
+  ALLOC(g->ts.blk, blk_rows_bytes(ctx->num_sms, 1));
+  g->ts.blk_blocks = ctx->num_sms * kBlkMaxPerSM;
+  g->ts.blk_rows = 1;
 #undef ALLOC
   cudaStream_t st = g->stream;
   if ((rc = upload(g->nH, d->n_H, n8, d->mem_kind, st)) != RT_OK) { delete g; return rc; }
@@ -829,6 +845,7 @@ static int enqueue_trace(rt_grid* g, const rt_trace_params* p, int passes, bool 
   CUDA_TRY(trace_occupancy(g->precision, fsl ? 1 : 0, block, &per_sm));
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
+  if ((rc = g->ts.bind_rows(A, per_sm * g->ctx->num_sms, 1))) return rc;
   if ((rc = launch_passes(A, g->ts.cap * g->ts.rec_bytes, g->src_dev, nsrc, passes, g->precision, fsl ? 1 : 0, mode,
                           in_cap, per_sm * g->ctx->num_sms, g->ev0, g->ev1, st, (p->flags & RT_TRACE_SELFTEST_STALL) != 0)))
     return rc;
@@ -1635,6 +1652,7 @@ static int batch_enqueue(rt_batch* b, const rt_trace_params* p, int passes) {
   CUDA_TRY(trace_occupancy(b->precision, 0, 256, &per_sm));
   if (per_sm < 1) per_sm = 1;
   if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
+  if ((rc = b->ts.bind_rows(A, per_sm * b->ctx->num_sms, ninst))) return rc;
   if ((rc = launch_passes(A, b->ts.cap * b->ts.rec_bytes, b->src_dev, b->nsrc, passes, b->precision, 0, FLIGHT_OFF, 0,
                           per_sm * b->ctx->num_sms,
                           b->ev0, b->ev1, st)))
@@ -1716,6 +1734,11 @@ int rt_batch_create(rt_ctx* ctx, void* stream, rt_batch** out) {
   }
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->ts.ctl, CTL_N * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemsetAsync(b->ts.ctl, 0, CTL_N * sizeof(unsigned long long), b->stream);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->ts.blk, blk_rows_bytes(ctx->num_sms, kBlkGrids));
+  if (e == cudaSuccess) {
+    b->ts.blk_blocks = ctx->num_sms * kBlkMaxPerSM;
+    b->ts.blk_rows = kBlkGrids;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);

@@ -55,7 +55,9 @@ constexpr size_t kNaSrcOff = 2048;  // RT_NOALLOC_MAX_SOURCES SourceDev
 constexpr size_t kNaTabOff = na_align(kNaSrcOff + (size_t)RT_NOALLOC_MAX_SOURCES * sizeof(SourceDev));
 constexpr size_t kNaQueueOff = na_align(kNaTabOff + kNaTableEntries * 2 * sizeof(float4));
 constexpr size_t kNaQueueBytes = (size_t)RT_NOALLOC_MAX_RECORDS * sizeof(QRec32);
-constexpr size_t kNaBytes = kNaQueueOff + kNaQueueBytes;
+constexpr int kNaMaxBlocks = 2048;  // trace blocks the budget rows are laid out for
+constexpr size_t kNaBlkOff = na_align(kNaQueueOff + kNaQueueBytes);
+constexpr size_t kNaBytes = kNaBlkOff + (size_t)kNaMaxBlocks * kBlkRow * sizeof(double);
 static_assert(CTL_N * 8 <= kNaAccOff && kNaAccOff + kNaAccWords * 8 <= kNaCntOff && kNaCntOff + kCntWords * 8 <= kNaInstOff &&
                   sizeof(InstDev) <= kNaSrcOff - kNaInstOff,
               "scratch layout");
@@ -254,6 +256,9 @@ int rt_trace_noalloc(const rt_noalloc_grid* g, int nsrc, const double* pos_cm, c
     if ((e = trace_occupancy(RT_FP32_MIXED, 0, 256, &per_sm)) != cudaSuccess) return na_fail(RT_ERR_CUDA, "occupancy", e);
     if (per_sm < 1) per_sm = 1;
     if (p->blocks_per_sm > 0 && p->blocks_per_sm < per_sm) per_sm = p->blocks_per_sm;
+    if (per_sm * sms > kNaMaxBlocks) return na_fail(RT_ERR_INVALID_ARG, "more trace blocks than the budget rows hold");
+    A.blk = (double*)(base + kNaBlkOff);
+    A.blk_rows = 1;
     if ((e = launch_trace(RT_FP32_MIXED, 0, A, per_sm * sms, 256, st)) != cudaSuccess)
       return na_fail(RT_ERR_CUDA, "trace launch", e);
     long long blocks = ((long long)ncell + 255) / 256;

@@ -103,6 +103,20 @@ constexpr int kCntFallbacks = 2 * kLevels + 1;
 constexpr int kCntFallbacksTau = 2 * kLevels + 2;
 constexpr int kCntWords = 2 * kLevels + 3;
 
+// Per-block budget rows of a trace launch (global memory, one buffer per
+// grid or batch): for each block and each of the launch's first kBlkGrids
+// grids, kBlkRow 8-byte words (emitted, absorbed, escaped, resumed, halted
+// as doubles, then the segment count as an unsigned 64-bit integer).  A
+// lane adds its sums there with fire-and-forget reductions when its next
+// package belongs to another grid; the block adds its rows into the grid's
+// sums when it finishes.
+constexpr int kBlkGrids = 64;
+constexpr int kBlkRow = 6;
+constexpr int kBlkMaxPerSM = 8;  // 256-thread blocks: at most 2048 threads per SM
+inline size_t blk_rows_bytes(int num_sms, int rows) {
+  return (size_t)num_sms * kBlkMaxPerSM * (size_t)rows * kBlkRow * sizeof(double);
+}
+
 // Queue records.  The tag word is written last with release semantics and
 // equals the trace's epoch once the record is complete.  The same layouts
 // hold packages in flight between traces (finite speed of light), where the
@@ -183,6 +197,10 @@ struct TraceArgs {
   const void* res_in;       // packages halted by the previous trace (Rec)
   void* halt_out;           // packages this trace halts (Rec)
   unsigned long long halt_cap;
+  // per-block budget rows: [gridDim.x][blk_rows][kBlkRow] words,
+  // blk_rows = min(ninst, kBlkGrids); each block clears its own rows
+  double* blk;
+  int blk_rows;
 };
 
 // 64-bit finaliser used for the created-package checksum (documented in rt.h).

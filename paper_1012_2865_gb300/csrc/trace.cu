@@ -47,7 +47,8 @@
 namespace rtg {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kShInst = 64;  // grids whose budget and level counters a block keeps in shared memory
+constexpr int kShInst = 64;  // grids whose level counters and fallback counts a block keeps in shared memory
+static_assert(kBlkGrids <= kShInst, "a grid with a budget row has its counters in shared memory");
 constexpr int kBlock = 256;  // threads per block of the trace kernel
 
 enum Event { EV_NONE = 0, EV_SPLIT = 1, EV_DONE = 2, EV_HALT = 3 };
@@ -85,18 +86,21 @@ struct LaneAcc {
 };
 static_assert(sizeof(LaneAcc) == 72, "conflict-free stride of the per-lane sums");
 
-// A block's budget sums per grid, in shared memory, for the first kShInst
-// grids of the launch: a lane that moves to a package of another grid adds
-// its sums here (shared atomics) instead of into global memory, and the
-// block flushes the table once at the end.
+// A block's budget sums per grid for the first kBlkGrids grids of the
+// launch: its rows of TraceArgs.blk (global memory, kBlkRow words per grid)
+// and, for the rare fallback counts, a table in shared memory.  A lane that
+// moves to a package of another grid adds its sums to the rows with
+// reductions whose results it does not wait for; the block adds its rows
+// into the grids' sums once at the end.  (Shared-memory FP64 atomics, which
+// return their result, cost the 64-grid batch 11 % of its trace time.)
 struct BlockBudget {
-  double* sums;             // [kShInst][kAcc]: emitted, absorbed, escaped, resumed, halted
-  unsigned long long* segs; // [kShInst]
+  double* rows;             // [nrows][kBlkRow]: emitted, absorbed, escaped, resumed, halted, segments
+  int nrows;                // min(grids of the launch, kBlkGrids)
   unsigned int* fb;         // [kShInst][2]: fallbacks, fallbacks_tau
 };
 
-// Grids beyond the block's shared table (rare: batches of more than
-// kShInst grids) flush to global memory, out of line.
+// Grids beyond the block's rows (rare: batches of more than kBlkGrids
+// grids) flush to the grid's sums directly, out of line.
 __device__ __noinline__ void acc_flush_global(const LaneAcc& a, const TraceArgs& A) {
   const InstDev& I = A.inst[a.inst];
   if (a.emitted != 0.0) atomicAdd(&I.acc[0], a.emitted);
@@ -109,9 +113,9 @@ __device__ __noinline__ void acc_flush_global(const LaneAcc& a, const TraceArgs&
   if (a.fallbacks_tau) atomicAdd(&I.cnt[kCntFallbacksTau], (unsigned long long)a.fallbacks_tau);
 }
 __device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A, const BlockBudget& bb) {
-  if (a.inst >= 0 && a.inst < kShInst) {
-    // straight-line shared atomics (adding zeros costs less than branching)
-    double* t = bb.sums + kAcc * a.inst;
+  if (a.inst >= 0 && a.inst < bb.nrows) {
+    // straight-line reductions (adding zeros costs less than branching)
+    double* t = bb.rows + kBlkRow * a.inst;
     atomicAdd(&t[0], a.emitted);
     atomicAdd(&t[1], a.absorbed);
     atomicAdd(&t[2], a.escaped);
@@ -119,7 +123,7 @@ __device__ __forceinline__ void acc_flush(LaneAcc& a, const TraceArgs& A, const 
       atomicAdd(&t[3], a.resumed);
       atomicAdd(&t[4], a.halted);
     }
-    atomicAdd(&bb.segs[a.inst], a.segments);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&t[kAcc]), a.segments);
     if (a.fallbacks | a.fallbacks_tau) {
       atomicAdd(&bb.fb[2 * a.inst], a.fallbacks);
       atomicAdd(&bb.fb[2 * a.inst + 1], a.fallbacks_tau);
@@ -940,17 +944,15 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   __shared__ unsigned int sh_cnt[kShInst * kLevels];
   __shared__ unsigned long long sh_hsh[kShInst * kLevels];
   __shared__ LaneAcc sh_acc[kBlock];
-  __shared__ double sh_bsum[kShInst * kAcc];
-  __shared__ unsigned long long sh_bseg[kShInst];
   __shared__ unsigned int sh_bfb[kShInst * 2];
   for (int i = threadIdx.x; i < kShInst * kLevels; i += blockDim.x) {
     sh_cnt[i] = 0;
     sh_hsh[i] = 0;
   }
-  for (int i = threadIdx.x; i < kShInst * kAcc; i += blockDim.x) sh_bsum[i] = 0.0;
+  double* const brow = A.blk + (size_t)blockIdx.x * A.blk_rows * kBlkRow;
+  for (int i = threadIdx.x; i < A.blk_rows * kBlkRow; i += blockDim.x) brow[i] = 0.0;  // also 0 as an integer
   for (int i = threadIdx.x; i < kShInst * 2; i += blockDim.x) sh_bfb[i] = 0u;
-  for (int i = threadIdx.x; i < kShInst; i += blockDim.x) sh_bseg[i] = 0ULL;
-  const BlockBudget BB{sh_bsum, sh_bseg, sh_bfb};
+  const BlockBudget BB{brow, A.blk_rows, sh_bfb};
   LaneAcc& acc = sh_acc[threadIdx.x];
   acc.emitted = acc.absorbed = acc.escaped = acc.resumed = acc.halted = 0.0;
   acc.segments = acc.fallbacks = acc.fallbacks_tau = 0;
@@ -1210,12 +1212,18 @@ __global__ void __launch_bounds__(kBlock, MinBlocks) trace_kernel(TraceArgs A) {
   } else {
     acc_flush(acc, A, BB);
   }
+  // the block's reductions into its rows are complete and visible before
+  // the rows are read back (from L2)
+  __threadfence();
   __syncthreads();
-  for (int i = threadIdx.x; i < kShInst && i < A.ninst; i += blockDim.x) {
+  for (int i = threadIdx.x; i < A.blk_rows; i += blockDim.x) {
     const InstDev& I = A.inst[i];
-    for (int k = 0; k < kAcc; ++k)
-      if (sh_bsum[kAcc * i + k] != 0.0) atomicAdd(&I.acc[k], sh_bsum[kAcc * i + k]);
-    if (sh_bseg[i]) atomicAdd(&I.cnt[kCntSegments], sh_bseg[i]);
+    for (int k = 0; k < kAcc; ++k) {
+      const double v = __ldcg(&brow[kBlkRow * i + k]);
+      if (v != 0.0) atomicAdd(&I.acc[k], v);
+    }
+    const unsigned long long sg = __ldcg(reinterpret_cast<const unsigned long long*>(&brow[kBlkRow * i + kAcc]));
+    if (sg) atomicAdd(&I.cnt[kCntSegments], sg);
     if (sh_bfb[2 * i]) atomicAdd(&I.cnt[kCntFallbacks], (unsigned long long)sh_bfb[2 * i]);
     if (sh_bfb[2 * i + 1]) atomicAdd(&I.cnt[kCntFallbacksTau], (unsigned long long)sh_bfb[2 * i + 1]);
   }
