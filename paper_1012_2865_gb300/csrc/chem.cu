@@ -664,8 +664,13 @@ cudaError_t launch_batch_zero(const InstDev* inst, int ninst, int precision, lon
 cudaError_t launch_batch_chem(const InstDev* inst, int ninst, int precision, long long max_cells, double h,
                               int nsub, double alpha, cudaStream_t st) {
   if (ninst <= 0) return cudaSuccess;
-  long long bx = (max_cells + 255) / 256;
-  if (bx > 64) bx = 64;
+  // blocks per grid for ~4096 cells each (up to 1024): a grid's cells are
+  // spread over blocks in proportion to its size, so the largest grids of a
+  // batch do not finish last on a few blocks; the blocks a smaller grid does
+  // not need return at once.  (64 blocks per grid took 4.0 vs 2.5 ms on the
+  // 64-grid batch.)
+  long long bx = (max_cells + 4095) / 4096;
+  if (bx > 1024) bx = 1024;
   if (bx < 1) bx = 1;
   if (precision == RT_FP64)
     batch_chem_kernel<false><<<dim3((unsigned)bx, (unsigned)ninst), 256, 0, st>>>(inst, h, nsub, alpha,
